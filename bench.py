@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of the map-maker's hot path on the ACT-like patch (1024 detectors x
+2^20 samples, 1200x900 TQU map at 0.5', FP32 time-ordered data with FP64 CG).
+
+A step is one iteration of circulant-preconditioned conjugate gradients: one
+application of A = P^T N^-1 P (pointing, gather, noise filter, binning), the
+FP64 CG vector updates and one application of the circulant preconditioner
+(2-D FFTs and the per-mode 3x3 solve).  ``value`` is samples per second per
+A-application inside that loop (N_s / time per iteration), with all inputs
+resident in HBM.  The time-ordered spectra streamed every step (4.3 GB) exceed
+L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "samples/s per P^T N^-1 P apply (inside circulant PCG)"
+UNIT = "samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
+    ap.add_argument("--n-det", type=int, default=1024)
+    ap.add_argument("--n-t", type=int, default=1 << 20)
+    ap.add_argument("--det-chunk", type=int, default=0)
+    ap.add_argument("--taper", type=float, default=20.0)
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-6 solves")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    return {"workload": f"ACT-like patch: {args.n_det} det hex 1 deg, {args.n_t} samples/det at 400 Hz, "
+                        f"10 deg throw rising+setting, 1200x900 TQU CAR 0.5'",
+            "n_det": args.n_det, "n_samp": args.n_t, "map": [3, 900, 1200],
+            "precon": "circulant", "taper_sigma_px": args.taper,
+            "l2": "no flush: 4.3 GB of spectra streamed per step exceed the 129 MB L2"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_rate(args, seconds, rank=0):
+    """Samples/s of the FP64 CPU oracle's A-application on a bounded sample of the
+    workload (the first few detectors of the same scan)."""
+    import numpy as np
+
+    import gen
+    from oracle import mapmaker as om
+    scan, noise = gen.config2(real=rank, n_det=args.n_det, n_t=args.n_t)
+    n_sub = 4
+    sub = scan.subset(np.arange(n_sub))
+    nsub = noise.subset(np.arange(n_sub))
+    mask = om.pixel_mask(sub)
+    op = om.make_operator(sub, nsub, mask)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=2, real=rank)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        om.apply_A(op, m)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    rate = reps * n_sub * scan.n_t / el
+    sample = (f"{reps} oracle A-applications of {n_sub} of {scan.n_det} detectors "
+              f"({n_sub * scan.n_t} samples each) in {el:.1f} s")
+    return rate, sample
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import gen
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    prec = {"f32": cmm.PREC_F32, "f64": cmm.PREC_F64, "bf16": cmm.PREC_BF16}[args.prec]
+    t_setup = time.perf_counter()
+    scan, noise = gen.config2(real=rank, n_det=args.n_det, n_t=args.n_t)
+    n_s = scan.n_det * scan.n_t
+    with torch.cuda.stream(stream):
+        ctx = cmm.Context(dev, stream=stream.cuda_stream)
+        op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=args.det_chunk)
+        m_sky = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=2, real=rank), device=f"cuda:{dev}")
+        tod = op.project(m_sky)                 # noise-free TOD, as in the paper's test
+        b = op.rhs(tod)
+        del tod
+        t_pc = time.perf_counter()
+        pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=args.taper)
+        stream.synchronize()
+        t_pc = time.perf_counter() - t_pc
+    setup_s = time.perf_counter() - t_setup
+
+    def iterate(k):
+        x = op.new_map()
+        cmm.cmm_solve(op.h, pc.h, b, x, 0.0, k, k, True, False, None, None)
+
+    with torch.cuda.stream(stream):
+        iterate(args.warmup)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            iterate(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * n_s * args.steps / (ms / 1e3)
+
+    # per-pass durations of the A-application (CUDA events between its kernels)
+    with torch.cuda.stream(stream):
+        mo = op.new_map()
+        prof = cmm.cmm_profile_apply(op.h, b, mo, 5)
+    names = ["k_tod_fwd (pointing+gather+FFT pass 1)", "k_tod_filter (FFT pass 2 + N^-1)",
+             "k_tod_inv_bin (inverse FFT pass + P^T)"]
+    chunk_dets = min(op_chunk(op, scan, args), scan.n_det)
+    elt = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
+    per_launch_bytes = [elt // 2 * chunk_dets * scan.n_t, elt * chunk_dets * scan.n_t,
+                        elt // 2 * chunk_dets * scan.n_t]
+    dom = int(np.argmax(prof[:3]))
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = per_launch_bytes[dom] / (prof[dom] / 1e3) / 1e9
+    apply_bytes = 2 * elt * n_s + 16 * scan.n_t + scan.npix * (3 * 8 * 2 + 16 * 2)
+    apply_gbs = apply_bytes / (prof[4] / 1e3) / 1e9
+
+    # end to end through the host-buffer entry point: H2D map, A, D2H map per step
+    m_host = torch.empty((3, scan.ny, scan.nx), dtype=torch.float64).pin_memory()
+    m_host.copy_(m_sky.cpu())
+    out_host = torch.empty_like(m_host).pin_memory()
+    mi, mo_np = m_host.numpy(), out_host.numpy()
+    cmm.cmm_apply_A_host(op.h, mi, mo_np)
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        cmm.cmm_apply_A_host(op.h, mi, mo_np)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    map_bytes = 3 * scan.npix * 8
+
+    solves = None
+    if not args.no_solve:
+        solves = {}
+        with torch.cuda.stream(stream):
+            for name, kind, kw in (("binned", cmm.PRECON_BINNED, {}),
+                                   ("circulant", cmm.PRECON_CIRCULANT, {"taper_sigma_px": args.taper})):
+                t1 = time.perf_counter()
+                p2 = pc if name == "circulant" else cmm.Precon(op, kind, **kw)
+                torch.cuda.synchronize()
+                build_s = 0.0 if name == "circulant" else time.perf_counter() - t1
+                if name == "circulant":
+                    build_s = t_pc
+                x, info, _, _ = cmm.solve(op, p2, b, tol=1e-6, maxit=1000, check_every=10)
+                solves[name] = {"iterations": info.iterations, "status": cmm.STATUS[info.status],
+                                "seconds": round(info.seconds, 4), "build_seconds": round(build_s, 4),
+                                "rel_resid": info.rel_resid}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f32": "f32 (FP64 CG)", "f64": "f64", "bf16": "bf16-storage/f32"}[args.prec],
+        "data": "synthetic (seeded ACT-like scan, C_l ~ l^-2 sky, noise-free TOD as in the paper's test)",
+        "config": {**workload(args), "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "global_batch": world, "seq_len": scan.n_t},
+        "gpu_launches": None,
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                     "algorithmic_bytes_per_launch": per_launch_bytes[dom]},
+        "apply": {"ms": prof[4], "samples_per_s": n_s / (prof[4] / 1e3), "algorithmic_GBps": apply_gbs,
+                  "frac_of_measured_hbm": apply_gbs / peak,
+                  "ms_per_pass": {"fwd": prof[0], "filter": prof[1], "inv_bin": prof[2], "map_copies": prof[3]},
+                  "det_chunk": chunk_dets},
+        "e2e": {"value": n_s / e2e_s, "unit": UNIT, "h2d_bytes_per_step": map_bytes, "d2h_bytes_per_step": map_bytes,
+                "step": "cmm_apply_A_host: H2D map, A, D2H map"},
+        "solves_to_1e-6": solves,
+        "setup_seconds": round(setup_s, 2),
+        "clocks": clocks,
+    }
+    nchunks = math.ceil(scan.n_det / chunk_dets)
+    it_launches = 3 * nchunks + 2 + 6 + 12   # A (3 per chunk + 2 map copies), CG kernels, circulant apply
+    out["gpu_launches"] = it_launches * args.steps
+    return out
+
+
+def op_chunk(op, scan, args):
+    if args.det_chunk > 0:
+        return args.det_chunk
+    elt = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
+    return max(1, (8 << 30) // (elt * scan.n_t // 2))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cores = 1
+        rates = []
+        t_all = time.perf_counter()
+        per = max(1.0, args.cpu_seconds / max(1, args.steps))
+        for _ in range(args.warmup):
+            oracle_rate(args, 0.1)
+        sample = ""
+        for _ in range(args.steps):
+            r, sample = oracle_rate(args, per)
+            rates.append(r)
+        value = statistics.mean(rates)
+        el = time.perf_counter() - t_all
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        rate, sample = oracle_rate(args, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

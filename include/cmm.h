@@ -1,0 +1,209 @@
+/*
+ * cmm.h -- C ABI of the GB300 map-maker: maximum-likelihood CMB map-making by
+ * preconditioned conjugate gradients with the binned, Jacobi and circulant
+ * ("constant correlation") preconditioners of Naess & Louis, "A fast map-making
+ * preconditioner for regular scanning patterns" (arXiv:1309.7473).
+ *
+ * Conventions for every call
+ * --------------------------
+ * - Every call returns an int status: CMM_OK (0) or one of CMM_ERR_*; the text of
+ *   the last error of the calling thread is returned by cmm_last_error().
+ * - Handles (cmm_ctx, cmm_pointing, cmm_noise, cmm_op, cmm_precon) are created and
+ *   freed by the library; each *_destroy frees the device memory the handle owns.
+ *   Handles must be destroyed before the context they were made from.
+ * - "host" arguments are ordinary host memory that the call reads (or writes)
+ *   before it returns.  "device" arguments are caller-owned device memory on the
+ *   context's device, at least 16-byte aligned; the library never frees them.
+ * - Maps are FP64 device arrays laid out [ncomp][ny][nx] (Stokes-major, x fastest),
+ *   ncomp = 1 (T) or 3 (T, Q, U).  Pixel (iy, ix) is centred at map coordinate
+ *   (x, y) = (ix, iy) in pixel units.
+ * - All device work is issued on the stream given to cmm_ctx_create, in order;
+ *   calls return without waiting unless stated (cmm_solve waits; *_host calls wait).
+ * - Calls on one handle are not thread-safe; different contexts may be used from
+ *   different threads.
+ */
+#ifndef CMM_H
+#define CMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum cmm_status {
+  CMM_OK = 0,
+  CMM_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad enum) */
+  CMM_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed */
+  CMM_ERR_OOM = 3,            /* device allocation failed */
+  CMM_ERR_BREAKDOWN = 4,      /* PCG breakdown: p^T A p <= 0, r^T z <= 0 or a non-finite scalar */
+  CMM_ERR_NOT_CONVERGED = 5,  /* maxit reached before the tolerance */
+  CMM_ERR_TIMEOUT = 6,        /* a bounded device wait ran out */
+  CMM_ERR_UNSUPPORTED = 7     /* size or mode not implemented (e.g. n_samp not a power of two) */
+};
+
+/* Arithmetic of the operator A = P^T N^-1 P.
+ * F64: everything in FP64 (parity mode).
+ * F32: time-ordered data, FFTs, noise filter and projection in FP32; map accumulator,
+ *      CG vectors and scalars in FP64.
+ * BF16: as F32, but the intermediate half-spectra are stored in BF16 between passes. */
+enum cmm_precision { CMM_PREC_F64 = 0, CMM_PREC_F32 = 1, CMM_PREC_BF16 = 2 };
+
+enum cmm_precon_kind {
+  CMM_PRECON_BINNED = 0,    /* M_B, Eq. 3-4: per-pixel inverse of P^T diag(N^-1) P */
+  CMM_PRECON_JACOBI = 1,    /* M_J, Eq. 5: per-pixel inverse of P^T P */
+  CMM_PRECON_CIRCULANT = 2, /* M_C, Eq. 7-13 with the Gaussian regularisation */
+  CMM_PRECON_IDENTITY = 3   /* M = I (plain CG) */
+};
+
+typedef struct cmm_ctx cmm_ctx;
+typedef struct cmm_pointing cmm_pointing;
+typedef struct cmm_noise cmm_noise;
+typedef struct cmm_op cmm_op;
+typedef struct cmm_precon cmm_precon;
+
+/* Map geometry: ny rows of nx pixels, ncomp Stokes components (1 or 3);
+ * periodic != 0 wraps pixel indices instead of cutting samples that fall off
+ * the map. */
+typedef struct {
+  int32_t ny, nx, ncomp, periodic;
+} cmm_map_geom;
+
+typedef struct {
+  double taper_sigma_px; /* Gaussian regularisation width in pixels (Sec. Regularization); <= 0 or inf: off */
+  int64_t ref_pixel;     /* linear index of the reference pixel (Sec. Implementation); -1: nearest the centre */
+  double pd_eps;         /* eigenvalue floor relative to the largest mode eigenvalue; <= 0: 1e-6 */
+} cmm_precon_opts;
+
+typedef struct {
+  double tol;          /* stop when ||r_k|| / ||b|| <= tol */
+  int32_t maxit;       /* iteration limit */
+  int32_t check_every; /* iterations per captured graph launch between host checks (>= 1) */
+  int32_t use_graph;   /* != 0: replay the iteration as a CUDA graph */
+  int32_t x0_given;    /* != 0: x holds the starting guess; else x0 = 0 */
+} cmm_solve_opts;
+
+typedef struct {
+  int32_t iterations;   /* A-applications inside the loop */
+  int32_t status;       /* CMM_OK, CMM_ERR_NOT_CONVERGED or CMM_ERR_BREAKDOWN */
+  double rel_resid;     /* last recursive ||r|| / ||b|| */
+  double seconds;       /* wall time of the call */
+} cmm_solve_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int cmm_ctx_create(int device, void* stream, cmm_ctx** out);
+int cmm_ctx_destroy(cmm_ctx* ctx);
+/* Text of the calling thread's last error ("" if none).  Valid until the next call. */
+const char* cmm_last_error(void);
+/* Version string of the library. */
+const char* cmm_version(void);
+
+/* ---------------------------------------------------------------- pointing
+ * The pointing matrix P of Eq. 1, never stored: each sample's pixel and response
+ * are computed on the fly from a boresight table and a detector table.
+ *   bore    host int32 [n_samp][4]: (bx, by) boresight in units of 2^-16 pixel,
+ *           (cphi, sphi) = (cos, sin) of the sky rotation in units of 2^-30.
+ *   det_off host int32 [n_det][2]: (dx, dy) detector offset in units of 2^-16 pixel.
+ *   det_pol host double [n_det][2]: (cos 2psi, sin 2psi) of the detector angle psi.
+ * Sample (d, t) lies at x = (bx << 30) + cphi*dx - sphi*dy, y = (by << 30) + sphi*dx
+ * + cphi*dy (units of 2^-46 pixel, exact in int64) and hits pixel ix = (x + 2^45) >> 46,
+ * iy likewise (nearest pixel, halves rounded up).  Its row of P is (1) for T maps and
+ * (1, cos 2a, sin 2a), a = psi + phi, for TQU maps (Sec. Test setup).  Samples off
+ * the map (unless periodic) and samples of masked pixels have a zero row.  A pixel is
+ * masked when its unit-weight hit block sum_t P_t P_t^T has no hits or reciprocal
+ * condition number below 1e-3.  The tables are copied; `bore` requires
+ * |cphi|, |sphi| <= 2^30.
+ */
+int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det,
+                        const int32_t* det_off, const double* det_pol, int64_t n_samp,
+                        const int32_t* bore, cmm_pointing** out);
+int cmm_pointing_destroy(cmm_pointing* pt);
+/* Copy the pixel mask (host uint8 [ny*nx], 1 = solved for) and return the number
+ * of unmasked pixels in *n_good (may be NULL). */
+int cmm_pointing_mask(cmm_pointing* pt, uint8_t* mask_host, int64_t* n_good);
+
+/* ---------------------------------------------------------------- noise
+ * Stationary per-detector noise (Eq. 1: n gaussian with covariance N), applied as
+ * the Fourier-diagonal filter N_d^-1 = F^-1 diag(w_d) F over the n_samp samples of
+ * each detector, w_d(f) = 1 / (sigma_d^2 (1 + (f / fknee_d)^-alpha_d)),
+ * f_k = k f_samp / n_samp; fknee_d = 0 means white noise; the k = 0 bin takes the
+ * k = 1 value.  sigma, fknee, alpha: host double [n_det].
+ */
+int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
+                     const double* sigma, const double* fknee, const double* alpha,
+                     cmm_noise** out);
+int cmm_noise_destroy(cmm_noise* nz);
+/* diag(N_d^-1) = mean of w_d over the two-sided DFT grid (host double [n_det]). */
+int cmm_noise_diag(cmm_noise* nz, double* diag_host);
+
+/* ---------------------------------------------------------------- operator
+ * A = P^T N^-1 P (Eq. 2) in the given precision.  n_samp must be a power of two,
+ * 32 <= n_samp <= 2^25.  det_chunk > 0 bounds how many detectors share one pass
+ * through the intermediate spectrum buffer (<= 0: automatic).  The handle owns
+ * that buffer (n_chunk * n_samp * 4 bytes in F32, 8 in F64, 2 in BF16) and a few
+ * map-sized buffers.
+ */
+int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precision,
+                  int32_t det_chunk, cmm_op** out);
+int cmm_op_destroy(cmm_op* op);
+/* m_out = A m_in (Eq. 2).  device double [ncomp][ny][nx] each; must not alias. */
+int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out);
+/* Same with host buffers: copies m_in to the device, applies A, copies the result
+ * back and waits. */
+int cmm_apply_A_host(cmm_op* op, const double* m_in_host, double* m_out_host);
+/* Profiling: runs `reps` applications of A (as cmm_apply_A) with CUDA events
+ * between its kernels and waits.  ms_host (host double [5]) receives the mean
+ * duration in milliseconds of one launch of the forward pass (pointing, gather,
+ * first FFT pass), of the filter pass, of the inverse pass with binning (per
+ * detector chunk), of the map-side copies per application, and of one whole
+ * application. */
+int cmm_profile_apply(cmm_op* op, const double* m_in, double* m_out, int32_t reps, double* ms_host);
+/* tod = P m (Eq. 1): device double [ncomp][ny][nx] -> device float [n_det][n_samp]
+ * (tod_is_f64 = 0) or double (tod_is_f64 != 0). */
+int cmm_project(cmm_op* op, const double* m, void* tod, int32_t tod_is_f64);
+/* b = P^T N^-1 d (right-hand side of Eq. 2): device float or double [n_det][n_samp]
+ * -> device double [ncomp][ny][nx]. */
+int cmm_rhs(cmm_op* op, const void* tod, int32_t tod_is_f64, double* b);
+/* *result_host = x^T y over n FP64 device elements (a deterministic tree sum);
+ * waits for the result. */
+int cmm_dot(cmm_op* op, const double* x, const double* y, int64_t n, double* result_host);
+
+/* ---------------------------------------------------------------- preconditioners
+ * BINNED (Eq. 3-4): blocks B_p = sum_t diag(N^-1)_d P_t P_t^T, M_B = B_p^-1 per pixel.
+ * JACOBI (Eq. 5): the same with unit weights.
+ * CIRCULANT (Eq. 7-13): Sigma = B_p^(1/2) (symmetric), rows A e_{ref,gamma} (Eq. 6),
+ *   Q row (Eq. 13), made symmetric (q_k + q_{-k}^T)/2, multiplied by the Gaussian
+ *   exp(-|k|^2 / (2 s^2)) over wrapped offsets (Sec. Regularization), H_f = (Fq)*_f
+ *   (Eq. 11) inverted per Fourier mode with eigenvalues floored at pd_eps * max;
+ *   applied as z = Sigma^-1 F^-1 H^-1 F Sigma^-1 r (Eq. 12).
+ * opts may be NULL (taper off, centre reference pixel, pd_eps 1e-6).  The circulant
+ * build runs ncomp applications of A.
+ */
+int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm_precon** out);
+int cmm_precon_destroy(cmm_precon* pc);
+/* z = M r: device double [ncomp][ny][nx] each. */
+int cmm_precon_apply(cmm_precon* pc, const double* r, double* z);
+/* Number of Fourier modes whose eigenvalues were floored (circulant), else 0. */
+int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped);
+
+/* ---------------------------------------------------------------- solver
+ * Preconditioned conjugate gradients on A x = b (Eq. 2, with M ~ A^-1 as in the
+ * Introduction's footnote).  b, x: device double [ncomp][ny][nx]; x receives the
+ * solution (and holds x0 if opts->x0_given).  resid_hist (device double
+ * [maxit + 1], may be NULL) receives ||r_k|| / ||b||; anorm_terms (device double
+ * [maxit], may be NULL) receives alpha_k r_k^T z_k, whose sums over the next d
+ * steps estimate the squared error A-norm (Results footnote).  Waits for the
+ * result; info->status reports convergence.
+ */
+int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x,
+              const cmm_solve_opts* opts, double* resid_hist, double* anorm_terms,
+              cmm_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMM_H */

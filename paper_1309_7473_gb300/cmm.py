@@ -1,0 +1,376 @@
+"""Thin Python binding of the map-maker's C ABI (``include/cmm.h``).
+
+The functions ``cmm_*`` below marshal arguments to the entry points of the same
+name in ``libcmm.so``: torch tensors are passed as raw device pointers, numpy
+arrays as host pointers.  No map-making arithmetic happens here; every step runs
+in the library's CUDA kernels.  There is no CPU fallback: importing this module
+without the built library raises.
+
+The small classes (Context, Pointing, Noise, Operator, Precon) own the library
+handles and free them when garbage-collected.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcmm.so")
+
+PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+PRECON_BINNED, PRECON_JACOBI, PRECON_CIRCULANT, PRECON_IDENTITY = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN",
+          5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+
+
+class CmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MapGeom(C.Structure):
+    _fields_ = [("ny", C.c_int32), ("nx", C.c_int32), ("ncomp", C.c_int32), ("periodic", C.c_int32)]
+
+
+class PreconOpts(C.Structure):
+    _fields_ = [("taper_sigma_px", C.c_double), ("ref_pixel", C.c_int64), ("pd_eps", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
+                ("use_graph", C.c_int32), ("x0_given", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_resid", C.c_double),
+                ("seconds", C.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_1309_7473_gb300/build.py "
+                      "(or __graft_entry__.build()) first")
+_lib = C.CDLL(LIB_PATH)
+
+_vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_PP = C.POINTER(C.c_void_p)
+_SIGS = {
+    "cmm_ctx_create": [C.c_int, _vp, _PP],
+    "cmm_ctx_destroy": [_vp],
+    "cmm_pointing_create": [_vp, C.POINTER(MapGeom), _i32, _vp, _vp, _i64, _vp, _PP],
+    "cmm_pointing_destroy": [_vp],
+    "cmm_pointing_mask": [_vp, _vp, C.POINTER(_i64)],
+    "cmm_noise_create": [_vp, _i32, _i64, _d, _vp, _vp, _vp, _PP],
+    "cmm_noise_destroy": [_vp],
+    "cmm_noise_diag": [_vp, _vp],
+    "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
+    "cmm_op_destroy": [_vp],
+    "cmm_apply_A": [_vp, _vp, _vp],
+    "cmm_apply_A_host": [_vp, _vp, _vp],
+    "cmm_profile_apply": [_vp, _vp, _vp, _i32, _vp],
+    "cmm_project": [_vp, _vp, _vp, _i32],
+    "cmm_rhs": [_vp, _vp, _i32, _vp],
+    "cmm_dot": [_vp, _vp, _vp, _i64, C.POINTER(_d)],
+    "cmm_precon_create": [_vp, _i32, C.POINTER(PreconOpts), _PP],
+    "cmm_precon_destroy": [_vp],
+    "cmm_precon_apply": [_vp, _vp, _vp],
+    "cmm_precon_clamped": [_vp, C.POINTER(_i64)],
+    "cmm_solve": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveInfo)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.cmm_last_error.restype = C.c_char_p
+_lib.cmm_last_error.argtypes = []
+_lib.cmm_version.restype = C.c_char_p
+_lib.cmm_version.argtypes = []
+
+EXPORTED = sorted(list(_SIGS) + ["cmm_last_error", "cmm_version"])
+
+
+def _check(code):
+    if code != 0:
+        raise CmmError(code, _lib.cmm_last_error().decode())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dev(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (checked)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- raw entry points
+
+def cmm_version() -> str:
+    return _lib.cmm_version().decode()
+
+
+def cmm_last_error() -> str:
+    return _lib.cmm_last_error().decode()
+
+
+def cmm_ctx_create(device: int, stream: int):
+    h = C.c_void_p()
+    _check(_lib.cmm_ctx_create(device, C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def cmm_ctx_destroy(h):
+    _check(_lib.cmm_ctx_destroy(h))
+
+
+def cmm_pointing_create(ctx, ny, nx, ncomp, periodic, det_off, det_pol, bore):
+    geom = MapGeom(ny, nx, ncomp, 1 if periodic else 0)
+    det_off, p_off = _host(det_off, np.int32)
+    det_pol, p_pol = _host(det_pol, np.float64)
+    bore, p_bore = _host(bore, np.int32)
+    n_det = det_off.shape[0]
+    if det_off.shape != (n_det, 2) or det_pol.shape != (n_det, 2) or bore.ndim != 2 or bore.shape[1] != 4:
+        raise ValueError("bad pointing table shapes")
+    h = C.c_void_p()
+    _check(_lib.cmm_pointing_create(ctx, C.byref(geom), n_det, p_off, p_pol, bore.shape[0], p_bore, C.byref(h)))
+    return h
+
+
+def cmm_pointing_destroy(h):
+    _check(_lib.cmm_pointing_destroy(h))
+
+
+def cmm_pointing_mask(h, npix):
+    out = np.empty(npix, np.uint8)
+    n = C.c_int64()
+    _check(_lib.cmm_pointing_mask(h, out.ctypes.data_as(C.c_void_p), C.byref(n)))
+    return out.astype(bool), int(n.value)
+
+
+def cmm_noise_create(ctx, n_samp, f_samp, sigma, fknee, alpha):
+    sigma, ps = _host(sigma, np.float64)
+    fknee, pf = _host(fknee, np.float64)
+    alpha, pa = _host(alpha, np.float64)
+    h = C.c_void_p()
+    _check(_lib.cmm_noise_create(ctx, sigma.size, n_samp, f_samp, ps, pf, pa, C.byref(h)))
+    return h
+
+
+def cmm_noise_destroy(h):
+    _check(_lib.cmm_noise_destroy(h))
+
+
+def cmm_noise_diag(h, n_det):
+    out = np.empty(n_det)
+    _check(_lib.cmm_noise_diag(h, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def cmm_op_create(ctx, pointing, noise, precision=PREC_F32, det_chunk=0):
+    h = C.c_void_p()
+    _check(_lib.cmm_op_create(ctx, pointing, noise, precision, det_chunk, C.byref(h)))
+    return h
+
+
+def cmm_op_destroy(h):
+    _check(_lib.cmm_op_destroy(h))
+
+
+def cmm_apply_A(op, m_in, m_out):
+    _check(_lib.cmm_apply_A(op, _dev(m_in, name="m_in"), _dev(m_out, name="m_out")))
+
+
+def cmm_apply_A_host(op, m_in: np.ndarray, m_out: np.ndarray):
+    if m_in.dtype != np.float64 or m_out.dtype != np.float64 or not m_out.flags.c_contiguous:
+        raise ValueError("host maps must be contiguous float64")
+    m_in = np.ascontiguousarray(m_in)
+    _check(_lib.cmm_apply_A_host(op, m_in.ctypes.data_as(C.c_void_p), m_out.ctypes.data_as(C.c_void_p)))
+
+
+def cmm_profile_apply(op, m_in, m_out, reps):
+    """Mean ms per launch: [forward pass, filter pass, inverse+binning pass, map copies, whole apply]."""
+    out = np.zeros(5)
+    _check(_lib.cmm_profile_apply(op, _dev(m_in, name="m_in"), _dev(m_out, name="m_out"), int(reps),
+                                  out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def cmm_project(op, m, tod):
+    import torch
+    _check(_lib.cmm_project(op, _dev(m, torch.float64, name="m"), _dev(tod, name="tod"),
+                            1 if tod.dtype == torch.float64 else 0))
+
+
+def cmm_rhs(op, tod, b):
+    import torch
+    if tod.dtype not in (torch.float32, torch.float64):
+        raise ValueError("tod must be float32 or float64")
+    _check(_lib.cmm_rhs(op, _dev(tod, name="tod"), 1 if tod.dtype == torch.float64 else 0,
+                        _dev(b, torch.float64, name="b")))
+
+
+def cmm_dot(op, x, y):
+    out = C.c_double()
+    _check(_lib.cmm_dot(op, _dev(x), _dev(y), x.numel(), C.byref(out)))
+    return out.value
+
+
+def cmm_precon_create(op, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0):
+    opts = PreconOpts(float(taper_sigma_px), int(ref_pixel), float(pd_eps))
+    h = C.c_void_p()
+    _check(_lib.cmm_precon_create(op, kind, C.byref(opts), C.byref(h)))
+    return h
+
+
+def cmm_precon_destroy(h):
+    _check(_lib.cmm_precon_destroy(h))
+
+
+def cmm_precon_apply(pc, r, z):
+    _check(_lib.cmm_precon_apply(pc, _dev(r, name="r"), _dev(z, name="z")))
+
+
+def cmm_precon_clamped(pc):
+    n = C.c_int64()
+    _check(_lib.cmm_precon_clamped(pc, C.byref(n)))
+    return int(n.value)
+
+
+def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
+              resid_hist=None, anorm_terms=None):
+    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0)
+    info = SolveInfo()
+    _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
+                          _dev(resid_hist, numel=None, name="resid_hist"),
+                          _dev(anorm_terms, numel=None, name="anorm_terms"), C.byref(info)))
+    return info
+
+
+# ---------------------------------------------------------------- handle owners
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        self.h = cmm_ctx_create(device, stream)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_ctx_destroy(self.h)
+            self.h = None
+
+
+class Pointing:
+    def __init__(self, ctx: Context, scan):
+        self.ctx = ctx
+        self.scan = scan
+        self.shape = (scan.ncomp, scan.ny, scan.nx)
+        self.h = cmm_pointing_create(ctx.h, scan.ny, scan.nx, scan.ncomp, scan.periodic,
+                                     scan.det_off, scan.det_pol, scan.bore)
+
+    def mask(self):
+        return cmm_pointing_mask(self.h, self.scan.npix)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_pointing_destroy(self.h)
+            self.h = None
+
+
+class Noise:
+    def __init__(self, ctx: Context, noise, n_samp, f_samp):
+        self.ctx = ctx
+        self.n_det = noise.sigma.size
+        self.h = cmm_noise_create(ctx.h, n_samp, f_samp, noise.sigma, noise.fknee, noise.alpha)
+
+    def diag(self):
+        return cmm_noise_diag(self.h, self.n_det)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_noise_destroy(self.h)
+            self.h = None
+
+
+class Operator:
+    """A = P^T N^-1 P for one scan and noise model."""
+
+    def __init__(self, ctx: Context, scan, noise, precision=PREC_F32, det_chunk=0):
+        self.ctx = ctx
+        self.pointing = Pointing(ctx, scan)
+        self.noise = Noise(ctx, noise, scan.n_t, scan.f_samp)
+        self.shape = self.pointing.shape
+        self.n_det, self.n_t = scan.n_det, scan.n_t
+        self.h = cmm_op_create(ctx.h, self.pointing.h, self.noise.h, precision, det_chunk)
+
+    def new_map(self):
+        import torch
+        return torch.zeros(self.shape, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+
+    def apply(self, m, out=None):
+        out = self.new_map() if out is None else out
+        cmm_apply_A(self.h, m, out)
+        return out
+
+    def project(self, m, dtype=None):
+        import torch
+        tod = torch.empty((self.n_det, self.n_t), dtype=dtype or torch.float32, device=m.device)
+        cmm_project(self.h, m, tod)
+        return tod
+
+    def rhs(self, tod, out=None):
+        out = self.new_map() if out is None else out
+        cmm_rhs(self.h, tod, out)
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_op_destroy(self.h)
+            self.h = None
+
+
+class Precon:
+    def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0):
+        self.op = op
+        self.kind = kind
+        self.h = cmm_precon_create(op.h, kind, taper_sigma_px, ref_pixel, pd_eps)
+
+    def apply(self, r, out=None):
+        out = self.op.new_map() if out is None else out
+        cmm_precon_apply(self.h, r, out)
+        return out
+
+    def clamped(self):
+        return cmm_precon_clamped(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_precon_destroy(self.h)
+            self.h = None
+
+
+def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=10, use_graph=True,
+          history=False):
+    """PCG on A x = b; returns (x, info, resid_hist, anorm_terms)."""
+    import torch
+    x0_given = x is not None
+    x = op.new_map() if x is None else x
+    hist = torch.zeros(maxit + 1, dtype=torch.float64, device=b.device) if history else None
+    terms = torch.zeros(max(maxit, 1), dtype=torch.float64, device=b.device) if history else None
+    info = cmm_solve(op.h, pc.h, b, x, tol, maxit, check_every, use_graph, x0_given, hist, terms)
+    return x, info, hist, terms

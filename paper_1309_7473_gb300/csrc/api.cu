@@ -1,0 +1,777 @@
+// Host runtime and C ABI of the map-maker (include/cmm.h).
+#include <math.h>
+
+#include <cmath>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "map_kernels.cuh"
+
+// ------------------------------------------------------------------ errors
+namespace cmm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  g_err = std::string(cudaGetErrorString(e)) + " in " + what + " (" + file + ":" + std::to_string(line) + ")";
+  return e == cudaErrorMemoryAllocation ? CMM_ERR_OOM : CMM_ERR_CUDA;
+}
+
+template <typename P>
+static int dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CMM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return CMM_OK;
+}
+
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+
+// diag(N^-1) per detector: deterministic FP64 sum of w over the two-sided grid
+__global__ void k_noise_diag(const double4_32a* __restrict__ coef, long long n_t, double* __restrict__ out) {
+  const int d = blockIdx.x;
+  const double4_32a cf = coef[d];
+  const long long N = n_t / 2;
+  double acc = 0.0;
+  for (long long k = threadIdx.x; k <= N; k += blockDim.x) {
+    double w;
+    if (cf.w != 0.0) {
+      w = cf.x;
+    } else {
+      const double kk = (double)(k == 0 ? 1 : k);
+      w = cf.x / (1.0 + exp2(fma(-cf.y, log2(kk), cf.z)));
+    }
+    acc += (k == 0 || k == N) ? w : 2.0 * w;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[d] = sh[0] / (double)n_t;
+}
+
+__global__ void k_set_unit(double* __restrict__ v, long long idx) { v[idx] = 1.0; }
+
+}  // namespace cmm
+
+using namespace cmm;
+
+struct cmm_precon {
+  cmm_op* op = nullptr;
+  int kind = 0;
+  double* inv = nullptr;       // binned / Jacobi: inverse blocks
+  double* sig = nullptr;       // circulant: Sigma
+  double* sig_inv = nullptr;   // circulant: Sigma^-1
+  double* hinv = nullptr;      // circulant: per-mode packed inverse
+  void* planes = nullptr;      // complex workspace [ncomp][npix]
+  double* tmp = nullptr;       // [ncomp * npix]
+  Fft2Plan plan;
+  int64_t n_clamped = 0;
+  int64_t ref = -1;
+  double taper = 0.0;
+};
+
+extern "C" {
+
+const char* cmm_last_error(void) { return g_err.c_str(); }
+
+const char* cmm_version(void) { return "cmm 0.1 (sm_103a)"; }
+
+int cmm_ctx_create(int device, void* stream, cmm_ctx** out) {
+  if (!out) return fail(CMM_ERR_ARG, "out is null");
+  *out = nullptr;
+  int n = 0;
+  CMM_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(CMM_ERR_ARG, "bad device index");
+  CMM_CUDA(cudaSetDevice(device));
+  cmm_ctx* c = new cmm_ctx();
+  c->device = device;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
+    }
+    c->own_stream = true;
+  }
+  int s = dalloc(&c->d_partial, sizeof(double) * (kRedBlocks + 16));
+  if (s == CMM_OK) s = dalloc(&c->d_scalar, sizeof(double) * 16);
+  if (s == CMM_OK && cudaMallocHost(&c->h_scalar, sizeof(double) * 64) != cudaSuccess) s = fail(CMM_ERR_OOM, "pinned alloc");
+  if (s != CMM_OK) {
+    cmm_ctx_destroy(c);
+    return s;
+  }
+  *out = c;
+  return CMM_OK;
+}
+
+int cmm_ctx_destroy(cmm_ctx* c) {
+  if (!c) return CMM_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c->d_partial);
+  dfree(c->d_scalar);
+  if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ pointing
+int cmm_pointing_destroy(cmm_pointing* pt) {
+  if (!pt) return CMM_OK;
+  cudaSetDevice(pt->ctx->device);
+  cudaStreamSynchronize(pt->ctx->stream);
+  dfree(pt->bore);
+  dfree(pt->det_off);
+  dfree(pt->det_pol64);
+  dfree(pt->det_pol32);
+  dfree(pt->mask);
+  delete pt;
+  return CMM_OK;
+}
+
+int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, const int32_t* det_off,
+                        const double* det_pol, int64_t n_samp, const int32_t* bore, cmm_pointing** out) {
+  if (!ctx || !geom || !det_off || !det_pol || !bore || !out) return fail(CMM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (geom->ny <= 0 || geom->nx <= 0 || (long long)geom->ny * geom->nx > (1LL << 30))
+    return fail(CMM_ERR_ARG, "bad map size");
+  if (geom->ncomp != 1 && geom->ncomp != 3) return fail(CMM_ERR_ARG, "ncomp must be 1 or 3");
+  if (n_det <= 0 || n_samp <= 0 || n_det > 65535) return fail(CMM_ERR_ARG, "bad detector or sample count");
+  CMM_CUDA(cudaSetDevice(ctx->device));
+  cmm_pointing* pt = new cmm_pointing();
+  pt->ctx = ctx;
+  pt->ny = geom->ny;
+  pt->nx = geom->nx;
+  pt->ncomp = geom->ncomp;
+  pt->periodic = geom->periodic ? 1 : 0;
+  pt->n_det = n_det;
+  pt->n_t = n_samp;
+  pt->npix = (int64_t)geom->ny * geom->nx;
+  std::vector<float2> pol32(n_det);
+  for (int d = 0; d < n_det; ++d) pol32[d] = float2{(float)det_pol[2 * d], (float)det_pol[2 * d + 1]};
+  double* blocks = nullptr;
+  const int nb = pt->ncomp == 1 ? 1 : 6;
+  int s = dalloc(&pt->bore, sizeof(int4) * n_samp);
+  if (s == CMM_OK) s = dalloc(&pt->det_off, sizeof(int2) * n_det);
+  if (s == CMM_OK) s = dalloc(&pt->det_pol64, sizeof(double2) * n_det);
+  if (s == CMM_OK) s = dalloc(&pt->det_pol32, sizeof(float2) * n_det);
+  if (s == CMM_OK) s = dalloc(&pt->mask, pt->npix);
+  if (s == CMM_OK) s = dalloc(&blocks, sizeof(double) * nb * pt->npix);
+  if (s != CMM_OK) {
+    dfree(blocks);
+    cmm_pointing_destroy(pt);
+    return s;
+  }
+  cudaStream_t st = ctx->stream;
+  auto run = [&]() -> int {
+    CMM_CUDA(cudaMemcpyAsync(pt->bore, bore, sizeof(int4) * n_samp, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemcpyAsync(pt->det_off, det_off, sizeof(int2) * n_det, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemcpyAsync(pt->det_pol64, det_pol, sizeof(double2) * n_det, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemcpyAsync(pt->det_pol32, pol32.data(), sizeof(float2) * n_det, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * pt->npix, st));
+    CMM_TRY(launch_hit_blocks(pt, nullptr, nullptr, blocks, nullptr));
+    CMM_TRY(launch_mask_from_hits(pt, blocks));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    return CMM_OK;
+  };
+  s = run();
+  dfree(blocks);
+  if (s != CMM_OK) {
+    cmm_pointing_destroy(pt);
+    return s;
+  }
+  *out = pt;
+  return CMM_OK;
+}
+
+int cmm_pointing_mask(cmm_pointing* pt, uint8_t* mask_host, int64_t* n_good) {
+  if (!pt) return fail(CMM_ERR_ARG, "null pointing");
+  CMM_CUDA(cudaSetDevice(pt->ctx->device));
+  if (mask_host) {
+    CMM_CUDA(cudaMemcpyAsync(mask_host, pt->mask, pt->npix, cudaMemcpyDeviceToHost, pt->ctx->stream));
+    CMM_CUDA(cudaStreamSynchronize(pt->ctx->stream));
+  }
+  if (n_good) *n_good = pt->n_good;
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ noise
+int cmm_noise_destroy(cmm_noise* nz) {
+  if (!nz) return CMM_OK;
+  cudaSetDevice(nz->ctx->device);
+  cudaStreamSynchronize(nz->ctx->stream);
+  dfree(nz->coef64);
+  dfree(nz->coef32);
+  dfree(nz->diag);
+  delete nz;
+  return CMM_OK;
+}
+
+int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp, const double* sigma,
+                     const double* fknee, const double* alpha, cmm_noise** out) {
+  if (!ctx || !sigma || !fknee || !alpha || !out) return fail(CMM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (n_det <= 0 || n_samp < 2 || !(f_samp > 0)) return fail(CMM_ERR_ARG, "bad noise sizes");
+  std::vector<double4_32a> c64(n_det);
+  std::vector<float4> c32(n_det);
+  for (int d = 0; d < n_det; ++d) {
+    if (!(sigma[d] > 0) || fknee[d] < 0 || !std::isfinite(alpha[d])) return fail(CMM_ERR_ARG, "bad noise parameter");
+    const double iv = 1.0 / (sigma[d] * sigma[d]);
+    if (fknee[d] == 0.0) {
+      c64[d] = double4_32a{iv, 0.0, 0.0, 1.0};
+    } else {
+      const double sc = f_samp / ((double)n_samp * fknee[d]);
+      c64[d] = double4_32a{iv, alpha[d], -alpha[d] * std::log2(sc), 0.0};
+    }
+    c32[d] = float4{(float)c64[d].x, (float)c64[d].y, (float)c64[d].z, (float)c64[d].w};
+  }
+  CMM_CUDA(cudaSetDevice(ctx->device));
+  cmm_noise* nz = new cmm_noise();
+  nz->ctx = ctx;
+  nz->n_det = n_det;
+  nz->n_t = n_samp;
+  nz->f_samp = f_samp;
+  int s = dalloc(&nz->coef64, sizeof(double4_32a) * n_det);
+  if (s == CMM_OK) s = dalloc(&nz->coef32, sizeof(float4) * n_det);
+  if (s == CMM_OK) s = dalloc(&nz->diag, sizeof(double) * n_det);
+  if (s != CMM_OK) {
+    cmm_noise_destroy(nz);
+    return s;
+  }
+  auto run = [&]() -> int {
+    cudaStream_t st = ctx->stream;
+    CMM_CUDA(cudaMemcpyAsync(nz->coef64, c64.data(), sizeof(double4_32a) * n_det, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemcpyAsync(nz->coef32, c32.data(), sizeof(float4) * n_det, cudaMemcpyHostToDevice, st));
+    k_noise_diag<<<n_det, 256, 0, st>>>(nz->coef64, n_samp, nz->diag);
+    CMM_LAUNCH_CHECK();
+    nz->diag_host.resize(n_det);
+    CMM_CUDA(cudaMemcpyAsync(nz->diag_host.data(), nz->diag, sizeof(double) * n_det, cudaMemcpyDeviceToHost, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    return CMM_OK;
+  };
+  s = run();
+  if (s != CMM_OK) {
+    cmm_noise_destroy(nz);
+    return s;
+  }
+  *out = nz;
+  return CMM_OK;
+}
+
+int cmm_noise_diag(cmm_noise* nz, double* diag_host) {
+  if (!nz || !diag_host) return fail(CMM_ERR_ARG, "null argument");
+  std::memcpy(diag_host, nz->diag_host.data(), sizeof(double) * nz->n_det);
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ operator
+int cmm_op_destroy(cmm_op* op) {
+  if (!op) return CMM_OK;
+  cudaSetDevice(op->ctx->device);
+  cudaStreamSynchronize(op->ctx->stream);
+  dfree(op->spec);
+  dfree(op->gather);
+  dfree(op->acc);
+  dfree(op->tw);
+  dfree(op->tmp_a);
+  dfree(op->tmp_b);
+  dfree(op->sol);
+  dfree(op->sol_state);
+  delete op;
+  return CMM_OK;
+}
+
+int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precision, int32_t det_chunk,
+                  cmm_op** out) {
+  if (!ctx || !pt || !nz || !out) return fail(CMM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (pt->n_det != nz->n_det || pt->n_t != nz->n_t) return fail(CMM_ERR_ARG, "pointing and noise sizes differ");
+  if (precision < CMM_PREC_F64 || precision > CMM_PREC_BF16) return fail(CMM_ERR_ARG, "bad precision");
+  const int64_t n_t = pt->n_t;
+  if (n_t < 32 || n_t > (1LL << 22) || (n_t & (n_t - 1)))
+    return fail(CMM_ERR_UNSUPPORTED, "n_samp must be a power of two in [32, 2^22]");
+  CMM_CUDA(cudaSetDevice(ctx->device));
+  cmm_op* op = new cmm_op();
+  op->ctx = ctx;
+  op->pt = pt;
+  op->nz = nz;
+  op->prec = precision;
+  op->N = n_t / 2;
+  int logN = 0;
+  while ((1LL << logN) < op->N) ++logN;
+  op->logR = logN / 2;
+  op->logC = logN - op->logR;
+  op->R = 1 << op->logR;
+  op->C = 1 << op->logC;
+  const size_t elt = precision == CMM_PREC_F64 ? 16 : (precision == CMM_PREC_BF16 ? 4 : 8);
+  const size_t per_det = elt * (size_t)op->N;
+  int chunk = det_chunk > 0 ? det_chunk : (int)std::max<size_t>(1, (size_t(8) << 30) / per_det);
+  chunk = std::min(chunk, pt->n_det);
+  op->chunk = chunk;
+  const int64_t npix = pt->npix;
+  const int nc = pt->ncomp;
+  op->acc_stride = nc == 1 ? 1 : 4;
+  const size_t gel = precision == CMM_PREC_F64 ? 8 : 4;
+  int s = dalloc(&op->spec, per_det * chunk);
+  if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * npix);
+  if (s == CMM_OK) s = dalloc(&op->acc, sizeof(double) * op->acc_stride * npix);
+  if (s == CMM_OK) s = dalloc(&op->tmp_a, sizeof(double) * nc * npix);
+  if (s == CMM_OK) s = dalloc(&op->tmp_b, sizeof(double) * nc * npix);
+  if (s == CMM_OK) s = op_init_twiddles(op);
+  if (s == CMM_OK) s = op_prepare_kernels(op);
+  if (s != CMM_OK) {
+    cmm_op_destroy(op);
+    return s;
+  }
+  *out = op;
+  return CMM_OK;
+}
+
+static int apply_A_dev(cmm_op* op, const double* m_in, double* m_out) {
+  CMM_TRY(launch_map_to_gather(op, m_in));
+  for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
+    const int nd = std::min(op->chunk, op->pt->n_det - d0);
+    CMM_TRY(launch_apply_chunk(op, d0, nd, nullptr, 0));
+  }
+  return launch_acc_to_map(op, m_out);
+}
+
+int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out) {
+  if (!op || !m_in || !m_out) return fail(CMM_ERR_ARG, "null argument");
+  if (m_in == m_out) return fail(CMM_ERR_ARG, "m_in and m_out must not alias");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  return apply_A_dev(op, m_in, m_out);
+}
+
+int cmm_profile_apply(cmm_op* op, const double* m_in, double* m_out, int32_t reps, double* ms_host) {
+  if (!op || !m_in || !m_out || !ms_host || reps <= 0) return fail(CMM_ERR_ARG, "bad argument");
+  if (m_in == m_out) return fail(CMM_ERR_ARG, "m_in and m_out must not alias");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = op->ctx->stream;
+  const int nchunk = (op->pt->n_det + op->chunk - 1) / op->chunk;
+  const int nev = 2 + reps * (1 + 3 * nchunk + 1);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  for (auto& e : ev) CMM_CUDA(cudaEventCreate(&e));
+  int s = [&]() -> int {
+    int k = 0;
+    CMM_CUDA(cudaEventRecord(ev[k++], st));
+    for (int r = 0; r < reps; ++r) {
+      CMM_TRY(launch_map_to_gather(op, m_in));
+      CMM_CUDA(cudaEventRecord(ev[k++], st));
+      for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
+        const int nd = std::min(op->chunk, op->pt->n_det - d0);
+        for (int pass = 0; pass < 3; ++pass) {
+          CMM_TRY(launch_apply_chunk(op, d0, nd, nullptr, 0, pass));
+          CMM_CUDA(cudaEventRecord(ev[k++], st));
+        }
+      }
+      CMM_TRY(launch_acc_to_map(op, m_out));
+      CMM_CUDA(cudaEventRecord(ev[k++], st));
+    }
+    CMM_CUDA(cudaEventRecord(ev[k++], st));
+    CMM_CUDA(cudaEventSynchronize(ev[k - 1]));
+    double acc[5] = {0, 0, 0, 0, 0};
+    float t = 0;
+    k = 1;
+    for (int r = 0; r < reps; ++r) {
+      CMM_CUDA(cudaEventElapsedTime(&t, ev[k - 1], ev[k]));
+      acc[3] += t;  // gather copy + accumulator clear
+      ++k;
+      for (int c = 0; c < nchunk; ++c)
+        for (int pass = 0; pass < 3; ++pass) {
+          CMM_CUDA(cudaEventElapsedTime(&t, ev[k - 1], ev[k]));
+          acc[pass] += t;
+          ++k;
+        }
+      CMM_CUDA(cudaEventElapsedTime(&t, ev[k - 1], ev[k]));
+      acc[3] += t;
+      ++k;
+    }
+    CMM_CUDA(cudaEventElapsedTime(&t, ev[0], ev[k]));
+    acc[4] = t;
+    for (int i = 0; i < 3; ++i) ms_host[i] = acc[i] / (reps * nchunk);
+    ms_host[3] = acc[3] / reps;
+    ms_host[4] = acc[4] / reps;
+    return CMM_OK;
+  }();
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return s;
+}
+
+int cmm_apply_A_host(cmm_op* op, const double* m_in_host, double* m_out_host) {
+  if (!op || !m_in_host || !m_out_host) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const size_t bytes = sizeof(double) * op->pt->ncomp * op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  CMM_CUDA(cudaMemcpyAsync(op->tmp_a, m_in_host, bytes, cudaMemcpyHostToDevice, st));
+  CMM_TRY(apply_A_dev(op, op->tmp_a, op->tmp_b));
+  CMM_CUDA(cudaMemcpyAsync(m_out_host, op->tmp_b, bytes, cudaMemcpyDeviceToHost, st));
+  CMM_CUDA(cudaStreamSynchronize(st));
+  return CMM_OK;
+}
+
+int cmm_project(cmm_op* op, const double* m, void* tod, int32_t tod_is_f64) {
+  if (!op || !m || !tod) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  return launch_project(op, m, tod, tod_is_f64);
+}
+
+int cmm_rhs(cmm_op* op, const void* tod, int32_t tod_is_f64, double* b) {
+  if (!op || !tod || !b) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_CUDA(cudaMemsetAsync(op->acc, 0, sizeof(double) * op->acc_stride * op->pt->npix, op->ctx->stream));
+  for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
+    const int nd = std::min(op->chunk, op->pt->n_det - d0);
+    CMM_TRY(launch_apply_chunk(op, d0, nd, tod, tod_is_f64));
+  }
+  return launch_acc_to_map(op, b);
+}
+
+int cmm_dot(cmm_op* op, const double* x, const double* y, int64_t n, double* result_host) {
+  if (!op || !x || !y || !result_host || n < 0) return fail(CMM_ERR_ARG, "bad argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  cmm_ctx* c = op->ctx;
+  CMM_TRY(launch_dot(x, y, n, c->d_partial, c->d_scalar, nullptr, c->stream));
+  CMM_CUDA(cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CMM_CUDA(cudaStreamSynchronize(c->stream));
+  *result_host = c->h_scalar[0];
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ preconditioners
+int cmm_precon_destroy(cmm_precon* pc) {
+  if (!pc) return CMM_OK;
+  cudaSetDevice(pc->op->ctx->device);
+  cudaStreamSynchronize(pc->op->ctx->stream);
+  dfree(pc->inv);
+  dfree(pc->sig);
+  dfree(pc->sig_inv);
+  dfree(pc->hinv);
+  dfree(pc->planes);
+  dfree(pc->tmp);
+  dfree(pc->plan.tw);
+  delete pc;
+  return CMM_OK;
+}
+
+static int64_t pick_reference(const std::vector<uint8_t>& mask, int ny, int nx) {
+  const int64_t p0 = (int64_t)(ny / 2) * nx + nx / 2;
+  if (mask[p0]) return p0;
+  int64_t best = -1;
+  long long bd = -1;
+  for (int64_t p = 0; p < (int64_t)mask.size(); ++p) {
+    if (!mask[p]) continue;
+    const long long dy = p / nx - ny / 2, dx = p % nx - nx / 2;
+    const long long d2 = dy * dy + dx * dx;
+    if (best < 0 || d2 < bd) {
+      best = p;
+      bd = d2;
+    }
+  }
+  return best;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
+  cmm_op* op = pc->op;
+  cmm_pointing* pt = op->pt;
+  cudaStream_t st = op->ctx->stream;
+  const int nc = pt->ncomp;
+  const int64_t npix = pt->npix;
+  const int nb = nc == 1 ? 1 : 6;
+  CMM_TRY(fft2_plan_init<T>(pc->plan, pt->ny, pt->nx));
+  double* blocks = nullptr;
+  double* rows = nullptr;
+  void* qplanes = nullptr;
+  unsigned long long* scratch = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    dfree(blocks);
+    dfree(rows);
+    dfree(qplanes);
+    dfree(scratch);
+  };
+  auto run = [&]() -> int {
+    CMM_TRY(dalloc(&blocks, sizeof(double) * nb * npix));
+    CMM_TRY(dalloc(&rows, sizeof(double) * nc * nc * npix));
+    CMM_TRY(dalloc(&qplanes, sizeof(V2<T>) * nc * nc * npix));
+    CMM_TRY(dalloc(&scratch, sizeof(unsigned long long) * 2));
+    CMM_TRY(dalloc(&pc->sig, sizeof(double) * nb * npix));
+    CMM_TRY(dalloc(&pc->sig_inv, sizeof(double) * nb * npix));
+    CMM_TRY(dalloc(&pc->hinv, sizeof(double) * (nc == 1 ? 1 : 9) * npix));
+    CMM_TRY(dalloc(&pc->planes, sizeof(V2<T>) * nc * npix));
+    CMM_TRY(dalloc(&pc->tmp, sizeof(double) * nc * npix));
+    // Eq. 7: Sigma^T Sigma = binned blocks
+    CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * npix, st));
+    CMM_TRY(launch_hit_blocks(pt, op->nz->diag, pt->mask, blocks, nullptr));
+    CMM_TRY(launch_block_sqrt(nc, npix, blocks, pt->mask, pc->sig, pc->sig_inv, st));
+    // reference pixel
+    std::vector<uint8_t> mask(npix);
+    CMM_CUDA(cudaMemcpyAsync(mask.data(), pt->mask, npix, cudaMemcpyDeviceToHost, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    int64_t ref = (o && o->ref_pixel >= 0) ? o->ref_pixel : pick_reference(mask, pt->ny, pt->nx);
+    if (ref < 0 || ref >= npix || !mask[ref]) return fail(CMM_ERR_ARG, "no usable reference pixel");
+    pc->ref = ref;
+    // Eq. 6: rows A e_{ref, gamma}
+    for (int g = 0; g < nc; ++g) {
+      CMM_CUDA(cudaMemsetAsync(op->tmp_a, 0, sizeof(double) * nc * npix, st));
+      k_set_unit<<<1, 1, 0, st>>>(op->tmp_a, (long long)g * npix + ref);
+      CMM_LAUNCH_CHECK();
+      CMM_TRY(apply_A_dev(op, op->tmp_a, rows + (size_t)g * nc * npix));
+    }
+    // Eq. 13 + symmetrisation + Gaussian taper, then Eq. 11: H = conj(F q)
+    double taper = (o && o->taper_sigma_px > 0 && std::isfinite(o->taper_sigma_px)) ? o->taper_sigma_px : 0.0;
+    pc->taper = taper;
+    CMM_TRY(launch_circ_q<T>(nc, rows, pc->sig_inv, (int)ref, pt->ny, pt->nx, taper, (V2<T>*)qplanes, st));
+    CMM_TRY(fft2<T>(pc->plan, (V2<T>*)qplanes, nc * nc, -1, nullptr, st));
+    const double eps = (o && o->pd_eps > 0) ? o->pd_eps : 1e-6;
+    CMM_TRY(launch_mode_inverse<T>(nc, (const V2<T>*)qplanes, npix, eps, pc->hinv, scratch, st));
+    unsigned long long h[2];
+    CMM_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    pc->n_clamped = (int64_t)(h[1] / 2);
+    return CMM_OK;
+  };
+  int s = run();
+  cleanup();
+  return s;
+}
+
+extern "C" {
+
+int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm_precon** out) {
+  if (!op || !out) return fail(CMM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (kind < CMM_PRECON_BINNED || kind > CMM_PRECON_IDENTITY) return fail(CMM_ERR_ARG, "bad preconditioner kind");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  cmm_precon* pc = new cmm_precon();
+  pc->op = op;
+  pc->kind = kind;
+  cmm_pointing* pt = op->pt;
+  const int nb = pt->ncomp == 1 ? 1 : 6;
+  cudaStream_t st = op->ctx->stream;
+  int s = CMM_OK;
+  if (kind == CMM_PRECON_BINNED || kind == CMM_PRECON_JACOBI) {
+    double* blocks = nullptr;
+    s = dalloc(&blocks, sizeof(double) * nb * pt->npix);
+    if (s == CMM_OK) s = dalloc(&pc->inv, sizeof(double) * nb * pt->npix);
+    if (s == CMM_OK) {
+      auto run = [&]() -> int {
+        CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * pt->npix, st));
+        CMM_TRY(launch_hit_blocks(pt, kind == CMM_PRECON_BINNED ? op->nz->diag : nullptr, pt->mask, blocks, nullptr));
+        CMM_TRY(launch_block_inverse(pt->ncomp, pt->npix, blocks, pt->mask, pc->inv, st));
+        CMM_CUDA(cudaStreamSynchronize(st));
+        return CMM_OK;
+      };
+      s = run();
+    }
+    dfree(blocks);
+  } else if (kind == CMM_PRECON_CIRCULANT) {
+    s = op->prec == CMM_PREC_F64 ? circulant_build<double>(pc, opts) : circulant_build<float>(pc, opts);
+  }
+  if (s != CMM_OK) {
+    cmm_precon_destroy(pc);
+    return s;
+  }
+  *out = pc;
+  return CMM_OK;
+}
+
+}  // extern "C"
+
+// z = M r; when `partial` is given, also the per-block partials of r^T z.
+template <typename T>
+static int circulant_apply(cmm_precon* pc, const double* r, double* z, double* partial, const int* done) {
+  cmm_op* op = pc->op;
+  const int nc = op->pt->ncomp;
+  const int64_t npix = op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  CMM_TRY(launch_block_apply_dot(nc, npix, pc->sig_inv, r, pc->tmp, nullptr, nullptr, done, st));
+  CMM_TRY(launch_real_to_planes<T>(pc->tmp, (V2<T>*)pc->planes, nc * npix, done, st));
+  CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, -1, done, st));
+  CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv, npix, done, st));
+  CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, 1, done, st));
+  CMM_TRY(launch_planes_to_real<T>((const V2<T>*)pc->planes, pc->tmp, nc * npix, 1.0 / (double)npix, done, st));
+  return launch_block_apply_dot(nc, npix, pc->sig_inv, pc->tmp, z, r, partial, done, st);
+}
+
+extern "C" {
+
+static int precon_apply_dev(cmm_precon* pc, const double* r, double* z, double* partial, const int* done) {
+  cmm_op* op = pc->op;
+  const int nc = op->pt->ncomp;
+  const int64_t npix = op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  switch (pc->kind) {
+    case CMM_PRECON_BINNED:
+    case CMM_PRECON_JACOBI:
+      return launch_block_apply_dot(nc, npix, pc->inv, r, z, r, partial, done, st);
+    case CMM_PRECON_CIRCULANT:
+      return op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, partial, done)
+                                      : circulant_apply<float>(pc, r, z, partial, done);
+    default:
+      CMM_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * nc * npix, cudaMemcpyDeviceToDevice, st));
+      if (partial) CMM_TRY(launch_dot_partial(r, z, nc * npix, partial, done, st));
+      return CMM_OK;
+  }
+}
+
+int cmm_precon_apply(cmm_precon* pc, const double* r, double* z) {
+  if (!pc || !r || !z) return fail(CMM_ERR_ARG, "null argument");
+  if (r == z) return fail(CMM_ERR_ARG, "r and z must not alias");
+  CMM_CUDA(cudaSetDevice(pc->op->ctx->device));
+  return precon_apply_dev(pc, r, z, nullptr, nullptr);
+}
+
+int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped) {
+  if (!pc || !n_clamped) return fail(CMM_ERR_ARG, "null argument");
+  *n_clamped = pc->n_clamped;
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ solver
+static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, double* r, double* z, double* p, double* q,
+                           SolverDev* dst, double* p1, double* hist, double* anorm) {
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  const int* done = &dst->done;
+  CMM_TRY(apply_A_dev(op, p, q));
+  CMM_TRY(launch_dot_partial(p, q, n, p1, done, st));
+  CMM_TRY(launch_solver_alpha(dst, p1, anorm, st));
+  CMM_TRY(launch_update_xr(x, r, p, q, n, dst, p1, st));
+  CMM_TRY(launch_solver_check(dst, p1, hist, st));
+  CMM_TRY(precon_apply_dev(pc, r, z, p1, done));
+  CMM_TRY(launch_solver_beta(dst, p1, st));
+  CMM_TRY(launch_update_p(p, z, n, dst, st));
+  return CMM_OK;
+}
+
+int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_solve_opts* opts,
+              double* resid_hist, double* anorm_terms, cmm_solve_info* info) {
+  if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
+  if (pc->op != op) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
+  if (opts->maxit < 0 || !(opts->tol >= 0)) return fail(CMM_ERR_ARG, "bad solve options");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  cmm_ctx* c = op->ctx;
+  cudaStream_t st = c->stream;
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (4 * n + 2 * kRedBlocks)));
+  if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
+  double* r = op->sol;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* p1 = q + n;
+  double* p2 = p1 + kRedBlocks;
+  SolverDev* dst = (SolverDev*)op->sol_state;
+  // ||b||^2
+  double bnorm2 = 0.0;
+  CMM_TRY(cmm_dot(op, b, b, n, &bnorm2));
+  SolverDev h{};
+  h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
+  h.tol = opts->tol;
+  h.maxit = opts->maxit;
+  CMM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  if (!(bnorm2 > 0)) {
+    CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    info->iterations = 0;
+    info->status = CMM_OK;
+    info->rel_resid = 0.0;
+    info->seconds = 0.0;
+    return CMM_OK;
+  }
+  if (opts->x0_given) {
+    CMM_TRY(apply_A_dev(op, x, q));
+    CMM_TRY(launch_copy_sub(r, b, q, n, st));
+  } else {
+    CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CMM_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  CMM_TRY(precon_apply_dev(pc, r, z, p1, nullptr));
+  CMM_TRY(launch_dot_partial(r, r, n, p2, nullptr, st));
+  CMM_TRY(launch_solver_init(dst, p1, p2, resid_hist, st));
+  CMM_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  const int per = std::max(1, opts->check_every);
+  op->done = &dst->done;
+  cudaGraphExec_t exec = nullptr;
+  int status = CMM_OK;
+  if (opts->use_graph) {
+    cudaGraph_t graph = nullptr;
+    status = [&]() -> int {
+      CMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int s2 = CMM_OK;
+      for (int i = 0; i < per && s2 == CMM_OK; ++i) s2 = solve_iteration(op, pc, x, r, z, p, q, dst, p1, resid_hist, anorm_terms);
+      cudaError_t e = cudaStreamEndCapture(st, &graph);
+      if (s2 != CMM_OK) return s2;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+      CMM_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      return CMM_OK;
+    }();
+    if (graph) cudaGraphDestroy(graph);
+  }
+  SolverDev* hs = (SolverDev*)c->h_scalar;
+  int launched = 0;
+  while (status == CMM_OK) {
+    if (exec) {
+      cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+        break;
+      }
+    } else {
+      for (int i = 0; i < per && status == CMM_OK; ++i)
+        status = solve_iteration(op, pc, x, r, z, p, q, dst, p1, resid_hist, anorm_terms);
+      if (status != CMM_OK) break;
+    }
+    launched += per;
+    cudaError_t e = cudaMemcpyAsync(hs, dst, sizeof(SolverDev), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "solver state readback", __FILE__, __LINE__);
+      break;
+    }
+    if (hs->done) break;
+    if (launched > opts->maxit + per) break;
+  }
+  op->done = nullptr;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (status != CMM_OK) return status;
+  info->iterations = hs->iter;
+  info->status = hs->status;
+  info->rel_resid = hs->rel;
+  info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return CMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Internal definitions shared by the CUDA translation units of the map-maker.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cmm.h"
+
+namespace cmm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CMM_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::cmm::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CMM_LAUNCH_CHECK() CMM_CUDA(cudaGetLastError())
+
+#define CMM_TRY(call)            \
+  do {                           \
+    int s_ = (call);             \
+    if (s_ != CMM_OK) return s_; \
+  } while (0)
+
+// ------------------------------------------------------------------ vector types
+template <typename T> struct V2t;
+template <> struct V2t<float> { using t = float2; };
+template <> struct V2t<double> { using t = double2; };
+template <typename T> using V2 = typename V2t<T>::t;
+
+template <typename T> struct V4t;
+template <> struct V4t<float> { using t = float4; };
+template <> struct V4t<double> { using t = double4_32a; };
+template <typename T> using V4 = typename V4t<T>::t;
+
+template <typename V>
+__host__ __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename V>
+__host__ __device__ __forceinline__ V cmulc(V a, V b) {  // a * conj(b)
+  return V{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename V>
+__host__ __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V>
+__host__ __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V>
+__host__ __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
+
+// ------------------------------------------------------------------ handles
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace cmm
+
+struct cmm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double* d_partial = nullptr;   // reduction partials [kRedBlocks]
+  double* d_scalar = nullptr;    // small scalar scratch [16]
+  double* h_scalar = nullptr;    // pinned host mirror [16]
+};
+
+struct cmm_pointing {
+  cmm_ctx* ctx = nullptr;
+  int ny = 0, nx = 0, ncomp = 0, periodic = 0;
+  int n_det = 0;
+  int64_t n_t = 0, npix = 0, n_good = 0;
+  int4* bore = nullptr;        // [n_t] (bx, by, cphi, sphi)
+  int2* det_off = nullptr;     // [n_det] (dx, dy)
+  double2* det_pol64 = nullptr;  // [n_det] (cos 2psi, sin 2psi)
+  float2* det_pol32 = nullptr;
+  uint8_t* mask = nullptr;     // [npix]
+};
+
+struct cmm_noise {
+  cmm_ctx* ctx = nullptr;
+  int n_det = 0;
+  int64_t n_t = 0;
+  double f_samp = 0;
+  // per detector (1/sigma^2, alpha, -alpha*log2(f_samp/(n_t*fknee)), white ? 1 : 0)
+  double4_32a* coef64 = nullptr;
+  float4* coef32 = nullptr;
+  double* diag = nullptr;      // [n_det] diag(N^-1)
+  std::vector<double> diag_host;
+};
+
+struct cmm_op {
+  cmm_ctx* ctx = nullptr;
+  cmm_pointing* pt = nullptr;
+  cmm_noise* nz = nullptr;
+  int prec = CMM_PREC_F32;
+  int64_t N = 0;               // complex length n_t / 2
+  int R = 0, C = 0, logR = 0, logC = 0;
+  int chunk = 0;               // detectors per pass through `spec`
+  void* spec = nullptr;        // [chunk][N] complex intermediate
+  void* gather = nullptr;      // [npix] map copy for the projection gather
+  double* acc = nullptr;       // [npix][acc_stride] FP64 accumulator of P^T
+  int acc_stride = 0;
+  void* tw = nullptr;          // twiddle tables in the op's compute type
+  double* tmp_a = nullptr;     // [ncomp*npix] device temporaries
+  double* tmp_b = nullptr;
+  const int* done = nullptr;   // solver stop flag seen by every kernel (nullptr: none)
+  double* sol = nullptr;       // PCG vectors r, z, p, q and reduction partials
+  void* sol_state = nullptr;   // PCG scalars (SolverDev)
+};
+
+namespace cmm {
+
+constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
+
+// twiddle table offsets inside cmm_op::tw (in elements of V2<T>)
+struct TwLayout {
+  int64_t R_off, C_off, Nlo_off, N2_off, C2_off, total;
+};
+inline TwLayout tw_layout(int R, int C) {
+  TwLayout l;
+  l.R_off = 0;            // w_R^e, e < R
+  l.C_off = R;            // w_C^e, e < C
+  l.Nlo_off = R + C;      // w_N^e, e < C
+  l.N2_off = R + 2 * C;   // w_{2N}^e, e < R
+  l.C2_off = 2 * R + 2 * C;  // w_{2C}^e, e < C
+  l.total = 2 * R + 3 * C;
+  return l;
+}
+
+// ---- launchers implemented in tod.cu
+int launch_map_to_gather(cmm_op* op, const double* m);
+int launch_acc_to_map(cmm_op* op, double* out);
+int launch_apply_chunk(cmm_op* op, int d0, int nd, const void* tod, int tod_is_f64, int pass = -1);
+int launch_project(cmm_op* op, const double* m, void* tod, int tod_is_f64);
+int launch_hit_blocks(cmm_pointing* pt, const double* det_weight, const uint8_t* mask,
+                      double* blocks, const int* done);
+int op_init_twiddles(cmm_op* op);
+int op_prepare_kernels(cmm_op* op);
+
+// ---- launchers implemented in map.cu
+int launch_mask_from_hits(cmm_pointing* pt, const double* blocks);
+int launch_block_inverse(int ncomp, int64_t npix, const double* blocks, const uint8_t* mask,
+                         double* inv, cudaStream_t s);
+int launch_block_sqrt(int ncomp, int64_t npix, const double* blocks, const uint8_t* mask,
+                      double* sig, double* sig_inv, cudaStream_t s);
+int launch_block_apply(int ncomp, int64_t npix, const double* blocks, const double* x,
+                       double* y, const int* done, cudaStream_t s);
+int launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out,
+               const int* done, cudaStream_t s);
+
+}  // namespace cmm

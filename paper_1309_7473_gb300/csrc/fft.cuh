@@ -1,0 +1,224 @@
+// Shared-memory FFT engines.
+//
+// * Power-of-two lengths (time-ordered data): Stockham auto-sort radix-2/4/8/16
+//   passes; each butterfly is a small DFT held in registers (iterative radix-2
+//   decimation in time with constant twiddles), passes ping-pong between two
+//   shared-memory buffers.
+// * 2/3/5-smooth lengths (map FFTs): the same Stockham schedule with radices
+//   2, 3, 4, 5 and table twiddles.
+//
+// A Stockham pass of radix R over a length-L sequence, after passes whose radices
+// multiply to p, takes for butterfly i (0 <= i < L/R, k = i mod p) the inputs
+// x_m = in[i + m L/R], multiplies x_m by w_{pR}^{m k}, forms the R-point DFT y and
+// writes y_q to out[(i - k) R + k + q p]; after the last pass the output is in
+// natural order.  w_L = exp(SIGN * 2 pi i / L), SIGN = -1 forward, +1 inverse.
+#pragma once
+
+#include "common.cuh"
+
+namespace cmm {
+
+// cos(2 pi k / 16) for integer k
+__host__ __device__ constexpr double cos16(int k) {
+  switch (k & 15) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128675613;
+    case 2: return 0.70710678118654752440;
+    case 3: return 0.38268343236508977173;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977173;
+    case 6: return -0.70710678118654752440;
+    case 7: return -0.92387953251128675613;
+    case 8: return -1.0;
+    case 9: return -0.92387953251128675613;
+    case 10: return -0.70710678118654752440;
+    case 11: return -0.38268343236508977173;
+    case 12: return 0.0;
+    case 13: return 0.38268343236508977173;
+    case 14: return 0.70710678118654752440;
+    default: return 0.92387953251128675613;
+  }
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k + 12); }
+
+// v * exp(SIGN * 2 pi i m / 16), m known at compile time after unrolling
+template <typename T, int SIGN>
+__device__ __forceinline__ V2<T> rot16(V2<T> v, int m) {
+  m &= 15;
+  if (m == 0) return v;
+  if (m == 8) return V2<T>{-v.x, -v.y};
+  if (m == 4) return SIGN < 0 ? V2<T>{v.y, -v.x} : V2<T>{-v.y, v.x};
+  if (m == 12) return SIGN < 0 ? V2<T>{-v.y, v.x} : V2<T>{v.y, -v.x};
+  const T c = (T)cos16(m);
+  const T s = (T)(SIGN * sin16(m));
+  return V2<T>{v.x * c - v.y * s, v.x * s + v.y * c};
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// In-register DFT of size R = 2^LR: x_q <- sum_j x_j w_R^{j q}
+template <typename T, int LR, int SIGN>
+__device__ __forceinline__ void dft_reg(V2<T>* x) {
+  constexpr int R = 1 << LR;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = bitrev(i, LR);
+    if (i < j) {
+      V2<T> t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < R; half *= 2) {
+#pragma unroll
+    for (int start = 0; start < R; start += 2 * half) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const V2<T> t = rot16<T, SIGN>(x[start + j + half], j * (16 / (2 * half)));
+        const V2<T> u = x[start + j];
+        x[start + j] = V2<T>{u.x + t.x, u.y + t.y};
+        x[start + j + half] = V2<T>{u.x - t.x, u.y - t.y};
+      }
+    }
+  }
+}
+
+// One power-of-two Stockham pass of radix 2^LR over `1 << lognseq` sequences of
+// length 2^logL; element e of sequence s sits at buf[s * sstride + e * estride].
+// tw holds w_L^e = exp(-2 pi i e / L), e < L (forward sign; conjugated for SIGN > 0).
+template <typename T, int LR, int SIGN>
+__device__ __forceinline__ void pow2_pass(const V2<T>* __restrict__ in, V2<T>* __restrict__ out,
+                                          int logL, int lp, int lognseq, int sstride, int estride,
+                                          const V2<T>* __restrict__ tw) {
+  constexpr int R = 1 << LR;
+  const int lognbf = logL - LR;
+  const int total = 1 << (lognbf + lognseq);
+  const int p = 1 << lp;
+  const int twsh = logL - lp - LR;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int s, i;
+    if (sstride == 1) {  // sequences interleaved: consecutive threads take consecutive sequences
+      s = t & ((1 << lognseq) - 1);
+      i = t >> lognseq;
+    } else {
+      i = t & ((1 << lognbf) - 1);
+      s = t >> lognbf;
+    }
+    const int k = i & (p - 1);
+    const V2<T>* src = in + s * sstride;
+    V2<T> x[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) x[m] = src[(i + (m << lognbf)) * estride];
+    if (k != 0) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) {
+        V2<T> w = tw[(m * k) << twsh];
+        if (SIGN > 0) w.y = -w.y;
+        x[m] = cmul(x[m], w);
+      }
+    }
+    dft_reg<T, LR, SIGN>(x);
+    const int base = ((i - k) << LR) + k;
+    V2<T>* dst = out + s * sstride;
+#pragma unroll
+    for (int m = 0; m < R; ++m) dst[(base + (m << lp)) * estride] = x[m];
+  }
+}
+
+// Full power-of-two FFT on data in `a` (scratch `b`); returns the buffer that holds
+// the result.  Radices are spread evenly over ceil(logL / 4) passes.
+template <typename T, int SIGN>
+__device__ V2<T>* block_fft_pow2(V2<T>* a, V2<T>* b, int logL, int lognseq, int sstride,
+                                 int estride, const V2<T>* __restrict__ tw) {
+  int rem = logL, lp = 0;
+  const int nst = (logL + 3) / 4;
+  for (int st = 0; st < nst; ++st) {
+    const int left = nst - st;
+    const int lr = (rem + left - 1) / left;
+    switch (lr) {
+      case 1: pow2_pass<T, 1, SIGN>(a, b, logL, lp, lognseq, sstride, estride, tw); break;
+      case 2: pow2_pass<T, 2, SIGN>(a, b, logL, lp, lognseq, sstride, estride, tw); break;
+      case 3: pow2_pass<T, 3, SIGN>(a, b, logL, lp, lognseq, sstride, estride, tw); break;
+      default: pow2_pass<T, 4, SIGN>(a, b, logL, lp, lognseq, sstride, estride, tw); break;
+    }
+    __syncthreads();
+    V2<T>* t = a;
+    a = b;
+    b = t;
+    lp += lr;
+    rem -= lr;
+  }
+  return a;
+}
+
+// ------------------------------------------------------------------ mixed radix
+constexpr int kMaxFactors = 24;
+struct MixedPlan {
+  int L;
+  int nrad;
+  int rad[kMaxFactors];
+};
+
+// One mixed-radix Stockham pass (radix R in {2,3,4,5}); tw holds w_L^e, e < L.
+template <typename T>
+__device__ __forceinline__ void mixed_pass(const V2<T>* __restrict__ in, V2<T>* __restrict__ out,
+                                           int L, int R, int p, int nseq, int sstride, int estride,
+                                           const V2<T>* __restrict__ tw, int sign) {
+  const int nbf = L / R;
+  const int total = nbf * nseq;
+  const int step = L / (p * R);
+  const int rstep = L / R;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int s, i;
+    if (sstride == 1) {
+      s = t % nseq;
+      i = t / nseq;
+    } else {
+      i = t % nbf;
+      s = t / nbf;
+    }
+    const int k = i % p;
+    const V2<T>* src = in + s * sstride;
+    V2<T> x[5];
+    for (int m = 0; m < R; ++m) {
+      V2<T> v = src[(i + m * nbf) * estride];
+      V2<T> w = tw[m * k * step];
+      if (sign > 0) w.y = -w.y;
+      x[m] = cmul(v, w);
+    }
+    const int base = (i - k) * R + k;
+    V2<T>* dst = out + s * sstride;
+    for (int q = 0; q < R; ++q) {
+      V2<T> acc = x[0];
+      for (int m = 1; m < R; ++m) {
+        V2<T> w = tw[((m * q) % R) * rstep];
+        if (sign > 0) w.y = -w.y;
+        acc = cadd(acc, cmul(x[m], w));
+      }
+      dst[(base + q * p) * estride] = acc;
+    }
+  }
+}
+
+template <typename T>
+__device__ V2<T>* block_fft_mixed(V2<T>* a, V2<T>* b, const MixedPlan& plan, int nseq, int sstride,
+                                  int estride, const V2<T>* __restrict__ tw, int sign) {
+  int p = 1;
+  for (int st = 0; st < plan.nrad; ++st) {
+    const int R = plan.rad[st];
+    mixed_pass<T>(a, b, plan.L, R, p, nseq, sstride, estride, tw, sign);
+    __syncthreads();
+    V2<T>* t = a;
+    a = b;
+    b = t;
+    p *= R;
+  }
+  return a;
+}
+
+}  // namespace cmm

@@ -1,0 +1,82 @@
+// Declarations shared between map.cu (pixel-space kernels) and api.cu (host runtime).
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace cmm {
+
+// Scalars of one PCG solve, kept in device memory so that an iteration can be
+// replayed as a CUDA graph; every kernel of the loop returns early once `done`.
+struct SolverDev {
+  double rho, pq, alpha, beta, rr, rel, bnorm2, tol;
+  int iter, maxit, done, status;
+};
+
+struct Fft2Plan {
+  int ny = 0, nx = 0;
+  bool f64 = false;
+  MixedPlan py{}, px{};
+  void* tw = nullptr;   // [nx] w_nx^e then [ny] w_ny^e
+};
+
+// Block-wide (256 threads) sum of `v`, stored to partial[blockIdx.x] (fixed order).
+__device__ __forceinline__ void block_sum_store(double v, double* partial) {
+  __shared__ double sh[256];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// Sum of n partials by one block of 256 threads in a fixed order; result in every thread.
+__device__ __forceinline__ double block_sum_all(const double* partial, int n) {
+  __shared__ double sh2[256];
+  __syncthreads();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+  sh2[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh2[threadIdx.x] += sh2[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh2[0];
+  __syncthreads();
+  return r;
+}
+
+int launch_block_apply_dot(int ncomp, int64_t npix, const double* blk, const double* x, double* y,
+                           const double* w, double* partial, const int* done, cudaStream_t s);
+int launch_dot_partial(const double* x, const double* y, int64_t n, double* partial, const int* done,
+                       cudaStream_t s);
+int launch_copy_sub(double* dst, const double* a, const double* b, int64_t n, cudaStream_t s);
+int launch_solver_init(SolverDev* st, const double* prz, const double* prr, double* hist, cudaStream_t s);
+int launch_solver_alpha(SolverDev* st, const double* partial, double* anorm, cudaStream_t s);
+int launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const SolverDev* st,
+                     double* partial, cudaStream_t s);
+int launch_solver_check(SolverDev* st, const double* partial, double* hist, cudaStream_t s);
+int launch_solver_beta(SolverDev* st, const double* partial, cudaStream_t s);
+int launch_update_p(double* p, const double* z, int64_t n, const SolverDev* st, cudaStream_t s);
+
+template <typename T> int fft2_plan_init(Fft2Plan& p, int ny, int nx);
+template <typename T> int fft2(const Fft2Plan& p, V2<T>* data, int nplanes, int sign, const int* done, cudaStream_t s);
+template <typename T>
+int launch_circ_q(int ncomp, const double* rows, const double* sig_inv, int ref, int ny, int nx,
+                  double taper_sigma, V2<T>* planes, cudaStream_t s);
+template <typename T>
+int launch_mode_inverse(int ncomp, const V2<T>* planes, long long npix, double eps, double* hinv,
+                        unsigned long long* scratch2, cudaStream_t s);
+template <typename T>
+int launch_real_to_planes(const double* x, V2<T>* planes, long long n, const int* done, cudaStream_t s);
+template <typename T>
+int launch_planes_to_real(const V2<T>* planes, double* x, long long n, double scale, const int* done,
+                          cudaStream_t s);
+template <typename T>
+int launch_mode_apply(int ncomp, V2<T>* planes, const double* hinv, long long npix, const int* done,
+                      cudaStream_t s);
+
+}  // namespace cmm

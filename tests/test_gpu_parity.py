@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.
+
+Tolerances (norm-wise relative error ||gpu - oracle|| / ||oracle||):
+  FP64 mode: 1e-10 per operator; solutions 1e-5 (the target relative map error).
+  FP32 mode: 1e-5 per operator.  BF16 spectrum storage: 2e-2 per operator.
+Integer work (pixel masks) must agree exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import mapmaker as om
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm as c
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(cmm):
+    return cmm.Context(0)
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+TOL = {0: 1e-10, 1: 1e-5, 2: 2e-2}
+
+
+def small(ncomp=3, periodic=False, cfg=201):
+    if periodic:
+        scan = gen.bccb_scan(8, 16, 1024, diagonal=True, ncomp=ncomp)
+        noise = gen.Noise(np.ones(scan.n_det), np.full(scan.n_det, 30.0), np.full(scan.n_det, 2.0))
+        return scan, noise
+    scan = gen.small_scan(cfg=cfg, ny=24, nx=20, n_t=1 << 12, ncols=4, nrows=2, throw_px=30.0,
+                          ncomp=ncomp)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=cfg)
+    return scan, noise
+
+
+# ---------------------------------------------------------------- pointing / noise setup
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_mask_bit_exact(cmm, ctx, ncomp):
+    for scan in (small(ncomp)[0], gen.config1(ncomp=ncomp)[0],
+                 gen.small_scan(cfg=202, ny=16, nx=16, n_t=1 << 10, ncols=2, nrows=1, ncomp=ncomp)):
+        pt = cmm.Pointing(ctx, scan)
+        mask, n_good = pt.mask()
+        ref = om.pixel_mask(scan)
+        assert np.array_equal(mask, ref)
+        assert n_good == int(ref.sum())
+
+
+def test_noise_diagonal(cmm, ctx):
+    scan, noise = gen.config1()
+    nz = cmm.Noise(ctx, noise, scan.n_t, scan.f_samp)
+    w = om.filter_weights(noise, scan.n_t, scan.f_samp)
+    assert rel(nz.diag(), om.ninv_diagonal(w, scan.n_t)) < 1e-13
+    wn = gen.Noise(np.array([2.0]), np.array([0.0]), np.array([3.5]))
+    assert cmm.Noise(ctx, wn, 1024, 400.0).diag()[0] == pytest.approx(0.25, rel=1e-14)
+
+
+# ---------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("ncomp", [1, 3])
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_apply_A_small(cmm, ctx, prec, ncomp, chunk):
+    scan, noise = small(ncomp)
+    op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=chunk)
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=203)[0]
+    y = host(op.apply(dev(m)))
+    assert rel(y, om.apply_A(oop, m)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_A_periodic(cmm, ctx, prec):
+    scan, noise = small(3, periodic=True)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=204)[0]
+    assert rel(host(op.apply(dev(m))), om.apply_A(oop, m)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_apply_A_config1(cmm, ctx, prec):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=1)
+    y = host(op.apply(dev(m)))
+    ref = om.apply_A(oop, m)
+    assert rel(y, ref) < TOL[prec]
+    # host-buffer entry point gives the same numbers
+    out = np.empty_like(m)
+    cmm.cmm_apply_A_host(op.h, m, out)
+    assert rel(out, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_project_and_rhs(cmm, ctx, prec):
+    scan, noise = small(3)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=205)
+    tod_ref = om.project(oop, m)
+    tod = host(op.project(dev(m), dtype=torch.float64))
+    assert rel(tod, tod_ref) < (1e-13 if prec == 0 else 1e-6)
+    d = tod_ref + gen.noise_tod(noise, scan.n_t, scan.f_samp, cfg=205)
+    for dt in (torch.float64, torch.float32):
+        dd = torch.as_tensor(d, dtype=dt, device="cuda:0")
+        b = host(op.rhs(dd))
+        dref = d if dt == torch.float64 else d.astype(np.float32).astype(np.float64)
+        assert rel(b, om.rhs(oop, dref)) < TOL[prec]
+
+
+def test_A_symmetric_on_gpu(cmm, ctx):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    x, y = gen.random_maps(3, scan.ny, scan.nx, 2, cfg=206)
+    mask = op.pointing.mask()[0].reshape(scan.ny, scan.nx)
+    x[:, ~mask] = 0
+    y[:, ~mask] = 0
+    ax = host(op.apply(dev(x)))
+    ay = host(op.apply(dev(y)))
+    assert np.vdot(x, ay) == pytest.approx(np.vdot(y, ax), rel=1e-12)
+
+
+# ---------------------------------------------------------------- preconditioners
+
+@pytest.mark.parametrize("kind", ["binned", "jacobi"])
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_block_precon(cmm, ctx, kind, ncomp):
+    scan, noise = small(ncomp)
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    k = cmm.PRECON_BINNED if kind == "binned" else cmm.PRECON_JACOBI
+    pc = cmm.Precon(op, k)
+    r = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=207)[0]
+    assert rel(host(pc.apply(dev(r))), om.BlockPrecon(oop, kind)(r)) < 1e-11
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("ncomp", [1, 3])
+@pytest.mark.parametrize("taper", [math.inf, 3.0])
+def test_circulant_precon(cmm, ctx, prec, ncomp, taper):
+    scan, noise = small(ncomp)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=taper if math.isfinite(taper) else 0.0)
+    ref = om.CirculantPrecon(oop, taper_sigma=taper)
+    r = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=208)[0]
+    assert rel(host(pc.apply(dev(r))), ref(r)) < (1e-9 if prec == 0 else 1e-4)
+    if prec == 0:
+        assert pc.clamped() == ref.n_clamped
+
+
+def test_circulant_exact_on_bccb_gpu(cmm, ctx):
+    scan, noise = small(3, periodic=True)
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT)
+    x = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=209)[0]
+    b = op.apply(dev(x))
+    assert rel(host(pc.apply(b)), x) < 1e-10
+    sol, info, _, _ = cmm.solve(op, pc, b, tol=1e-9, maxit=20)
+    assert info.status == 0 and info.iterations == 1
+    assert rel(host(sol), x) < 1e-9
+
+
+# ---------------------------------------------------------------- solves
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_pcg_binned_config1_matches_oracle(cmm, ctx, graph):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=1)
+    d = om.project(oop, m)
+    b_ref = om.rhs(oop, d)
+    b = op.rhs(torch.as_tensor(d, device="cuda:0"))
+    assert rel(host(b), b_ref) < 1e-10
+    pc = cmm.Precon(op, cmm.PRECON_BINNED)
+    x, info, hist, terms = cmm.solve(op, pc, b, tol=1e-10, maxit=400, use_graph=graph, history=True)
+    assert info.status == 0
+    xo, io = om.pcg(lambda v: om.apply_A(oop, v), om.BlockPrecon(oop), b_ref, tol=1e-10, maxit=400)
+    assert rel(host(x), xo) < 1e-5
+    assert abs(info.iterations - io.iterations) <= max(2, 0.1 * io.iterations)
+    h = host(hist)[: info.iterations + 1]
+    np.testing.assert_allclose(h[:10], io.rel_resid[:10], rtol=1e-6)
+    t = host(terms)[: info.iterations]
+    np.testing.assert_allclose(t[:10], io.anorm_terms[:10], rtol=1e-6)
+    # noise-free data: the solution is the input map on unmasked pixels
+    assert rel(host(x), m) < 1e-6
+
+
+def test_pcg_circulant_config1(cmm, ctx):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=1)
+    b_ref = om.apply_A(oop, m)
+    b = dev(b_ref)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+    x, info, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=400)
+    xo, io = om.pcg(lambda v: om.apply_A(oop, v), om.CirculantPrecon(oop, taper_sigma=8.0), b_ref,
+                    tol=1e-6, maxit=400)
+    assert info.status == 0 and io.converged
+    assert abs(info.iterations - io.iterations) <= max(2, 0.1 * io.iterations)
+    assert rel(host(x), xo) < 1e-5
