@@ -18,39 +18,35 @@
 
 namespace cmm {
 
-// cos(2 pi k / 16) for integer k
-__host__ __device__ constexpr double cos16(int k) {
-  switch (k & 15) {
+// cos(2 pi k / 32) for integer k (exact constants of the 32nd roots of unity)
+__host__ __device__ constexpr double cos32(int k) {
+  k &= 31;
+  if (k > 16) k = 32 - k;           // cos is even
+  if (k > 8) return -cos32(16 - k);  // cos(pi - x) = -cos x
+  switch (k) {
     case 0: return 1.0;
-    case 1: return 0.92387953251128675613;
-    case 2: return 0.70710678118654752440;
-    case 3: return 0.38268343236508977173;
-    case 4: return 0.0;
-    case 5: return -0.38268343236508977173;
-    case 6: return -0.70710678118654752440;
-    case 7: return -0.92387953251128675613;
-    case 8: return -1.0;
-    case 9: return -0.92387953251128675613;
-    case 10: return -0.70710678118654752440;
-    case 11: return -0.38268343236508977173;
-    case 12: return 0.0;
-    case 13: return 0.38268343236508977173;
-    case 14: return 0.70710678118654752440;
-    default: return 0.92387953251128675613;
+    case 1: return 0.98078528040323044913;
+    case 2: return 0.92387953251128675613;
+    case 3: return 0.83146961230254523708;
+    case 4: return 0.70710678118654752440;
+    case 5: return 0.55557023301960222474;
+    case 6: return 0.38268343236508977173;
+    case 7: return 0.19509032201612826785;
+    default: return 0.0;
   }
 }
-__host__ __device__ constexpr double sin16(int k) { return cos16(k + 12); }
+__host__ __device__ constexpr double sin32(int k) { return cos32(k - 8); }
 
-// v * exp(SIGN * 2 pi i m / 16), m known at compile time after unrolling
+// v * exp(SIGN * 2 pi i m / 32), m known at compile time after unrolling
 template <typename T, int SIGN>
-__device__ __forceinline__ V2<T> rot16(V2<T> v, int m) {
-  m &= 15;
+__device__ __forceinline__ V2<T> rot32(V2<T> v, int m) {
+  m &= 31;
   if (m == 0) return v;
-  if (m == 8) return V2<T>{-v.x, -v.y};
-  if (m == 4) return SIGN < 0 ? V2<T>{v.y, -v.x} : V2<T>{-v.y, v.x};
-  if (m == 12) return SIGN < 0 ? V2<T>{-v.y, v.x} : V2<T>{v.y, -v.x};
-  const T c = (T)cos16(m);
-  const T s = (T)(SIGN * sin16(m));
+  if (m == 16) return V2<T>{-v.x, -v.y};
+  if (m == 8) return SIGN < 0 ? V2<T>{v.y, -v.x} : V2<T>{-v.y, v.x};
+  if (m == 24) return SIGN < 0 ? V2<T>{-v.y, v.x} : V2<T>{v.y, -v.x};
+  const T c = (T)cos32(m);
+  const T s = (T)(SIGN * sin32(m));
   return V2<T>{v.x * c - v.y * s, v.x * s + v.y * c};
 }
 
@@ -60,7 +56,7 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
   return r;
 }
 
-// In-register DFT of size R = 2^LR: x_q <- sum_j x_j w_R^{j q}
+// In-register DFT of size R = 2^LR (R <= 32): x_q <- sum_j x_j w_R^{j q}
 template <typename T, int LR, int SIGN>
 __device__ __forceinline__ void dft_reg(V2<T>* x) {
   constexpr int R = 1 << LR;
@@ -79,7 +75,7 @@ __device__ __forceinline__ void dft_reg(V2<T>* x) {
     for (int start = 0; start < R; start += 2 * half) {
 #pragma unroll
       for (int j = 0; j < half; ++j) {
-        const V2<T> t = rot16<T, SIGN>(x[start + j + half], j * (16 / (2 * half)));
+        const V2<T> t = rot32<T, SIGN>(x[start + j + half], j * (32 / (2 * half)));
         const V2<T> u = x[start + j];
         x[start + j] = V2<T>{u.x + t.x, u.y + t.y};
         x[start + j + half] = V2<T>{u.x - t.x, u.y - t.y};

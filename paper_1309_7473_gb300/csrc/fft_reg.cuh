@@ -1,0 +1,93 @@
+// Register-resident Stockham FFT used by the fast-path time-ordered-data kernels.
+//
+// A thread owns E elements of one length-L sequence (L = product of the stage
+// radices, every radix divides E): on entry x[e] holds the element at position
+// i + e (L/E), 0 <= i < L/E, and on exit x[e] holds the transform at that same
+// position.  Every stage's butterflies read their inputs from those natural
+// positions (butterfly ib = i + (L/E) u, input m at ib + m L/R is register
+// u + m E/R), so only the outputs of non-final stages go through shared memory:
+// a sequence of S stages costs S - 1 exchanges, each one store and one load per
+// element, instead of a load and a store per stage.  Twiddles w_{PR}^{mk} come
+// from a table of w_L^e, e < L (forward sign, conjugated for SIGN > 0).
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace cmm {
+
+constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+template <int... Rs> struct RadProd;
+template <> struct RadProd<> { static constexpr int value = 1; };
+template <int R, int... Rs> struct RadProd<R, Rs...> { static constexpr int value = R * RadProd<Rs...>::value; };
+
+template <int SIGN, int E, int L, int P, typename Addr, int R, int... REST>
+__device__ __forceinline__ void rfft_stages(float2 (&x)[E], const int i, const float2* __restrict__ tw,
+                                            const Addr& ad) {
+  static_assert(E % R == 0, "every radix must divide the elements per thread");
+  constexpr int NB = E / R;
+  constexpr bool LAST = sizeof...(REST) == 0;
+  if constexpr (!LAST) __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int ib = i + (L / E) * u;
+    const int k = ib & (P - 1);
+    float2 z[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) z[m] = x[u + m * NB];
+    if constexpr (P > 1) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) {
+        float2 w = __ldg(tw + (m * k) * (L / (P * R)));
+        if (SIGN > 0) w.y = -w.y;
+        z[m] = cmul(z[m], w);
+      }
+    }
+    dft_reg<float, clog2(R), SIGN>(z);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[u + q * NB] = z[q];
+    } else {
+      const int base = (ib - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) ad.st(base + q * P, z[q]);
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = ad.ld(i + e * (L / E));
+    rfft_stages<SIGN, E, L, P * R, Addr, REST...>(x, i, tw, ad);
+  }
+}
+
+template <int SIGN, int E, int... RS, typename Addr>
+__device__ __forceinline__ void rfft(float2 (&x)[E], const int i, const float2* __restrict__ tw, const Addr& ad) {
+  rfft_stages<SIGN, E, RadProd<RS...>::value, 1, Addr, RS...>(x, i, tw, ad);
+}
+
+// Shared-memory tile of J = 8 interleaved columns (pass T): position pos of column
+// cl at 8 (pos + pos / 8) + (cl ^ (pos mod 8)): the eight columns of a row share
+// one 64-byte segment (permuted within it), consecutive groups of eight rows shift
+// by half the banks, and a thread reading the eight columns of one row in order
+// meets no bank conflict with its neighbours.
+struct ColAddr {
+  float2* buf;
+  int cl;
+  __device__ __forceinline__ int idx(int pos) const { return ((pos + (pos >> 3)) << 3) + (cl ^ (pos & 7)); }
+  __device__ __forceinline__ void st(int pos, float2 v) const { buf[idx(pos)] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return buf[idx(pos)]; }
+};
+__host__ __device__ constexpr int col_tile_elems(int L) { return 8 * (L + L / 8); }
+
+// One contiguous row (pass F), padded by one element every 2^PS positions.
+template <int PS>
+struct RowAddr {
+  float2* buf;
+  __device__ __forceinline__ int idx(int pos) const { return pos + (pos >> PS); }
+  __device__ __forceinline__ void st(int pos, float2 v) const { buf[idx(pos)] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return buf[idx(pos)]; }
+};
+
+}  // namespace cmm

@@ -233,3 +233,53 @@ def test_pcg_circulant_config1(cmm, ctx):
     assert info.status == 0 and io.converged
     assert abs(info.iterations - io.iterations) <= max(2, 0.1 * io.iterations)
     assert rel(host(x), xo) < 1e-5
+
+
+# ---------------------------------------------------------------- fast-path sizes
+# The FP32 kernels with register-resident FFTs serve n_samp = 2^13 .. 2^21; these
+# cases run them on the ACT-like focal plane at the bench's per-detector sizes
+# (2^20 samples = the launch configuration of the 1024-detector bench) on a few
+# detectors spread over the focal plane, which the oracle evaluates in seconds.
+
+@pytest.mark.parametrize("log_nt", [13, 17, 18, 19, 20])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
+    full, fnoise = gen.config2(n_t=1 << log_nt)
+    dets = np.array([0, 300, 611, 1023, 17])
+    scan, noise = full.subset(dets), fnoise.subset(dets)
+    op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=2)
+    oop = om.make_operator(scan, noise)
+    assert np.array_equal(op.pointing.mask()[0], oop.mask)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=2)
+    y = host(op.apply(dev(m)))
+    assert rel(y, om.apply_A(oop, m)) < TOL[prec]
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_apply_A_fast_small_ragged(cmm, ctx, ncomp):
+    scan = gen.small_scan(cfg=210, ny=30, nx=22, n_t=1 << 13, ncols=5, nrows=1, throw_px=33.0, ncomp=ncomp)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=210)
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=210)[0]
+    ref = om.apply_A(oop, m)
+    for chunk in (0, 2, 3):
+        op = cmm.Operator(ctx, scan, noise, precision=1, det_chunk=chunk)
+        assert rel(host(op.apply(dev(m))), ref) < TOL[1]
+
+
+def test_full_size_symmetry_and_rhs(cmm, ctx):
+    """At the bench's full size (1024 x 2^20, 1200x900): x^T A y = y^T A x, and the
+    right-hand side of noise-free data P m equals A m."""
+    scan, noise = gen.config2()
+    op = cmm.Operator(ctx, scan, noise, precision=1)
+    x, y = gen.random_maps(3, scan.ny, scan.nx, 2, cfg=211)
+    mask = op.pointing.mask()[0].reshape(scan.ny, scan.nx)
+    x[:, ~mask] = 0
+    y[:, ~mask] = 0
+    xd, yd = dev(x), dev(y)
+    ax, ay = host(op.apply(xd)), host(op.apply(yd))
+    assert np.vdot(x, ay) == pytest.approx(np.vdot(y, ax), rel=1e-5)
+    m = dev(gen.sky_map(scan.ny, scan.nx, cfg=2))
+    b1 = host(op.rhs(op.project(m, dtype=torch.float32)))
+    b2 = host(op.apply(m))
+    assert rel(b1, b2) < 1e-5
