@@ -72,6 +72,15 @@ __global__ void k_noise_diag(const double4_32a* __restrict__ coef, long long n_t
   if (threadIdx.x == 0) out[d] = sh[0] / (double)n_t;
 }
 
+// (cos 2phi, sin 2phi) per sample from the Q1.30 rotation, in FP64, stored in FP32.
+__global__ void k_rot2(const int4* __restrict__ bore, long long n, float2* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int4 b = bore[t];
+    const double cf = (double)b.z * 0x1p-30, sf = (double)b.w * 0x1p-30;
+    out[t] = make_float2((float)(cf * cf - sf * sf), (float)(2.0 * cf * sf));
+  }
+}
+
 __global__ void k_set_unit(double* __restrict__ v, long long idx) { v[idx] = 1.0; }
 
 }  // namespace cmm
@@ -150,6 +159,7 @@ int cmm_pointing_destroy(cmm_pointing* pt) {
   dfree(pt->det_off);
   dfree(pt->det_pol64);
   dfree(pt->det_pol32);
+  dfree(pt->rot2);
   dfree(pt->mask);
   delete pt;
   return CMM_OK;
@@ -182,6 +192,7 @@ int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, c
   if (s == CMM_OK) s = dalloc(&pt->det_pol64, sizeof(double2) * n_det);
   if (s == CMM_OK) s = dalloc(&pt->det_pol32, sizeof(float2) * n_det);
   if (s == CMM_OK) s = dalloc(&pt->mask, pt->npix);
+  if (s == CMM_OK) s = dalloc(&pt->rot2, sizeof(float2) * n_samp);
   if (s == CMM_OK) s = dalloc(&blocks, sizeof(double) * nb * pt->npix);
   if (s != CMM_OK) {
     dfree(blocks);
@@ -194,6 +205,8 @@ int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, c
     CMM_CUDA(cudaMemcpyAsync(pt->det_off, det_off, sizeof(int2) * n_det, cudaMemcpyHostToDevice, st));
     CMM_CUDA(cudaMemcpyAsync(pt->det_pol64, det_pol, sizeof(double2) * n_det, cudaMemcpyHostToDevice, st));
     CMM_CUDA(cudaMemcpyAsync(pt->det_pol32, pol32.data(), sizeof(float2) * n_det, cudaMemcpyHostToDevice, st));
+    k_rot2<<<(int)std::min<long long>((n_samp + 255) / 256, 4096), 256, 0, st>>>(pt->bore, n_samp, pt->rot2);
+    CMM_LAUNCH_CHECK();
     CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * pt->npix, st));
     CMM_TRY(launch_hit_blocks(pt, nullptr, nullptr, blocks, nullptr));
     CMM_TRY(launch_mask_from_hits(pt, blocks));

@@ -83,6 +83,7 @@ struct cmm_pointing {
   int2* det_off = nullptr;     // [n_det] (dx, dy)
   double2* det_pol64 = nullptr;  // [n_det] (cos 2psi, sin 2psi)
   float2* det_pol32 = nullptr;
+  float2* rot2 = nullptr;      // [n_t] (cos 2phi, sin 2phi) rounded to FP32 (FP32 response)
   uint8_t* mask = nullptr;     // [npix]
 };
 

@@ -64,6 +64,7 @@ template <> struct Store<float, __nv_bfloat162> {
 struct TodArgs {
   const int4* bore;
   const int2* det_off;
+  const float2* rot2;   // [n_t] (cos 2phi, sin 2phi) in FP32
   const void* pol;      // V2<T> [n_det]
   const void* coef;     // V4<T> [n_det]
   int ny, nx, periodic;
@@ -138,6 +139,7 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   TodArgs a;
   a.bore = pt->bore;
   a.det_off = pt->det_off;
+  a.rot2 = pt->rot2;
   const bool f64 = op->prec == CMM_PREC_F64;
   a.pol = f64 ? (const void*)pt->det_pol64 : (const void*)pt->det_pol32;
   a.coef = f64 ? (const void*)op->nz->coef64 : (const void*)op->nz->coef32;

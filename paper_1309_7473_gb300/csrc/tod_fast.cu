@@ -23,12 +23,42 @@ namespace cmm {
 
 constexpr int kDetsPerCta = 2;
 
+// GB300's FP64 unit also executes int <-> float and float <-> double conversions,
+// at a small fraction of the FP32 rate; the helpers below do them exactly on the
+// integer and FP32 pipes instead.
+
+// Exact float of an integer 0 <= k < 2^23 (IEEE-754 single: 2^23 + k has k as its
+// mantissa).
+__device__ __forceinline__ float small_int_to_float(int k) {
+  return __int_as_float(0x4B000000 | k) - 8388608.0f;
+}
+
+// Exact double of a float, by re-biasing the exponent (bias 127 -> 1023) and
+// widening the mantissa (23 -> 52 bits); zeros and subnormals give +-0.
+__device__ __forceinline__ double float_to_double_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned ed = (e == 0xffu) ? 0x7ffu : e + 896u;
+  const unsigned hi = sign | (ed << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lo = u << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // exp2 / log2 on the special function unit; relative error of w below 1e-6.
-__device__ __forceinline__ float filter_weight_fast(const float4 cf, long long k) {
+__device__ __forceinline__ float filter_weight_fast(const float4 cf, int k) {
   if (cf.w != 0.0f) return cf.x;
-  const float kk = (float)(k == 0 ? 1 : k);
+  const float kk = small_int_to_float(k == 0 ? 1 : k);
   const float e = exp2f(fmaf(-cf.y, __log2f(kk), cf.z));
   return __fdividef(cf.x, 1.0f + e);
+}
+
+// (cos 2a, sin 2a) of sample t, a = psi_d + phi_t, from the FP32 (cos 2phi, sin 2phi)
+__device__ __forceinline__ void response_fast(const TodArgs& a, long long t, const float2 pol, float& c, float& s) {
+  const float2 r2 = __ldg(a.rot2 + t);
+  c = pol.x * r2.x - pol.y * r2.y;
+  s = pol.y * r2.x + pol.x * r2.y;
 }
 
 __device__ __forceinline__ float2 tw_N(const TodArgs& a, const float2* __restrict__ tw, long long e) {
@@ -45,13 +75,14 @@ __device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, 
   if (NC == 1) return __ldg((const float*)a.gather + p);
   const float4 g = __ldg((const float4*)a.gather + p);
   float c, s;
-  sample_response<float>(b, pol, c, s);
+  response_fast(a, t, pol, c, s);
   return g.x + c * g.y + s * g.z;
 }
 
 // ------------------------------------------------------------------ pass T (forward)
 template <int NC, typename S, int... RR>
-__global__ void __launch_bounds__(RadProd<RR...>::value) k_fast_fwd(const TodArgs a, int nd) {
+__global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::value)
+    k_fast_fwd(const TodArgs a, int nd) {
   constexpr int R = RadProd<RR...>::value;
   constexpr int E = 8;
   constexpr int TPC = R / E;
@@ -61,9 +92,6 @@ __global__ void __launch_bounds__(RadProd<RR...>::value) k_fast_fwd(const TodArg
   const int i = threadIdx.x >> 3;
   const int c = (blockIdx.x << 3) + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  float2 t4[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) t4[e] = tw_N(a, tw, (long long)c * (i + e * TPC));
   const ColAddr ad{smf, cl};
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
@@ -82,14 +110,16 @@ __global__ void __launch_bounds__(RadProd<RR...>::value) k_fast_fwd(const TodArg
     rfft<-1, E, RR...>(x, i, tw + a.twl.R_off, ad);
     S* Y = reinterpret_cast<S*>(a.spec) + (long long)dl * a.N;
 #pragma unroll
-    for (int e = 0; e < E; ++e)
-      Store<float, S>::st(Y + ((long long)(i + e * TPC) << a.logC) + c, cmul(x[e], t4[e]));
+    for (int e = 0; e < E; ++e) {
+      const int kr = i + e * TPC;
+      Store<float, S>::st(Y + ((long long)kr << a.logC) + c, cmul(x[e], tw_N(a, tw, (long long)c * kr)));
+    }
   }
 }
 
 // ------------------------------------------------------------------ pass F (filter)
 template <typename S, int E, int... RC>
-__global__ void __launch_bounds__(256) k_fast_filter(const TodArgs a) {
+__global__ void __launch_bounds__(256, 2) k_fast_filter(const TodArgs a) {
   constexpr int C = RadProd<RC...>::value;
   constexpr int TPR = C / E;
   constexpr int ROWS = 256 / TPR;
@@ -144,7 +174,7 @@ __global__ void __launch_bounds__(256) k_fast_filter(const TodArgs a) {
       else if (ra == 0) j2 = (C - kc) & (C - 1);
       else j2 = C - 1 - kc;
       const int i1 = kc + (kc >> PS), i2 = j2 + (j2 >> PS);
-      const long long k = (long long)ra + (long long)a.R * kc;
+      const int k = ra + a.R * kc;   // < N <= 2^20
       const float2 A = r0[i1];
       const float2 B = cconj(r1[i2]);
       const float2 Ev{(A.x + B.x) * 0.5f, (A.y + B.y) * 0.5f};
@@ -152,7 +182,7 @@ __global__ void __launch_bounds__(256) k_fast_filter(const TodArgs a) {
       const float2 O{Dv.y, -Dv.x};
       const float2 W = cmul(wrow, __ldg(tw + a.twl.C2_off + kc));
       const float wk = filter_weight_fast(cf, k);
-      const float wm = filter_weight_fast(cf, a.N - k);
+      const float wm = filter_weight_fast(cf, (int)a.N - k);
       const float ws = 0.5f * (wk + wm), wd = 0.5f * (wk - wm);
       const float2 WO = cmul(W, O);
       const float2 Ep{ws * Ev.x + wd * WO.x, ws * Ev.y + wd * WO.y};
@@ -181,17 +211,18 @@ template <int NC>
 __device__ __forceinline__ void flush_bin(double* acc, int p, float aT, float aQ, float aU) {
   if (p < 0) return;
   if (NC == 1) {
-    atomicAdd(acc + p, (double)aT);
+    atomicAdd(acc + p, float_to_double_exact(aT));
     return;
   }
   double* dst = acc + 4 * (long long)p;
-  atomicAdd(dst + 0, (double)aT);
-  atomicAdd(dst + 1, (double)aQ);
-  atomicAdd(dst + 2, (double)aU);
+  atomicAdd(dst + 0, float_to_double_exact(aT));
+  atomicAdd(dst + 1, float_to_double_exact(aQ));
+  atomicAdd(dst + 2, float_to_double_exact(aU));
 }
 
 template <int NC, typename S, int... RR>
-__global__ void __launch_bounds__(RadProd<RR...>::value) k_fast_inv_bin(const TodArgs a, int nd) {
+__global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::value)
+    k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int R = RadProd<RR...>::value;
   constexpr int E = 8;
   constexpr int TPC = R / E;
@@ -244,7 +275,7 @@ __global__ void __launch_bounds__(RadProd<RR...>::value) k_fast_inv_bin(const To
           aT += u;
           if (NC == 3) {
             float cc, ss;
-            sample_response<float>(b, pol, cc, ss);
+            response_fast(a, t, pol, cc, ss);
             aQ += cc * u;
             aU += ss * u;
           }
@@ -322,8 +353,8 @@ static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
     case 6: return run_F<S, 16, 4, 16>(a, nd, st, attr_only);
     case 7: return run_F<S, 16, 8, 16>(a, nd, st, attr_only);
     case 8: return run_F<S, 16, 16, 16>(a, nd, st, attr_only);
-    case 9: return run_F<S, 32, 16, 32>(a, nd, st, attr_only);
-    default: return run_F<S, 32, 32, 32>(a, nd, st, attr_only);
+    case 9: return run_F<S, 16, 2, 16, 16>(a, nd, st, attr_only);
+    default: return run_F<S, 16, 4, 16, 16>(a, nd, st, attr_only);
   }
 }
 
