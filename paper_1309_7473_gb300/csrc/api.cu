@@ -311,6 +311,7 @@ int cmm_op_destroy(cmm_op* op) {
   dfree(op->spec);
   dfree(op->gather);
   dfree(op->acc);
+  dfree(op->acc32);
   dfree(op->tw);
   dfree(op->tmp_a);
   dfree(op->tmp_b);
@@ -338,8 +339,10 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   op->N = n_t / 2;
   int logN = 0;
   while ((1LL << logN) < op->N) ++logN;
-  op->logR = logN / 2;
-  op->logC = logN - op->logR;
+  if (!fast_path_sizes(logN, precision, &op->logR, &op->logC)) {
+    op->logR = logN / 2;
+    op->logC = logN - op->logR;
+  }
   op->R = 1 << op->logR;
   op->C = 1 << op->logC;
   const size_t elt = precision == CMM_PREC_F64 ? 16 : (precision == CMM_PREC_BF16 ? 4 : 8);
@@ -354,6 +357,8 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   int s = dalloc(&op->spec, per_det * chunk);
   if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * npix);
   if (s == CMM_OK) s = dalloc(&op->acc, sizeof(double) * op->acc_stride * npix);
+  if (s == CMM_OK) s = dalloc(&op->acc32, sizeof(float) * op->acc_stride * npix);
+  if (s == CMM_OK) s = (cudaMemset(op->acc32, 0, sizeof(float) * op->acc_stride * npix) == cudaSuccess) ? CMM_OK : fail(CMM_ERR_CUDA, "memset");
   if (s == CMM_OK) s = dalloc(&op->tmp_a, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = dalloc(&op->tmp_b, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = op_init_twiddles(op);

@@ -110,6 +110,7 @@ struct cmm_op {
   void* spec = nullptr;        // [chunk][N] complex intermediate
   void* gather = nullptr;      // [npix] map copy for the projection gather
   double* acc = nullptr;       // [npix][acc_stride] FP64 accumulator of P^T
+  float* acc32 = nullptr;      // [npix][acc_stride] FP32 partial accumulator (fast path)
   int acc_stride = 0;
   void* tw = nullptr;          // twiddle tables in the op's compute type
   double* tmp_a = nullptr;     // [ncomp*npix] device temporaries
@@ -147,6 +148,7 @@ int launch_hit_blocks(cmm_pointing* pt, const double* det_weight, const uint8_t*
                       double* blocks, const int* done);
 int op_init_twiddles(cmm_op* op);
 int op_prepare_kernels(cmm_op* op);
+bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
 
 // ---- launchers implemented in map.cu
 int launch_mask_from_hits(cmm_pointing* pt, const double* blocks);

@@ -75,6 +75,8 @@ struct TodArgs {
   void* spec;           // S [nd][N]
   const void* gather;   // V4<T> / T [npix]
   double* acc;          // [npix][acc_stride]
+  float* acc32;         // [npix][acc_stride] FP32 partials (fast path)
+  long long npix;
   const void* tod;      // float / double [n_det][n_t]
   int d0;
   const int* done;
@@ -159,6 +161,8 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   a.spec = op->spec;
   a.gather = op->gather;
   a.acc = op->acc;
+  a.acc32 = op->acc32;
+  a.npix = pt->npix;
   a.tod = nullptr;
   a.d0 = d0;
   a.done = op->done;

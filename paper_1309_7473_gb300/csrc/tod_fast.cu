@@ -1,16 +1,23 @@
-// Fast path of A = P^T N^-1 P for FP32 compute (FP32 or BF16 spectrum storage):
-// the same four-step decomposition as tod.cu, with register-resident FFTs.
+// Fast path of A = P^T N^-1 P for FP32 compute (FP32 or BF16 spectrum storage).
 //
-//   k_fast_fwd:     pass T, R-point column FFTs (E = 8 elements per thread, J = 8
-//                   columns per CTA) of samples produced by P on the fly; each CTA
-//                   loops over a block of detectors and keeps the four-step
-//                   twiddles w_N^{c k_r} in registers.
-//   k_fast_filter:  pass F, C-point row FFTs (E = 16 or 32), the real-FFT split with
-//                   the noise filter w_d(f) evaluated with the SFU, inverse row FFTs.
-//   k_fast_inv_bin: pass T', inverse column FFTs, a transpose through shared memory
-//                   so that each thread owns 16 consecutive samples, and P^T with
-//                   runs of equal pixels summed in FP32 before one FP64 atomic per
-//                   Stokes component (partials over at most 16 samples).
+// The complex length N = n_t / 2 is split as N = R C with short columns
+// (R = 64 or 128) and long rows (C = N / R up to 4096):
+//
+//   k_fast_fwd:     pass T.  A CTA holds 32 adjacent columns; thread (lane cl, warp i)
+//                   owns the 16 rows i + e R/16 of column c0 + cl, so every warp
+//                   reads 64 consecutive samples at a time (coalesced boresight and
+//                   gather loads).  P m is produced on the fly, transformed by a
+//                   register-resident R-point FFT and stored times w_N^{c k_r}.
+//   k_fast_filter:  pass F.  Row pairs (k_r, R - k_r) of C points: forward FFT, the
+//                   real-FFT split, the noise filter w_d(f), the merge, inverse FFT.
+//   k_fast_inv_bin: pass T'.  Inverse R-point FFTs; each warp then holds 64
+//                   consecutive filtered samples in lane order, and runs of samples
+//                   that fall in the same pixel are summed by a warp-level segmented
+//                   scan, so that one vector FP32 reduction per run goes to an
+//                   L2-resident partial map.
+//   k_fast_flush:   adds the FP32 partial map into the FP64 accumulator and clears
+//                   it, after every group of at most kFlushDets detectors, so each
+//                   FP32 partial sums a bounded number of samples.
 #include <math.h>
 
 #include <algorithm>
@@ -22,28 +29,17 @@
 namespace cmm {
 
 constexpr int kDetsPerCta = 2;
+constexpr int kFlushDets = 128;
+constexpr int kE = 16;     // elements per thread in the column FFT
+constexpr int kJ = 32;     // columns per CTA (one per lane)
 
-// GB300's FP64 unit also executes int <-> float and float <-> double conversions,
-// at a small fraction of the FP32 rate; the helpers below do them exactly on the
-// integer and FP32 pipes instead.
+// GB300's FP64 unit also executes int <-> float conversions, at a small fraction
+// of the FP32 rate; this helper does the one of the filter exactly on the FP32 pipe.
 
 // Exact float of an integer 0 <= k < 2^23 (IEEE-754 single: 2^23 + k has k as its
 // mantissa).
 __device__ __forceinline__ float small_int_to_float(int k) {
   return __int_as_float(0x4B000000 | k) - 8388608.0f;
-}
-
-// Exact double of a float, by re-biasing the exponent (bias 127 -> 1023) and
-// widening the mantissa (23 -> 52 bits); zeros and subnormals give +-0.
-__device__ __forceinline__ double float_to_double_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned sign = u & 0x80000000u;
-  if (e == 0u) return __hiloint2double((int)sign, 0);
-  const unsigned ed = (e == 0xffu) ? 0x7ffu : e + 896u;
-  const unsigned hi = sign | (ed << 20) | ((u & 0x7fffffu) >> 3);
-  const unsigned lo = u << 29;
-  return __hiloint2double((int)hi, (int)lo);
 }
 
 // exp2 / log2 on the special function unit; relative error of w below 1e-6.
@@ -55,7 +51,8 @@ __device__ __forceinline__ float filter_weight_fast(const float4 cf, int k) {
 }
 
 // (cos 2a, sin 2a) of sample t, a = psi_d + phi_t, from the FP32 (cos 2phi, sin 2phi)
-__device__ __forceinline__ void response_fast(const TodArgs& a, long long t, const float2 pol, float& c, float& s) {
+__device__ __forceinline__ void response_fast(const TodArgs& a, long long t, const float2 pol, float& c,
+                                              float& s) {
   const float2 r2 = __ldg(a.rot2 + t);
   c = pol.x * r2.x - pol.y * r2.y;
   s = pol.y * r2.x + pol.x * r2.y;
@@ -79,20 +76,40 @@ __device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, 
   return g.x + c * g.y + s * g.z;
 }
 
+// 32 interleaved columns: position pos of column cl at 32 pos + cl, so every access
+// of the column FFT puts the 32 lanes of a warp on 32 consecutive elements.
+struct Col32 {
+  float2* buf;
+  int cl;
+  __device__ __forceinline__ void st(int pos, float2 v) const { buf[(pos << 5) + cl] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return buf[(pos << 5) + cl]; }
+};
+
+template <int R> struct ColPlan;
+template <> struct ColPlan<64> {
+  template <int SIGN, typename Addr>
+  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
+    rfft<SIGN, kE, 16, 4>(x, i, tw, ad);
+  }
+};
+template <> struct ColPlan<128> {
+  template <int SIGN, typename Addr>
+  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
+    rfft<SIGN, kE, 16, 8>(x, i, tw, ad);
+  }
+};
+
 // ------------------------------------------------------------------ pass T (forward)
-template <int NC, typename S, int... RR>
-__global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::value)
-    k_fast_fwd(const TodArgs a, int nd) {
-  constexpr int R = RadProd<RR...>::value;
-  constexpr int E = 8;
-  constexpr int TPC = R / E;
+template <int NC, typename S, int R>
+__global__ void __launch_bounds__(2 * R, 384 / R) k_fast_fwd(const TodArgs a, int nd) {
+  constexpr int TPC = R / kE;
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
-  const int cl = threadIdx.x & 7;
-  const int i = threadIdx.x >> 3;
-  const int c = (blockIdx.x << 3) + cl;
+  const int cl = threadIdx.x & 31;
+  const int i = threadIdx.x >> 5;
+  const int c = (blockIdx.x << 5) + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  const ColAddr ad{smf, cl};
+  const Col32 ad{smf, cl};
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
     const int dl = dl0 + dd;
@@ -100,17 +117,21 @@ __global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::
     const int d = a.d0 + dl;
     const int2 off = a.det_off[d];
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
-    float2 x[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
+    // samples into the tile (the previous detector's last reads are fenced first)
+    __syncthreads();
+#pragma unroll 2
+    for (int e = 0; e < kE; ++e) {
       const long long j = (long long)c + ((long long)(i + e * TPC) << a.logC);
-      x[e].x = project_fast<NC>(a, off, pol, 2 * j);
-      x[e].y = project_fast<NC>(a, off, pol, 2 * j + 1);
+      ad.st(i + e * TPC, make_float2(project_fast<NC>(a, off, pol, 2 * j), project_fast<NC>(a, off, pol, 2 * j + 1)));
     }
-    rfft<-1, E, RR...>(x, i, tw + a.twl.R_off, ad);
+    __syncthreads();
+    float2 x[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) x[e] = ad.ld(i + e * TPC);
+    ColPlan<R>::template run<-1>(x, i, tw + a.twl.R_off, ad);
     S* Y = reinterpret_cast<S*>(a.spec) + (long long)dl * a.N;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < kE; ++e) {
       const int kr = i + e * TPC;
       Store<float, S>::st(Y + ((long long)kr << a.logC) + c, cmul(x[e], tw_N(a, tw, (long long)c * kr)));
     }
@@ -118,13 +139,22 @@ __global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::
 }
 
 // ------------------------------------------------------------------ pass F (filter)
+template <int C, int E> struct FilterShape {
+  static constexpr int TPR = C / E;
+  static constexpr int THREADS = 2 * TPR > 256 ? 2 * TPR : 256;
+  static constexpr int ROWS = THREADS / TPR;
+  static constexpr int MINB = THREADS > 256 ? 1 : 2;
+};
+
 template <typename S, int E, int... RC>
-__global__ void __launch_bounds__(256, 2) k_fast_filter(const TodArgs a) {
+__global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS,
+                                  FilterShape<RadProd<RC...>::value, E>::MINB)
+    k_fast_filter(const TodArgs a) {
   constexpr int C = RadProd<RC...>::value;
   constexpr int TPR = C / E;
-  constexpr int ROWS = 256 / TPR;
+  constexpr int ROWS = FilterShape<C, E>::ROWS;
   constexpr int PAIRS = ROWS / 2;
-  constexpr int PS = clog2(E) <= 4 ? 4 : 5;
+  constexpr int PS = clog2(E);
   constexpr int ROWLEN = C + (C >> PS);
   static_assert(ROWS >= 2 && ROWS % 2 == 0, "a CTA holds whole row pairs");
   if (a.done && *a.done) return;
@@ -174,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) k_fast_filter(const TodArgs a) {
       else if (ra == 0) j2 = (C - kc) & (C - 1);
       else j2 = C - 1 - kc;
       const int i1 = kc + (kc >> PS), i2 = j2 + (j2 >> PS);
-      const int k = ra + a.R * kc;   // < N <= 2^20
+      const int k = ra + a.R * kc;   // < N <= 2^19
       const float2 A = r0[i1];
       const float2 B = cconj(r1[i2]);
       const float2 Ev{(A.x + B.x) * 0.5f, (A.y + B.y) * 0.5f};
@@ -207,33 +237,84 @@ __global__ void __launch_bounds__(256, 2) k_fast_filter(const TodArgs a) {
 }
 
 // ------------------------------------------------------------------ pass T' (inverse + P^T)
-template <int NC>
-__device__ __forceinline__ void flush_bin(double* acc, int p, float aT, float aQ, float aU) {
-  if (p < 0) return;
-  if (NC == 1) {
-    atomicAdd(acc + p, float_to_double_exact(aT));
-    return;
-  }
-  double* dst = acc + 4 * (long long)p;
-  atomicAdd(dst + 0, float_to_double_exact(aT));
-  atomicAdd(dst + 1, float_to_double_exact(aQ));
-  atomicAdd(dst + 2, float_to_double_exact(aU));
+
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(0.0f)
+               : "memory");
 }
 
-template <int NC, typename S, int... RR>
-__global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::value)
-    k_fast_inv_bin(const TodArgs a, int nd) {
-  constexpr int R = RadProd<RR...>::value;
-  constexpr int E = 8;
-  constexpr int TPC = R / E;
+// Bins the two samples of every lane of a warp, which hold 64 consecutive samples
+// in lane order (lane l: samples 2l, 2l + 1).  Items with equal pixels that are
+// adjacent in time are summed (in-lane, then across lanes by a segmented suffix
+// scan); the first item of every run issues one reduction.
+template <int NC>
+__device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0, float3 v1) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool two = p1 != p0;
+  if (!two) {
+    v0.x += v1.x;
+    v0.y += v1.y;
+    v0.z += v1.z;
+  }
+  const int g = two ? p1 : p0;                 // pixel of the lane's last item
+  const int fnext = __shfl_down_sync(full, p0, 1);
+  const bool link = lane < 31 && g >= 0 && g == fnext;   // next lane's first item continues my last run
+  const unsigned linkmask = __ballot_sync(full, link);
+  const bool linkprev = lane > 0 && ((linkmask >> (lane - 1)) & 1u);
+  // y_l = A_l + (single_l && link_l ? y_{l+1} : 0), by a segmented suffix scan
+  float3 y = v0;
+  bool cont = !two && link;
+  unsigned contmask = __ballot_sync(full, cont);
+  for (int dist = 1; contmask != 0u && dist < 32; dist <<= 1) {
+    const float yx = __shfl_down_sync(full, y.x, dist);
+    const float yy = __shfl_down_sync(full, y.y, dist);
+    const float yz = __shfl_down_sync(full, y.z, dist);
+    const bool other = lane + dist < 32 && ((contmask >> (lane + dist)) & 1u);
+    if (cont && lane + dist < 32) {
+      y.x += yx;
+      y.y += yy;
+      y.z += yz;
+      cont = other;
+    } else {
+      cont = false;
+    }
+    contmask = __ballot_sync(full, cont);
+  }
+  // carry_l = link_l ? y_{l+1} : 0
+  float3 carry;
+  carry.x = __shfl_down_sync(full, y.x, 1);
+  carry.y = __shfl_down_sync(full, y.y, 1);
+  carry.z = __shfl_down_sync(full, y.z, 1);
+  if (!link) carry = make_float3(0.f, 0.f, 0.f);
+  if (two) {
+    if (!linkprev && p0 >= 0) {
+      if (NC == 1) red_add(acc32 + p0, v0.x);
+      else red_add4(acc32 + 4 * (long long)p0, v0.x, v0.y, v0.z);
+    }
+    if (p1 >= 0) {
+      if (NC == 1) red_add(acc32 + p1, v1.x + carry.x);
+      else red_add4(acc32 + 4 * (long long)p1, v1.x + carry.x, v1.y + carry.y, v1.z + carry.z);
+    }
+  } else if (!linkprev && p0 >= 0) {
+    if (NC == 1) red_add(acc32 + p0, y.x);
+    else red_add4(acc32 + 4 * (long long)p0, y.x, y.y, y.z);
+  }
+}
+
+template <int NC, typename S, int R>
+__global__ void __launch_bounds__(2 * R, 384 / R) k_fast_inv_bin(const TodArgs a, int nd) {
+  constexpr int TPC = R / kE;
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
-  const int cl = threadIdx.x & 7;
-  const int i = threadIdx.x >> 3;
-  const int c0 = blockIdx.x << 3;
-  const int c = c0 + cl;
+  const int cl = threadIdx.x & 31;
+  const int i = threadIdx.x >> 5;
+  const int c = (blockIdx.x << 5) + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  const ColAddr ad{smf, cl};
+  const Col32 ad{smf, cl};
   const float scale = 1.0f / (float)a.N;
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
@@ -241,108 +322,117 @@ __global__ void __launch_bounds__(RadProd<RR...>::value, 1024 / RadProd<RR...>::
     if (dl >= nd) break;
     const int d = a.d0 + dl;
     const S* Y = reinterpret_cast<const S*>(a.spec) + (long long)dl * a.N;
-    float2 x[E];
+    float2 x[kE];
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = Store<float, S>::ld(Y + ((long long)(i + e * TPC) << a.logC) + c);
-    rfft<1, E, RR...>(x, i, tw + a.twl.R_off, ad);
+    for (int e = 0; e < kE; ++e) x[e] = Store<float, S>::ld(Y + ((long long)(i + e * TPC) << a.logC) + c);
+    __syncthreads();   // the previous detector's binning reads of the tile are done
+    ColPlan<R>::template run<1>(x, i, tw + a.twl.R_off, ad);
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) ad.st(i + e * TPC, make_float2(x[e].x * scale, x[e].y * scale));
+    for (int e = 0; e < kE; ++e) ad.st(i + e * TPC, x[e]);
     __syncthreads();
-    // thread r owns time row r: samples 2 (c0 + C r) .. + 15
-    const int r = threadIdx.x;
     const int2 off = a.det_off[d];
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
-    const long long t0 = 2 * ((long long)c0 + ((long long)r << a.logC));
-    const int rbase = (r + (r >> 3)) << 3;
-    int cur = -1;
-    float aT = 0.f, aQ = 0.f, aU = 0.f;
-#pragma unroll
-    for (int cq = 0; cq < 8; ++cq) {
-      const float2 v = smf[rbase + (cq ^ (r & 7))];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const long long t = t0 + 2 * cq + h;
-        const float u = h ? v.y : v.x;
-        const int4 b = __ldg(a.bore + t);
-        const int p = sample_pixel(b, off, a.ny, a.nx, a.periodic);
-        if (p != cur) {
-          flush_bin<NC>(a.acc, cur, aT, aQ, aU);
-          cur = p;
-          aT = aQ = aU = 0.f;
-        }
-        if (p >= 0) {
-          aT += u;
-          if (NC == 3) {
-            float cc, ss;
-            response_fast(a, t, pol, cc, ss);
-            aQ += cc * u;
-            aU += ss * u;
-          }
-        }
+#pragma unroll 2
+    for (int e = 0; e < kE; ++e) {
+      const long long j = (long long)c + ((long long)(i + e * TPC) << a.logC);
+      const long long t0 = 2 * j;
+      const int4 b0 = __ldg(a.bore + t0);
+      const int4 b1 = __ldg(a.bore + t0 + 1);
+      const int p0 = sample_pixel(b0, off, a.ny, a.nx, a.periodic);
+      const int p1 = sample_pixel(b1, off, a.ny, a.nx, a.periodic);
+      const float2 xe = ad.ld(i + e * TPC);
+      const float u0 = xe.x * scale, u1 = xe.y * scale;
+      float3 v0 = make_float3(u0, 0.f, 0.f), v1 = make_float3(u1, 0.f, 0.f);
+      if (NC == 3) {
+        float c0, s0, c1, s1;
+        response_fast(a, t0, pol, c0, s0);
+        response_fast(a, t0 + 1, pol, c1, s1);
+        v0.y = c0 * u0;
+        v0.z = s0 * u0;
+        v1.y = c1 * u1;
+        v1.z = s1 * u1;
+      }
+      warp_bin<NC>(a.acc32, p0, p1, v0, v1);
+    }
+  }
+}
+
+template <int NC>
+__global__ void k_fast_flush(float* __restrict__ acc32, double* __restrict__ acc, long long npix,
+                             const int* done) {
+  if (done && *done) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (NC == 1) {
+      const float v = acc32[p];
+      if (v != 0.0f) {
+        acc[p] += (double)v;
+        acc32[p] = 0.0f;
+      }
+    } else {
+      const float4 v = reinterpret_cast<float4*>(acc32)[p];
+      if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f) {
+        double* o = acc + 4 * p;
+        o[0] += (double)v.x;
+        o[1] += (double)v.y;
+        o[2] += (double)v.z;
+        reinterpret_cast<float4*>(acc32)[p] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    flush_bin<NC>(a.acc, cur, aT, aQ, aU);
   }
 }
 
 // ------------------------------------------------------------------ dispatch
+
+// Fast-path split of N = 2^logN: R = 64 below 2^16, R = 128 from 2^16 to 2^19.
+bool fast_path_sizes(int logN, int prec, int* logR, int* logC) {
+  if (prec == CMM_PREC_F64 || logN < 12 || logN > 19) return false;
+  *logR = logN < 16 ? 6 : 7;
+  *logC = logN - *logR;
+  return true;
+}
+
 bool fast_path_ok(const cmm_op* op) {
-  if (op->prec == CMM_PREC_F64) return false;
-  return op->logR >= 6 && op->logR <= 9 && op->logC >= 6 && op->logC <= 10;
+  int lr, lc;
+  return fast_path_sizes(op->logR + op->logC, op->prec, &lr, &lc) && lr == op->logR;
 }
 
-template <int NC, typename S, int... RR>
-static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st) {
-  constexpr int R = RadProd<RR...>::value;
-  const size_t smem = sizeof(float2) * col_tile_elems(R);
-  const dim3 g(a.C / 8, (nd + kDetsPerCta - 1) / kDetsPerCta);
-  if (pass == 0) k_fast_fwd<NC, S, RR...><<<g, R, smem, st>>>(a, nd);
-  else k_fast_inv_bin<NC, S, RR...><<<g, R, smem, st>>>(a, nd);
+template <int NC, typename S, int R>
+static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
+  const int smem = (int)(sizeof(float2) * R * kJ);
+  if (attr_only) {
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return CMM_OK;
+  }
+  const dim3 g(a.C / kJ, (nd + kDetsPerCta - 1) / kDetsPerCta);
+  if (pass == 0) k_fast_fwd<NC, S, R><<<g, 2 * R, smem, st>>>(a, nd);
+  else k_fast_inv_bin<NC, S, R><<<g, 2 * R, smem, st>>>(a, nd);
   CMM_LAUNCH_CHECK();
-  return CMM_OK;
-}
-
-template <int NC, typename S, int... RR>
-static int attr_T() {
-  constexpr int R = RadProd<RR...>::value;
-  const int smem = (int)(sizeof(float2) * col_tile_elems(R));
-  CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, RR...>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, RR...>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return CMM_OK;
 }
 
 template <int NC, typename S>
 static int dispatch_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
-  switch (a.logR) {
-    case 6: return attr_only ? attr_T<NC, S, 8, 8>() : run_T<NC, S, 8, 8>(a, nd, pass, st);
-    case 7: return attr_only ? attr_T<NC, S, 2, 8, 8>() : run_T<NC, S, 2, 8, 8>(a, nd, pass, st);
-    case 8: return attr_only ? attr_T<NC, S, 4, 8, 8>() : run_T<NC, S, 4, 8, 8>(a, nd, pass, st);
-    default: return attr_only ? attr_T<NC, S, 8, 8, 8>() : run_T<NC, S, 8, 8, 8>(a, nd, pass, st);
-  }
-}
-
-template <typename S, int E, int... RC>
-static size_t smem_F() {
-  constexpr int C = RadProd<RC...>::value;
-  constexpr int TPR = C / E;
-  constexpr int ROWS = 256 / TPR;
-  constexpr int PS = clog2(E) <= 4 ? 4 : 5;
-  return sizeof(float2) * ROWS * (C + (C >> PS));
+  if (a.logR == 6) return run_T<NC, S, 64>(a, nd, pass, st, attr_only);
+  return run_T<NC, S, 128>(a, nd, pass, st, attr_only);
 }
 
 template <typename S, int E, int... RC>
 static int run_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
   constexpr int C = RadProd<RC...>::value;
-  constexpr int PAIRS = (256 / (C / E)) / 2;
-  const size_t smem = smem_F<S, E, RC...>();
+  constexpr int ROWS = FilterShape<C, E>::ROWS;
+  constexpr int PAIRS = ROWS / 2;
+  constexpr int PS = clog2(E);
+  const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_fast_filter<S, E, RC...>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return CMM_OK;
   }
   const int npairs = a.R / 2 + 1;
   const dim3 g((npairs + PAIRS - 1) / PAIRS, nd);
-  k_fast_filter<S, E, RC...><<<g, 256, smem, st>>>(a);
+  k_fast_filter<S, E, RC...><<<g, FilterShape<C, E>::THREADS, smem, st>>>(a);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
@@ -350,12 +440,22 @@ static int run_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
 template <typename S>
 static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
   switch (a.logC) {
-    case 6: return run_F<S, 16, 4, 16>(a, nd, st, attr_only);
-    case 7: return run_F<S, 16, 8, 16>(a, nd, st, attr_only);
+    case 6: return run_F<S, 16, 16, 4>(a, nd, st, attr_only);
+    case 7: return run_F<S, 16, 16, 8>(a, nd, st, attr_only);
     case 8: return run_F<S, 16, 16, 16>(a, nd, st, attr_only);
-    case 9: return run_F<S, 16, 2, 16, 16>(a, nd, st, attr_only);
-    default: return run_F<S, 16, 4, 16, 16>(a, nd, st, attr_only);
+    case 9: return run_F<S, 16, 16, 16, 2>(a, nd, st, attr_only);
+    case 10: return run_F<S, 16, 16, 16, 4>(a, nd, st, attr_only);
+    case 11: return run_F<S, 16, 16, 16, 8>(a, nd, st, attr_only);
+    default: return run_F<S, 16, 16, 16, 16>(a, nd, st, attr_only);
   }
+}
+
+static int flush(const TodArgs& a, int nc, cudaStream_t st) {
+  const int blocks = (int)std::min<long long>((a.npix + 255) / 256, 4096);
+  if (nc == 1) k_fast_flush<1><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix, a.done);
+  else k_fast_flush<3><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix, a.done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
 }
 
 // Forward pass from a stored TOD (right-hand side) uses the generic kernel of
@@ -374,8 +474,15 @@ static int apply_fast_s(cmm_op* op, int d0, int nd, const void* tod, int tod_is_
   }
   if (pass < 0 || pass == 1) CMM_TRY(dispatch_F<S>(a, nd, st, false));
   if (pass < 0 || pass == 2) {
-    if (nc == 1) CMM_TRY((dispatch_T<1, S>(a, nd, 2, st, false)));
-    else CMM_TRY((dispatch_T<3, S>(a, nd, 2, st, false)));
+    for (int g0 = 0; g0 < nd; g0 += kFlushDets) {
+      TodArgs b = a;
+      const int gn = std::min(kFlushDets, nd - g0);
+      b.d0 = a.d0 + g0;
+      b.spec = reinterpret_cast<S*>(a.spec) + (long long)g0 * a.N;
+      if (nc == 1) CMM_TRY((dispatch_T<1, S>(b, gn, 2, st, false)));
+      else CMM_TRY((dispatch_T<3, S>(b, gn, 2, st, false)));
+      CMM_TRY(flush(b, nc, st));
+    }
   }
   return CMM_OK;
 }
