@@ -13,8 +13,9 @@ Conventions shared with the consumers (they are input formats, not method):
   Stokes-major storage ``[ncomp][ny][nx]`` (ncomp 1 = T, 3 = T, Q, U).
 * boresight table ``bore``: int32 ``[n_t, 4]`` = (bx, by, cphi, sphi) with
   bx, by in units of 2^-16 pixel and (cphi, sphi) = (cos phi, sin phi) of the
-  sky rotation in Q1.30 (units of 2^-30).
-* detector table ``det_off``: int32 ``[n_det, 2]`` = (dx, dy) in 2^-16 pixel;
+  sky rotation in units of 2^-15 (|cphi|, |sphi| <= 2^15).
+* detector table ``det_off``: int32 ``[n_det, 2]`` = (dx, dy) in units of 2^-7
+  pixel (|dx|, |dy| < 2^14);
   ``det_pol``: float64 ``[n_det, 2]`` = (cos 2psi, sin 2psi).
 * noise: per detector (sigma, f_knee, alpha) of PSD(f) = sigma^2 (1 + (f/f_knee)^-alpha).
 
@@ -27,8 +28,9 @@ import math
 
 import numpy as np
 
-Q16 = 1 << 16
-Q30 = 1 << 30
+QB = 1 << 16   # boresight position units per pixel
+QR = 1 << 15   # rotation cos/sin units
+QD = 1 << 7    # detector offset units per pixel
 
 KIND = {"sky": 0, "noise": 1, "psi": 2, "sigma": 3, "fknee": 4, "vec": 5, "misc": 6}
 
@@ -115,10 +117,10 @@ def hex_focal_plane(n_det: int, rings: int, spacing_px: float) -> np.ndarray:
 
 def _quantise_bore(bx, by, phi):
     bore = np.empty((bx.shape[0], 4), np.int32)
-    bore[:, 0] = np.round(bx * Q16).astype(np.int64)
-    bore[:, 1] = np.round(by * Q16).astype(np.int64)
-    bore[:, 2] = np.round(np.cos(phi) * Q30).astype(np.int64)
-    bore[:, 3] = np.round(np.sin(phi) * Q30).astype(np.int64)
+    bore[:, 0] = np.round(bx * QB).astype(np.int64)
+    bore[:, 1] = np.round(by * QB).astype(np.int64)
+    bore[:, 2] = np.round(np.cos(phi) * QR).astype(np.int64)
+    bore[:, 3] = np.round(np.sin(phi) * QR).astype(np.int64)
     return bore
 
 
@@ -162,7 +164,7 @@ def make_scan(*, cfg, real=0, ny, nx, n_t, focal_px, f_samp=400.0, speed_px_s=12
     bx, by, phi = drift_scan_positions(n_t, ny, nx, f_samp, speed_px_s, throw_px,
                                        list(segments), margin_px)
     bore = _quantise_bore(bx, by, phi)
-    det_off = np.round(focal_px * Q16).astype(np.int32)
+    det_off = np.round(focal_px * QD).astype(np.int32)
     psi = rng(cfg, real, "psi").uniform(0.0, np.pi, size=focal_px.shape[0])
     det_pol = np.stack([np.cos(2 * psi), np.sin(2 * psi)], axis=1)
     return Scan(ny=ny, nx=nx, bore=bore, det_off=det_off, det_pol=det_pol,
@@ -181,14 +183,14 @@ def bccb_scan(ny, nx, n_t, diagonal=False, ncomp=3):
         raise ValueError("n_t must be a multiple of the scan period")
     t = np.arange(n_t, dtype=np.int64)
     bore = np.zeros((n_t, 4), np.int32)
-    bore[:, 0] = (t % nx) * Q16
+    bore[:, 0] = (t % nx) * QB
     if diagonal:
-        bore[:, 1] = (t % ny) * Q16
-    bore[:, 2] = Q30
+        bore[:, 1] = (t % ny) * QB
+    bore[:, 2] = QR
     psis = np.array([0.0, np.pi / 6, np.pi / 3]) if ncomp == 3 else np.array([0.0])
     rows = np.repeat(np.arange(ny), len(psis))
     det_off = np.zeros((rows.size, 2), np.int32)
-    det_off[:, 1] = rows * Q16
+    det_off[:, 1] = rows * QD
     psi = np.tile(psis, ny)
     det_pol = np.stack([np.cos(2 * psi), np.sin(2 * psi)], axis=1)
     return Scan(ny=ny, nx=nx, bore=bore, det_off=det_off, det_pol=det_pol,

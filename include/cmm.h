@@ -106,17 +106,19 @@ const char* cmm_version(void);
  * The pointing matrix P of Eq. 1, never stored: each sample's pixel and response
  * are computed on the fly from a boresight table and a detector table.
  *   bore    host int32 [n_samp][4]: (bx, by) boresight in units of 2^-16 pixel,
- *           (cphi, sphi) = (cos, sin) of the sky rotation in units of 2^-30.
- *   det_off host int32 [n_det][2]: (dx, dy) detector offset in units of 2^-16 pixel.
+ *           |bx|, |by| <= 2^30 - 2^25; (cphi, sphi) = (cos, sin) of the sky rotation
+ *           in units of 2^-15, |cphi|, |sphi| <= 2^15.
+ *   det_off host int32 [n_det][2]: (dx, dy) detector offset in units of 2^-7 pixel,
+ *           |dx|, |dy| < 2^14.
  *   det_pol host double [n_det][2]: (cos 2psi, sin 2psi) of the detector angle psi.
- * Sample (d, t) lies at x = (bx << 30) + cphi*dx - sphi*dy, y = (by << 30) + sphi*dx
- * + cphi*dy (units of 2^-46 pixel, exact in int64) and hits pixel ix = (x + 2^45) >> 46,
- * iy likewise (nearest pixel, halves rounded up).  Its row of P is (1) for T maps and
+ * Sample (d, t) has the rotated offset ox = cphi*dx - sphi*dy, oy = sphi*dx + cphi*dy
+ * (exact int32, units of 2^-22 pixel), lies at x = bx + (ox >> 6), y = by + (oy >> 6)
+ * (units of 2^-16 pixel, arithmetic shifts) and hits pixel ix = (x + 2^15) >> 16, iy
+ * likewise (nearest pixel, halves rounded up).  Its row of P is (1) for T maps and
  * (1, cos 2a, sin 2a), a = psi + phi, for TQU maps (Sec. Test setup).  Samples off
  * the map (unless periodic) and samples of masked pixels have a zero row.  A pixel is
  * masked when its unit-weight hit block sum_t P_t P_t^T has no hits or reciprocal
- * condition number below 1e-3.  The tables are copied; `bore` requires
- * |cphi|, |sphi| <= 2^30.
+ * condition number below 1e-3.  The tables are copied.
  */
 int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det,
                         const int32_t* det_off, const double* det_pol, int64_t n_samp,

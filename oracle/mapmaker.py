@@ -52,19 +52,22 @@ DET_CHUNK = 16
 def sample_pixels(scan, dets):
     """Nearest pixel of every sample of detectors ``dets`` (R10).
 
-    x = (bx << 30) + cphi*dx - sphi*dy, y = (by << 30) + sphi*dx + cphi*dy in units
-    of 2^-46 pixel; ix = floor((x + 2^45) / 2^46) (round half up), same for iy.
-    Samples outside the map are -1 (cut) unless the scan is periodic, where the
-    indices wrap.
+    The rotated offset (ox, oy) = R(phi) (dx, dy) = (cphi dx - sphi dy, sphi dx + cphi dy)
+    is exact in units of 2^-22 pixel; it is floored to 2^-16 pixel and added to the
+    boresight: x = bx + floor(ox / 64); ix = floor((x + 2^15) / 2^16) (round half up),
+    same for y.  Samples outside the map are -1 (cut) unless the scan is periodic,
+    where the indices wrap.
     """
     bore = scan.bore.astype(np.int64)
     bx, by, cp, sp = bore[:, 0], bore[:, 1], bore[:, 2], bore[:, 3]
     dx = scan.det_off[dets, 0].astype(np.int64)[:, None]
     dy = scan.det_off[dets, 1].astype(np.int64)[:, None]
-    x = (bx << 30)[None, :] + cp[None, :] * dx - sp[None, :] * dy
-    y = (by << 30)[None, :] + sp[None, :] * dx + cp[None, :] * dy
-    ix = (x + (1 << 45)) >> 46
-    iy = (y + (1 << 45)) >> 46
+    ox = cp[None, :] * dx - sp[None, :] * dy
+    oy = sp[None, :] * dx + cp[None, :] * dy
+    x = bx[None, :] + np.floor_divide(ox, 64)
+    y = by[None, :] + np.floor_divide(oy, 64)
+    ix = np.floor_divide(x + (1 << 15), 1 << 16)
+    iy = np.floor_divide(y + (1 << 15), 1 << 16)
     if scan.periodic:
         ix = np.mod(ix, scan.nx)
         iy = np.mod(iy, scan.ny)
@@ -79,8 +82,8 @@ def sample_weights(scan, dets):
     nd = len(np.atleast_1d(dets))
     if scan.ncomp == 1:
         return np.ones((1, nd, scan.n_t))
-    cf = scan.bore[:, 2].astype(np.float64) * 2.0 ** -30
-    sf = scan.bore[:, 3].astype(np.float64) * 2.0 ** -30
+    cf = scan.bore[:, 2].astype(np.float64) * 2.0 ** -15
+    sf = scan.bore[:, 3].astype(np.float64) * 2.0 ** -15
     c2f = cf * cf - sf * sf
     s2f = 2.0 * cf * sf
     c2p = scan.det_pol[dets, 0][:, None]

@@ -72,11 +72,11 @@ __global__ void k_noise_diag(const double4_32a* __restrict__ coef, long long n_t
   if (threadIdx.x == 0) out[d] = sh[0] / (double)n_t;
 }
 
-// (cos 2phi, sin 2phi) per sample from the Q1.30 rotation, in FP64, stored in FP32.
+// (cos 2phi, sin 2phi) per sample from the 2^-15 fixed-point rotation, in FP64, stored in FP32.
 __global__ void k_rot2(const int4* __restrict__ bore, long long n, float2* __restrict__ out) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int4 b = bore[t];
-    const double cf = (double)b.z * 0x1p-30, sf = (double)b.w * 0x1p-30;
+    const double cf = (double)b.z * 0x1p-15, sf = (double)b.w * 0x1p-15;
     out[t] = make_float2((float)(cf * cf - sf * sf), (float)(2.0 * cf * sf));
   }
 }
@@ -173,6 +173,16 @@ int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, c
     return fail(CMM_ERR_ARG, "bad map size");
   if (geom->ncomp != 1 && geom->ncomp != 3) return fail(CMM_ERR_ARG, "ncomp must be 1 or 3");
   if (n_det <= 0 || n_samp <= 0 || n_det > 65535) return fail(CMM_ERR_ARG, "bad detector or sample count");
+  // ranges under which the fixed-point pointing is exact in int32
+  for (int d = 0; d < n_det; ++d)
+    if (std::abs((long long)det_off[2 * d]) >= (1 << 14) || std::abs((long long)det_off[2 * d + 1]) >= (1 << 14))
+      return fail(CMM_ERR_ARG, "detector offset out of range (|dx|, |dy| < 2^14)");
+  for (int64_t t = 0; t < n_samp; ++t) {
+    const int32_t* b = bore + 4 * t;
+    if (std::abs((long long)b[0]) > (1LL << 30) - (1LL << 25) || std::abs((long long)b[1]) > (1LL << 30) - (1LL << 25) ||
+        std::abs((long long)b[2]) > (1 << 15) || std::abs((long long)b[3]) > (1 << 15))
+      return fail(CMM_ERR_ARG, "boresight entry out of range");
+  }
   CMM_CUDA(cudaSetDevice(ctx->device));
   cmm_pointing* pt = new cmm_pointing();
   pt->ctx = ctx;

@@ -12,12 +12,16 @@ namespace cmm {
 
 // ------------------------------------------------------------------ pointing
 
-// Nearest pixel of sample (bore b, detector offset o): integer fixed point, exact.
+// Nearest pixel of sample (bore b, detector offset o), exact 32-bit fixed point:
+// the rotated offset (units 2^-22 px, |.| < 2^30) is floored to 2^-16 px and added
+// to the boresight (units 2^-16 px); the pixel is floor((x + 2^15) / 2^16).
 __device__ __forceinline__ int sample_pixel(const int4 b, const int2 o, int ny, int nx, int periodic) {
-  const long long x = (long long)b.x * (1LL << 30) + (long long)b.z * o.x - (long long)b.w * o.y;
-  const long long y = (long long)b.y * (1LL << 30) + (long long)b.w * o.x + (long long)b.z * o.y;
-  int ix = (int)((x + (1LL << 45)) >> 46);
-  int iy = (int)((y + (1LL << 45)) >> 46);
+  const int ox = b.z * o.x - b.w * o.y;
+  const int oy = b.w * o.x + b.z * o.y;
+  const int x = b.x + (ox >> 6);
+  const int y = b.y + (oy >> 6);
+  int ix = (x + (1 << 15)) >> 16;
+  int iy = (y + (1 << 15)) >> 16;
   if (periodic) {
     ix %= nx;
     if (ix < 0) ix += nx;
@@ -32,7 +36,7 @@ __device__ __forceinline__ int sample_pixel(const int4 b, const int2 o, int ny, 
 // Response (cos 2a, sin 2a), a = psi_d + phi_t, by angle addition.
 template <typename T>
 __device__ __forceinline__ void sample_response(const int4 b, const V2<T> pol, T& c, T& s) {
-  const T q = (T)9.31322574615478515625e-10;  // 2^-30
+  const T q = (T)3.0517578125e-05;  // 2^-15
   const T cf = (T)b.z * q, sf = (T)b.w * q;
   const T c2 = cf * cf - sf * sf;
   const T s2 = (T)2 * cf * sf;

@@ -31,7 +31,15 @@ namespace cmm {
 constexpr int kDetsPerCta = 2;
 constexpr int kFlushDets = 128;
 constexpr int kE = 16;     // elements per thread in the column FFT
-constexpr int kJ = 32;     // columns per CTA (one per lane)
+
+// Columns per CTA: 32 (one per lane) for R <= 128, 16 (one per half-warp lane)
+// for R = 256; either way a half-warp reads 16 complex = 32 consecutive samples
+// and touches 32 different shared-memory banks.
+template <int R> struct ColShape {
+  static constexpr int J = R >= 256 ? 16 : 32;
+  static constexpr int THREADS = J * R / kE;
+  static constexpr int MINB = 768 / THREADS;
+};
 
 // GB300's FP64 unit also executes int <-> float conversions, at a small fraction
 // of the FP32 rate; this helper does the one of the filter exactly on the FP32 pipe.
@@ -76,13 +84,14 @@ __device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, 
   return g.x + c * g.y + s * g.z;
 }
 
-// 32 interleaved columns: position pos of column cl at 32 pos + cl, so every access
-// of the column FFT puts the 32 lanes of a warp on 32 consecutive elements.
-struct Col32 {
+// J interleaved columns: position pos of column cl at J pos + cl, so every access
+// of the column FFT puts consecutive lanes on consecutive elements.
+template <int J>
+struct ColJ {
   float2* buf;
   int cl;
-  __device__ __forceinline__ void st(int pos, float2 v) const { buf[(pos << 5) + cl] = v; }
-  __device__ __forceinline__ float2 ld(int pos) const { return buf[(pos << 5) + cl]; }
+  __device__ __forceinline__ void st(int pos, float2 v) const { buf[pos * J + cl] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return buf[pos * J + cl]; }
 };
 
 template <int R> struct ColPlan;
@@ -98,18 +107,25 @@ template <> struct ColPlan<128> {
     rfft<SIGN, kE, 16, 8>(x, i, tw, ad);
   }
 };
+template <> struct ColPlan<256> {
+  template <int SIGN, typename Addr>
+  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
+    rfft<SIGN, kE, 16, 16>(x, i, tw, ad);
+  }
+};
 
 // ------------------------------------------------------------------ pass T (forward)
 template <int NC, typename S, int R>
-__global__ void __launch_bounds__(2 * R, 384 / R) k_fast_fwd(const TodArgs a, int nd) {
+__global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_fwd(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
+  constexpr int J = ColShape<R>::J;
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
-  const int cl = threadIdx.x & 31;
-  const int i = threadIdx.x >> 5;
-  const int c = (blockIdx.x << 5) + cl;
+  const int cl = threadIdx.x % J;
+  const int i = threadIdx.x / J;
+  const int c = blockIdx.x * J + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  const Col32 ad{smf, cl};
+  const ColJ<J> ad{smf, cl};
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
     const int dl = dl0 + dd;
@@ -246,14 +262,16 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
                : "memory");
 }
 
-// Bins the two samples of every lane of a warp, which hold 64 consecutive samples
-// in lane order (lane l: samples 2l, 2l + 1).  Items with equal pixels that are
-// adjacent in time are summed (in-lane, then across lanes by a segmented suffix
-// scan); the first item of every run issues one reduction.
-template <int NC>
+// Bins the two samples of every lane of a warp.  Each group of G consecutive lanes
+// holds 2G consecutive samples in lane order (lane l of a group: samples 2l, 2l + 1).
+// Items with equal pixels that are adjacent in time are summed (in-lane, then across
+// the lanes of a group by a segmented suffix scan); the first item of every run
+// issues one reduction.
+template <int NC, int G>
 __device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0, float3 v1) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const bool group_end = (lane % G) == G - 1;
   const bool two = p1 != p0;
   if (!two) {
     v0.x += v1.x;
@@ -262,7 +280,7 @@ __device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0
   }
   const int g = two ? p1 : p0;                 // pixel of the lane's last item
   const int fnext = __shfl_down_sync(full, p0, 1);
-  const bool link = lane < 31 && g >= 0 && g == fnext;   // next lane's first item continues my last run
+  const bool link = !group_end && g >= 0 && g == fnext;   // next lane's first item continues my last run
   const unsigned linkmask = __ballot_sync(full, link);
   const bool linkprev = lane > 0 && ((linkmask >> (lane - 1)) & 1u);
   // y_l = A_l + (single_l && link_l ? y_{l+1} : 0), by a segmented suffix scan
@@ -306,15 +324,16 @@ __device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0
 }
 
 template <int NC, typename S, int R>
-__global__ void __launch_bounds__(2 * R, 384 / R) k_fast_inv_bin(const TodArgs a, int nd) {
+__global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
+  constexpr int J = ColShape<R>::J;
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
-  const int cl = threadIdx.x & 31;
-  const int i = threadIdx.x >> 5;
-  const int c = (blockIdx.x << 5) + cl;
+  const int cl = threadIdx.x % J;
+  const int i = threadIdx.x / J;
+  const int c = blockIdx.x * J + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  const Col32 ad{smf, cl};
+  const ColJ<J> ad{smf, cl};
   const float scale = 1.0f / (float)a.N;
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(2 * R, 384 / R) k_fast_inv_bin(const TodArgs a
         v1.y = c1 * u1;
         v1.z = s1 * u1;
       }
-      warp_bin<NC>(a.acc32, p0, p1, v0, v1);
+      warp_bin<NC, J>(a.acc32, p0, p1, v0, v1);
     }
   }
 }
@@ -385,10 +404,11 @@ __global__ void k_fast_flush(float* __restrict__ acc32, double* __restrict__ acc
 
 // ------------------------------------------------------------------ dispatch
 
-// Fast-path split of N = 2^logN: R = 64 below 2^16, R = 128 from 2^16 to 2^19.
+// Fast-path split of N = 2^logN: R = 64 below 2^16, 128 for 2^16 and 2^17, 256 for
+// 2^18 and 2^19 (rows C = N / R of 64 to 2048 points).
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC) {
   if (prec == CMM_PREC_F64 || logN < 12 || logN > 19) return false;
-  *logR = logN < 16 ? 6 : 7;
+  *logR = logN < 16 ? 6 : (logN < 18 ? 7 : 8);
   *logC = logN - *logR;
   return true;
 }
@@ -400,15 +420,17 @@ bool fast_path_ok(const cmm_op* op) {
 
 template <int NC, typename S, int R>
 static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
-  const int smem = (int)(sizeof(float2) * R * kJ);
+  constexpr int J = ColShape<R>::J;
+  constexpr int NT = ColShape<R>::THREADS;
+  const int smem = (int)(sizeof(float2) * R * J);
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return CMM_OK;
   }
-  const dim3 g(a.C / kJ, (nd + kDetsPerCta - 1) / kDetsPerCta);
-  if (pass == 0) k_fast_fwd<NC, S, R><<<g, 2 * R, smem, st>>>(a, nd);
-  else k_fast_inv_bin<NC, S, R><<<g, 2 * R, smem, st>>>(a, nd);
+  const dim3 g(a.C / J, (nd + kDetsPerCta - 1) / kDetsPerCta);
+  if (pass == 0) k_fast_fwd<NC, S, R><<<g, NT, smem, st>>>(a, nd);
+  else k_fast_inv_bin<NC, S, R><<<g, NT, smem, st>>>(a, nd);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
@@ -416,7 +438,8 @@ static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_
 template <int NC, typename S>
 static int dispatch_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
   if (a.logR == 6) return run_T<NC, S, 64>(a, nd, pass, st, attr_only);
-  return run_T<NC, S, 128>(a, nd, pass, st, attr_only);
+  if (a.logR == 7) return run_T<NC, S, 128>(a, nd, pass, st, attr_only);
+  return run_T<NC, S, 256>(a, nd, pass, st, attr_only);
 }
 
 template <typename S, int E, int... RC>
