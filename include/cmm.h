@@ -54,7 +54,8 @@ enum cmm_precon_kind {
   CMM_PRECON_BINNED = 0,    /* M_B, Eq. 3-4: per-pixel inverse of P^T diag(N^-1) P */
   CMM_PRECON_JACOBI = 1,    /* M_J, Eq. 5: per-pixel inverse of P^T P */
   CMM_PRECON_CIRCULANT = 2, /* M_C, Eq. 7-13 with the Gaussian regularisation */
-  CMM_PRECON_IDENTITY = 3   /* M = I (plain CG) */
+  CMM_PRECON_IDENTITY = 3,  /* M = I (plain CG) */
+  CMM_PRECON_CIRC_LEARNED = 4 /* M_C followed by a learned correction (flexible CG) */
 };
 
 typedef struct cmm_ctx cmm_ctx;
@@ -82,6 +83,9 @@ typedef struct {
   int32_t check_every; /* iterations per captured graph launch between host checks (>= 1) */
   int32_t use_graph;   /* != 0: replay the iteration as a CUDA graph */
   int32_t x0_given;    /* != 0: x holds the starting guess; else x0 = 0 */
+  int32_t cg_f32;      /* != 0: CG vectors, dot products and scalars rounded to FP32 */
+  int32_t resid_replace; /* > 0: every that many iterations r = b - A x is recomputed */
+  int32_t flexible;    /* != 0: flexible CG, beta = z^T (r - r_old) / (z_old^T r_old) */
 } cmm_solve_opts;
 
 typedef struct {
@@ -204,6 +208,26 @@ int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped);
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x,
               const cmm_solve_opts* opts, double* resid_hist, double* anorm_terms,
               cmm_solve_info* info);
+
+/* ---------------------------------------------------------------- batches and tuning
+ * Batched solves (many Monte-Carlo realisations or patches of uneven size): n
+ * independent PCG solves, one per (ops[i], pcs[i], b[i], x[i]), are advanced
+ * together; every `check_every` iterations of the whole batch are one CUDA graph
+ * launch in which the solves are parallel branches, each on the stream of its own
+ * context (give each operator its own context for the solves to overlap).  A solve
+ * that has converged keeps returning early inside the graph.  opts as in
+ * cmm_solve (resid_replace must be 0); infos[i] receives each solve's result, its
+ * `seconds` the wall time of the whole batch.  Waits for the result.
+ */
+int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const double* const* b,
+                    double* const* x, const cmm_solve_opts* opts, cmm_solve_info* infos);
+/* Chooses the split N = R C of the time-ordered FFTs for this operator by timing
+ * `reps` applications of A for every split the kernels support, keeps the fastest,
+ * and remembers it for operators of the same (n_samp, n_det, precision, ncomp) in
+ * this process and, if cache_path is not NULL, in that text file (read first,
+ * appended to).  *chosen_logR (may be NULL) receives log2 R; *best_ms (may be NULL)
+ * the time of one application, or -1 when the decision came from a cache. */
+int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, double* best_ms);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcmm.so")
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
-PRECON_BINNED, PRECON_JACOBI, PRECON_CIRCULANT, PRECON_IDENTITY = 0, 1, 2, 3
+PRECON_BINNED, PRECON_JACOBI, PRECON_CIRCULANT, PRECON_IDENTITY, PRECON_CIRC_LEARNED = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 
@@ -41,7 +41,8 @@ class PreconOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
-                ("use_graph", C.c_int32), ("x0_given", C.c_int32)]
+                ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
+                ("resid_replace", C.c_int32), ("flexible", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -78,6 +79,8 @@ _SIGS = {
     "cmm_precon_apply": [_vp, _vp, _vp],
     "cmm_precon_clamped": [_vp, C.POINTER(_i64)],
     "cmm_solve": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveInfo)],
+    "cmm_batch_solve": [_i32, _vp, _vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)],
+    "cmm_autotune": [_vp, _i32, C.c_char_p, C.POINTER(_i32), C.POINTER(_d)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -250,13 +253,33 @@ def cmm_precon_clamped(pc):
 
 
 def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
-              resid_hist=None, anorm_terms=None):
-    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0)
+              resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False):
+    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0,
+                     1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0)
     info = SolveInfo()
     _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
                           _dev(resid_hist, numel=None, name="resid_hist"),
                           _dev(anorm_terms, numel=None, name="anorm_terms"), C.byref(info)))
     return info
+
+
+def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f32=False, flexible=False):
+    """Batched PCG over parallel lists of operator / preconditioner handles and
+    device maps; returns the list of SolveInfo."""
+    n = len(ops)
+    arr = lambda items: (C.c_void_p * n)(*[C.c_void_p(v if isinstance(v, int) else v.value) for v in items])
+    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0)
+    infos = (SolveInfo * n)()
+    _check(_lib.cmm_batch_solve(n, arr(ops), arr(pcs), arr([t.data_ptr() for t in bs]),
+                                arr([t.data_ptr() for t in xs]), C.byref(opts), infos))
+    return list(infos)
+
+
+def cmm_autotune(op, reps=3, cache_path=None):
+    lr = C.c_int32()
+    ms = C.c_double()
+    _check(_lib.cmm_autotune(op, int(reps), cache_path.encode() if cache_path else None, C.byref(lr), C.byref(ms)))
+    return int(lr.value), float(ms.value)
 
 
 # ---------------------------------------------------------------- handle owners
@@ -365,12 +388,13 @@ class Precon:
 
 
 def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=10, use_graph=True,
-          history=False):
+          history=False, cg_f32=False, resid_replace=0, flexible=False):
     """PCG on A x = b; returns (x, info, resid_hist, anorm_terms)."""
     import torch
     x0_given = x is not None
     x = op.new_map() if x is None else x
     hist = torch.zeros(maxit + 1, dtype=torch.float64, device=b.device) if history else None
     terms = torch.zeros(max(maxit, 1), dtype=torch.float64, device=b.device) if history else None
-    info = cmm_solve(op.h, pc.h, b, x, tol, maxit, check_every, use_graph, x0_given, hist, terms)
+    info = cmm_solve(op.h, pc.h, b, x, tol, maxit, check_every, use_graph, x0_given, hist, terms,
+                     cg_f32, resid_replace, flexible)
     return x, info, hist, terms

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -381,6 +382,24 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   return CMM_OK;
 }
 
+// Re-split N = R C (logR given) for the time-ordered FFTs: new twiddle tables and
+// kernel attributes.  The spectrum buffer holds N complex per detector either way.
+static int op_set_split(cmm_op* op, int logR) {
+  const int logN = op->logR + op->logC;
+  if (logR < 1 || logR >= logN) return fail(CMM_ERR_ARG, "bad split");
+  if (op->tw) {
+    CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+    dfree(op->tw);
+    op->tw = nullptr;
+  }
+  op->logR = logR;
+  op->logC = logN - logR;
+  op->R = 1 << op->logR;
+  op->C = 1 << op->logC;
+  CMM_TRY(op_init_twiddles(op));
+  return op_prepare_kernels(op);
+}
+
 static int apply_A_dev(cmm_op* op, const double* m_in, double* m_out) {
   CMM_TRY(launch_map_to_gather(op, m_in));
   for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
@@ -687,19 +706,31 @@ int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped) {
 }
 
 // ------------------------------------------------------------------ solver
-static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, double* r, double* z, double* p, double* q,
-                           SolverDev* dst, double* p1, double* hist, double* anorm) {
+struct SolveBufs {
+  double *r, *z, *p, *q, *r_old, *p1, *p2, *p3;
+};
+
+// z = M r (and the learned correction when the preconditioner has one), then the
+// CG dot products of z.
+static int precon_step(cmm_op* op, cmm_precon* pc, const SolveBufs& v, SolverDev* dst, bool flexible) {
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   cudaStream_t st = op->ctx->stream;
-  const int* done = &dst->done;
-  CMM_TRY(apply_A_dev(op, p, q));
-  CMM_TRY(launch_dot_partial(p, q, n, p1, done, st));
-  CMM_TRY(launch_solver_alpha(dst, p1, anorm, st));
-  CMM_TRY(launch_update_xr(x, r, p, q, n, dst, p1, st));
-  CMM_TRY(launch_solver_check(dst, p1, hist, st));
-  CMM_TRY(precon_apply_dev(pc, r, z, p1, done));
-  CMM_TRY(launch_solver_beta(dst, p1, st));
-  CMM_TRY(launch_update_p(p, z, n, dst, st));
+  CMM_TRY(precon_apply_dev(pc, v.r, v.z, nullptr, &dst->done));
+  return launch_solver_z(v.z, v.r, flexible ? v.r_old : nullptr, n, dst, v.p1, flexible ? v.p3 : nullptr, st);
+}
+
+static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBufs& v, SolverDev* dst,
+                           double* hist, double* anorm, bool flexible) {
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  CMM_TRY(apply_A_dev(op, v.p, v.q));
+  CMM_TRY(launch_dot_partial_cg(v.p, v.q, n, dst, v.p1, st));
+  CMM_TRY(launch_solver_alpha(dst, v.p1, anorm, st));
+  CMM_TRY(launch_update_xr(x, v.r, flexible ? v.r_old : nullptr, v.p, v.q, n, dst, v.p2, st));
+  CMM_TRY(launch_solver_check(dst, v.p2, hist, st));
+  CMM_TRY(precon_step(op, pc, v, dst, flexible));
+  CMM_TRY(launch_solver_beta(dst, v.p1, flexible ? v.p3 : nullptr, st));
+  CMM_TRY(launch_update_p(v.p, v.z, n, dst, st));
   return CMM_OK;
 }
 
@@ -707,28 +738,32 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
               double* resid_hist, double* anorm_terms, cmm_solve_info* info) {
   if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
   if (pc->op != op) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
-  if (opts->maxit < 0 || !(opts->tol >= 0)) return fail(CMM_ERR_ARG, "bad solve options");
+  if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace < 0) return fail(CMM_ERR_ARG, "bad solve options");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   const auto t0 = std::chrono::steady_clock::now();
   cmm_ctx* c = op->ctx;
   cudaStream_t st = c->stream;
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
-  if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (4 * n + 2 * kRedBlocks)));
+  const bool flexible = opts->flexible != 0 || pc->kind == CMM_PRECON_CIRC_LEARNED;
+  if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (5 * n + 3 * kRedBlocks)));
   if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
-  double* r = op->sol;
-  double* z = r + n;
-  double* p = z + n;
-  double* q = p + n;
-  double* p1 = q + n;
-  double* p2 = p1 + kRedBlocks;
+  SolveBufs v;
+  v.r = op->sol;
+  v.z = v.r + n;
+  v.p = v.z + n;
+  v.q = v.p + n;
+  v.r_old = v.q + n;
+  v.p1 = v.r_old + n;
+  v.p2 = v.p1 + kRedBlocks;
+  v.p3 = v.p2 + kRedBlocks;
   SolverDev* dst = (SolverDev*)op->sol_state;
-  // ||b||^2
   double bnorm2 = 0.0;
   CMM_TRY(cmm_dot(op, b, b, n, &bnorm2));
   SolverDev h{};
   h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
   h.tol = opts->tol;
   h.maxit = opts->maxit;
+  h.f32 = opts->cg_f32 ? 1 : 0;
   CMM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   if (!(bnorm2 > 0)) {
     CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
@@ -739,18 +774,21 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     info->seconds = 0.0;
     return CMM_OK;
   }
+  // r0 = b - A x0 (rounded in FP32 CG), z0 = M r0, p0 = z0
   if (opts->x0_given) {
-    CMM_TRY(apply_A_dev(op, x, q));
-    CMM_TRY(launch_copy_sub(r, b, q, n, st));
+    CMM_TRY(apply_A_dev(op, x, v.q));
   } else {
     CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    CMM_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    CMM_CUDA(cudaMemsetAsync(v.q, 0, sizeof(double) * n, st));
   }
-  CMM_TRY(precon_apply_dev(pc, r, z, p1, nullptr));
-  CMM_TRY(launch_dot_partial(r, r, n, p2, nullptr, st));
-  CMM_TRY(launch_solver_init(dst, p1, p2, resid_hist, st));
-  CMM_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  const int per = std::max(1, opts->check_every);
+  CMM_TRY(launch_residual(v.r, b, v.q, n, dst, v.p2, st));
+  CMM_CUDA(cudaMemcpyAsync(v.r_old, v.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CMM_TRY(precon_step(op, pc, v, dst, false));
+  CMM_TRY(launch_solver_init(dst, v.p1, v.p2, resid_hist, st));
+  CMM_CUDA(cudaMemcpyAsync(v.p, v.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  int per = std::max(1, opts->check_every);
+  if (opts->resid_replace > 0) per = std::min(per, opts->resid_replace);
+  while (opts->resid_replace > 0 && opts->resid_replace % per) --per;   // per divides the replacement period
   op->done = &dst->done;
   cudaGraphExec_t exec = nullptr;
   int status = CMM_OK;
@@ -759,7 +797,8 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     status = [&]() -> int {
       CMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       int s2 = CMM_OK;
-      for (int i = 0; i < per && s2 == CMM_OK; ++i) s2 = solve_iteration(op, pc, x, r, z, p, q, dst, p1, resid_hist, anorm_terms);
+      for (int i = 0; i < per && s2 == CMM_OK; ++i)
+        s2 = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible);
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       if (s2 != CMM_OK) return s2;
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
@@ -779,7 +818,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
       }
     } else {
       for (int i = 0; i < per && status == CMM_OK; ++i)
-        status = solve_iteration(op, pc, x, r, z, p, q, dst, p1, resid_hist, anorm_terms);
+        status = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible);
       if (status != CMM_OK) break;
     }
     launched += per;
@@ -791,6 +830,15 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     }
     if (hs->done) break;
     if (launched > opts->maxit + per) break;
+    if (opts->resid_replace > 0 && hs->iter % opts->resid_replace == 0) {
+      // residual replacement: r = b - A x, z = M r, rho = r^T z; p is kept
+      status = [&]() -> int {
+        CMM_TRY(apply_A_dev(op, x, v.q));
+        CMM_TRY(launch_residual(v.r, b, v.q, n, dst, v.p2, st));
+        CMM_TRY(precon_step(op, pc, v, dst, false));
+        return launch_solver_rho(dst, v.p1, st);
+      }();
+    }
   }
   op->done = nullptr;
   if (exec) cudaGraphExecDestroy(exec);
@@ -800,6 +848,215 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   info->rel_resid = hs->rel;
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return CMM_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+struct TuneKey {
+  int64_t n_t;
+  int n_det, prec, ncomp;
+  bool operator==(const TuneKey& o) const {
+    return n_t == o.n_t && n_det == o.n_det && prec == o.prec && ncomp == o.ncomp;
+  }
+};
+std::vector<std::pair<TuneKey, int>> g_tune_cache;
+}  // namespace
+
+int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, double* best_ms) {
+  if (!op || reps <= 0) return fail(CMM_ERR_ARG, "bad argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const TuneKey key{op->pt->n_t, op->pt->n_det, op->prec, op->pt->ncomp};
+  const int logN = op->logR + op->logC;
+  // cached decision (process-wide, then the optional file)
+  for (auto& e : g_tune_cache)
+    if (e.first == key) {
+      if (e.second != op->logR) CMM_TRY(op_set_split(op, e.second));
+      if (chosen_logR) *chosen_logR = e.second;
+      if (best_ms) *best_ms = -1.0;
+      return CMM_OK;
+    }
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      long long nt;
+      int nd, pr, nc, lr;
+      while (std::fscanf(f, "%lld %d %d %d %d", &nt, &nd, &pr, &nc, &lr) == 5)
+        if (TuneKey{nt, nd, pr, nc} == key && lr > 0 && lr < logN) {
+          std::fclose(f);
+          g_tune_cache.push_back({key, lr});
+          if (lr != op->logR) CMM_TRY(op_set_split(op, lr));
+          if (chosen_logR) *chosen_logR = lr;
+          if (best_ms) *best_ms = -1.0;
+          return CMM_OK;
+        }
+      std::fclose(f);
+    }
+  }
+  // candidates: every split the fast kernels support, else the current one
+  std::vector<int> cand;
+  for (int lr = 6; lr <= 8; ++lr)
+    if (logN - lr >= 6 && logN - lr <= 12 && op->prec != CMM_PREC_F64) cand.push_back(lr);
+  if (cand.empty()) cand.push_back(op->logR);
+  const size_t bytes = sizeof(double) * op->pt->ncomp * op->pt->npix;
+  CMM_CUDA(cudaMemsetAsync(op->tmp_a, 0, bytes, op->ctx->stream));
+  cudaEvent_t e0, e1;
+  CMM_CUDA(cudaEventCreate(&e0));
+  CMM_CUDA(cudaEventCreate(&e1));
+  int best = cand[0];
+  double best_t = 1e300;
+  int s = CMM_OK;
+  for (int lr : cand) {
+    s = op_set_split(op, lr);
+    if (s != CMM_OK) break;
+    s = apply_A_dev(op, op->tmp_a, op->tmp_b);   // warm-up
+    if (s != CMM_OK) break;
+    cudaEventRecord(e0, op->ctx->stream);
+    for (int r = 0; r < reps && s == CMM_OK; ++r) s = apply_A_dev(op, op->tmp_a, op->tmp_b);
+    cudaEventRecord(e1, op->ctx->stream);
+    if (s != CMM_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < best_t) {
+      best_t = ms / reps;
+      best = lr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != CMM_OK) return s;
+  if (best != op->logR) CMM_TRY(op_set_split(op, best));
+  g_tune_cache.push_back({key, best});
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%lld %d %d %d %d\n", (long long)key.n_t, key.n_det, key.prec, key.ncomp, best);
+      std::fclose(f);
+    }
+  }
+  if (chosen_logR) *chosen_logR = best;
+  if (best_ms) *best_ms = best_t;
+  return CMM_OK;
+}
+
+// ------------------------------------------------------------------ batched solves
+int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const double* const* b,
+                    double* const* x, const cmm_solve_opts* opts, cmm_solve_info* infos) {
+  if (n <= 0 || !ops || !pcs || !b || !x || !opts || !infos) return fail(CMM_ERR_ARG, "null argument");
+  for (int i = 0; i < n; ++i) {
+    if (!ops[i] || !pcs[i] || !b[i] || !x[i]) return fail(CMM_ERR_ARG, "null entry in batch");
+    if (pcs[i]->op != ops[i]) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
+    if (ops[i]->ctx->device != ops[0]->ctx->device) return fail(CMM_ERR_ARG, "batch spans devices");
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return fail(CMM_ERR_ARG, "an operator appears twice in the batch");
+  }
+  if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace != 0)
+    return fail(CMM_ERR_ARG, "bad batch solve options (residual replacement is per solve)");
+  CMM_CUDA(cudaSetDevice(ops[0]->ctx->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t main_st = ops[0]->ctx->stream;
+  std::vector<SolveBufs> vb(n);
+  std::vector<SolverDev*> dst(n);
+  std::vector<bool> flex(n);
+  // per-solve set-up on each solve's own stream
+  for (int i = 0; i < n; ++i) {
+    cmm_op* op = ops[i];
+    const int64_t m = (int64_t)op->pt->ncomp * op->pt->npix;
+    cudaStream_t st = op->ctx->stream;
+    if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (5 * m + 3 * kRedBlocks)));
+    if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
+    SolveBufs& v = vb[i];
+    v.r = op->sol;
+    v.z = v.r + m;
+    v.p = v.z + m;
+    v.q = v.p + m;
+    v.r_old = v.q + m;
+    v.p1 = v.r_old + m;
+    v.p2 = v.p1 + kRedBlocks;
+    v.p3 = v.p2 + kRedBlocks;
+    dst[i] = (SolverDev*)op->sol_state;
+    flex[i] = opts->flexible != 0 || pcs[i]->kind == CMM_PRECON_CIRC_LEARNED;
+    double bnorm2 = 0.0;
+    CMM_TRY(cmm_dot(op, b[i], b[i], m, &bnorm2));
+    SolverDev h{};
+    h.bnorm2 = bnorm2 > 0 ? bnorm2 : 1.0;
+    h.tol = opts->tol;
+    h.maxit = opts->maxit;
+    h.f32 = opts->cg_f32 ? 1 : 0;
+    CMM_CUDA(cudaMemcpyAsync(dst[i], &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    if (opts->x0_given) {
+      CMM_TRY(apply_A_dev(op, x[i], v.q));
+    } else {
+      CMM_CUDA(cudaMemsetAsync(x[i], 0, sizeof(double) * m, st));
+      CMM_CUDA(cudaMemsetAsync(v.q, 0, sizeof(double) * m, st));
+    }
+    CMM_TRY(launch_residual(v.r, b[i], v.q, m, dst[i], v.p2, st));
+    CMM_CUDA(cudaMemcpyAsync(v.r_old, v.r, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    CMM_TRY(precon_step(op, pcs[i], v, dst[i], false));
+    CMM_TRY(launch_solver_init(dst[i], v.p1, v.p2, nullptr, st));
+    CMM_CUDA(cudaMemcpyAsync(v.p, v.z, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    op->done = &dst[i]->done;
+  }
+  for (int i = 0; i < n; ++i) CMM_CUDA(cudaStreamSynchronize(ops[i]->ctx->stream));
+  const int per = std::max(1, opts->check_every);
+  // one graph per `per` batch iterations: every solve is a parallel branch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  int status = [&]() -> int {
+    for (auto& e : ev) CMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CMM_CUDA(cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal));
+    int s2 = CMM_OK;
+    cudaError_t e = cudaEventRecord(ev[n], main_st);
+    for (int i = 0; i < n && s2 == CMM_OK && e == cudaSuccess; ++i) {
+      cudaStream_t st = ops[i]->ctx->stream;
+      if (st != main_st) e = cudaStreamWaitEvent(st, ev[n], 0);
+      for (int k = 0; k < per && s2 == CMM_OK && e == cudaSuccess; ++k)
+        s2 = solve_iteration(ops[i], pcs[i], x[i], vb[i], dst[i], nullptr, nullptr, flex[i]);
+      if (e == cudaSuccess && st != main_st) {
+        e = cudaEventRecord(ev[i], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main_st, ev[i], 0);
+      }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(main_st, &graph);
+    if (s2 != CMM_OK) return s2;
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph capture", __FILE__, __LINE__);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+    CMM_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    return CMM_OK;
+  }();
+  if (graph) cudaGraphDestroy(graph);
+  std::vector<SolverDev> hs(n);
+  SolverDev* pinned = nullptr;
+  if (status == CMM_OK && cudaMallocHost(&pinned, sizeof(SolverDev) * n) != cudaSuccess)
+    status = fail(CMM_ERR_OOM, "pinned allocation failed");
+  int launched = 0;
+  while (status == CMM_OK) {
+    cudaError_t e = cudaGraphLaunch(exec, main_st);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(pinned + i, dst[i], sizeof(SolverDev), cudaMemcpyDeviceToHost, main_st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main_st);
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "batch solve", __FILE__, __LINE__);
+      break;
+    }
+    launched += per;
+    bool all = true;
+    for (int i = 0; i < n; ++i) all = all && pinned[i].done;
+    if (all || launched > opts->maxit + per) break;
+  }
+  for (int i = 0; i < n; ++i) ops[i]->done = nullptr;
+  if (exec) cudaGraphExecDestroy(exec);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (status == CMM_OK)
+    for (int i = 0; i < n; ++i) {
+      infos[i].iterations = pinned[i].iter;
+      infos[i].status = pinned[i].status;
+      infos[i].rel_resid = pinned[i].rel;
+      infos[i].seconds = secs;
+    }
+  if (pinned) cudaFreeHost(pinned);
+  return status;
 }
 
 }  // extern "C"

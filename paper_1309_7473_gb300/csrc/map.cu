@@ -226,6 +226,14 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
 }
 
 // ------------------------------------------------------------------ PCG state machine
+// With st->f32 the CG vectors, dot products and scalars are rounded to FP32
+// (the FP32-CG precision mode); the operator and preconditioner are unchanged.
+__device__ __forceinline__ double cg_round(const SolverDev* st, double v) { return st->f32 ? (double)(float)v : v; }
+
+__device__ __forceinline__ double cg_acc(const SolverDev* st, double acc, double term) {
+  return st->f32 ? (double)((float)acc + (float)term) : acc + term;
+}
+
 __global__ void k_solver_alpha(SolverDev* st, const double* __restrict__ partial, double* anorm_terms) {
   if (st->done) return;
   const double pq = block_sum_all(partial, kRedBlocks);
@@ -237,23 +245,36 @@ __global__ void k_solver_alpha(SolverDev* st, const double* __restrict__ partial
       st->alpha = 0.0;
       return;
     }
-    st->alpha = st->rho / pq;
+    st->alpha = cg_round(st, st->rho / pq);
     if (anorm_terms) anorm_terms[st->iter] = st->alpha * st->rho;
   }
 }
 
-__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, long long n, const SolverDev* st,
-                            double* __restrict__ partial) {
+__global__ void k_dot_partial_cg(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                 const SolverDev* st, double* __restrict__ partial) {
+  if (st->done) return;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc = cg_acc(st, acc, x[i] * y[i]);
+  block_sum_store(acc, partial);
+}
+
+// x += alpha p; r -= alpha q (r_old keeps the previous residual for flexible CG)
+__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, double* __restrict__ r_old,
+                            const double* __restrict__ p, const double* __restrict__ q, long long n,
+                            const SolverDev* st, double* __restrict__ partial) {
   if (st->done) return;
   const double alpha = st->alpha;
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
+    x[i] = cg_round(st, x[i] + alpha * p[i]);
+    const double r0 = r[i];
+    if (r_old) r_old[i] = r0;
+    const double ri = cg_round(st, r0 - alpha * q[i]);
     r[i] = ri;
-    acc += ri * ri;
+    acc = cg_acc(st, acc, ri * ri);
   }
   block_sum_store(acc, partial);
 }
@@ -280,16 +301,41 @@ __global__ void k_solver_check(SolverDev* st, const double* __restrict__ partial
   }
 }
 
-__global__ void k_solver_beta(SolverDev* st, const double* __restrict__ partial) {
+// After z = M r: round z (FP32 CG), partials of r^T z and, for flexible CG, of
+// z^T (r - r_old).
+__global__ void k_solver_z(double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ r_old,
+                           long long n, const SolverDev* st, double* __restrict__ p_rz,
+                           double* __restrict__ p_flex) {
   if (st->done) return;
-  const double rz = block_sum_all(partial, kRedBlocks);
+  double a1 = 0.0, a2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double zi = cg_round(st, z[i]);
+    z[i] = zi;
+    const double ri = r[i];
+    a1 = cg_acc(st, a1, ri * zi);
+    if (r_old) a2 = cg_acc(st, a2, zi * (ri - r_old[i]));
+  }
+  block_sum_store(a1, p_rz);
+  if (r_old) {
+    __syncthreads();
+    block_sum_store(a2, p_flex);
+  }
+}
+
+// beta = rz_new / rz (Fletcher-Reeves form of PCG) or z^T (r - r_old) / rz (flexible)
+__global__ void k_solver_beta(SolverDev* st, const double* __restrict__ p_rz, const double* __restrict__ p_flex) {
+  if (st->done) return;
+  const double rz = block_sum_all(p_rz, kRedBlocks);
+  double fl = 0.0;
+  if (p_flex) fl = block_sum_all(p_flex, kRedBlocks);
   if (threadIdx.x == 0) {
-    if (!(rz > 0.0) || !isfinite(rz)) {
+    if (!(rz > 0.0) || !isfinite(rz) || !isfinite(fl)) {
       st->status = CMM_ERR_BREAKDOWN;
       st->done = 1;
       return;
     }
-    st->beta = rz / st->rho;
+    st->beta = cg_round(st, (p_flex ? fl : rz) / st->rho);
     st->rho = rz;
   }
 }
@@ -300,7 +346,7 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z,
   const double beta = st->beta;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+    p[i] = cg_round(st, z[i] + beta * p[i]);
 }
 
 // Initialisation after r0, z0 are known: rho = r^T z (partial), bnorm2 set by host.
@@ -326,6 +372,34 @@ __global__ void k_solver_init(SolverDev* st, const double* __restrict__ partial_
     } else if (st->maxit <= 0) {
       st->done = 1;
     }
+  }
+}
+
+// Residual replacement: r = b - A x (already in q as A x), rounded for FP32 CG.
+__global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q,
+                           long long n, const SolverDev* st, double* __restrict__ partial) {
+  if (st->done) return;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double ri = cg_round(st, b[i] - q[i]);
+    r[i] = ri;
+    acc = cg_acc(st, acc, ri * ri);
+  }
+  block_sum_store(acc, partial);
+}
+
+// After a residual replacement: rho = r^T z of the new residual.
+__global__ void k_solver_rho(SolverDev* st, const double* __restrict__ p_rz) {
+  if (st->done) return;
+  const double rz = block_sum_all(p_rz, kRedBlocks);
+  if (threadIdx.x == 0) {
+    if (!(rz > 0.0) || !isfinite(rz)) {
+      st->status = CMM_ERR_BREAKDOWN;
+      st->done = 1;
+      return;
+    }
+    st->rho = rz;
   }
 }
 
@@ -663,9 +737,36 @@ int launch_solver_alpha(SolverDev* st, const double* partial, double* anorm, cud
   return CMM_OK;
 }
 
-int launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const SolverDev* st,
-                     double* partial, cudaStream_t s) {
-  k_update_xr<<<kRedBlocks, 256, 0, s>>>(x, r, p, q, n, st, partial);
+int launch_update_xr(double* x, double* r, double* r_old, const double* p, const double* q, int64_t n,
+                     const SolverDev* st, double* partial, cudaStream_t s) {
+  k_update_xr<<<kRedBlocks, 256, 0, s>>>(x, r, r_old, p, q, n, st, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_dot_partial_cg(const double* x, const double* y, int64_t n, const SolverDev* st, double* partial,
+                          cudaStream_t s) {
+  k_dot_partial_cg<<<kRedBlocks, 256, 0, s>>>(x, y, n, st, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_solver_z(double* z, const double* r, const double* r_old, int64_t n, const SolverDev* st,
+                    double* p_rz, double* p_flex, cudaStream_t s) {
+  k_solver_z<<<kRedBlocks, 256, 0, s>>>(z, r, r_old, n, st, p_rz, p_flex);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_residual(double* r, const double* b, const double* q, int64_t n, const SolverDev* st, double* partial,
+                    cudaStream_t s) {
+  k_residual<<<kRedBlocks, 256, 0, s>>>(r, b, q, n, st, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_solver_rho(SolverDev* st, const double* p_rz, cudaStream_t s) {
+  k_solver_rho<<<1, 256, 0, s>>>(st, p_rz);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
@@ -676,8 +777,8 @@ int launch_solver_check(SolverDev* st, const double* partial, double* hist, cuda
   return CMM_OK;
 }
 
-int launch_solver_beta(SolverDev* st, const double* partial, cudaStream_t s) {
-  k_solver_beta<<<1, 256, 0, s>>>(st, partial);
+int launch_solver_beta(SolverDev* st, const double* p_rz, const double* p_flex, cudaStream_t s) {
+  k_solver_beta<<<1, 256, 0, s>>>(st, p_rz, p_flex);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }

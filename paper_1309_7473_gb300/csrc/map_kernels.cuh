@@ -11,6 +11,7 @@ namespace cmm {
 struct SolverDev {
   double rho, pq, alpha, beta, rr, rel, bnorm2, tol;
   int iter, maxit, done, status;
+  int f32;        // FP32 CG vectors and scalars
 };
 
 struct Fft2Plan {
@@ -56,10 +57,17 @@ int launch_dot_partial(const double* x, const double* y, int64_t n, double* part
 int launch_copy_sub(double* dst, const double* a, const double* b, int64_t n, cudaStream_t s);
 int launch_solver_init(SolverDev* st, const double* prz, const double* prr, double* hist, cudaStream_t s);
 int launch_solver_alpha(SolverDev* st, const double* partial, double* anorm, cudaStream_t s);
-int launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const SolverDev* st,
-                     double* partial, cudaStream_t s);
+int launch_update_xr(double* x, double* r, double* r_old, const double* p, const double* q, int64_t n,
+                     const SolverDev* st, double* partial, cudaStream_t s);
+int launch_dot_partial_cg(const double* x, const double* y, int64_t n, const SolverDev* st, double* partial,
+                          cudaStream_t s);
+int launch_solver_z(double* z, const double* r, const double* r_old, int64_t n, const SolverDev* st,
+                    double* p_rz, double* p_flex, cudaStream_t s);
+int launch_residual(double* r, const double* b, const double* q, int64_t n, const SolverDev* st, double* partial,
+                    cudaStream_t s);
+int launch_solver_rho(SolverDev* st, const double* p_rz, cudaStream_t s);
 int launch_solver_check(SolverDev* st, const double* partial, double* hist, cudaStream_t s);
-int launch_solver_beta(SolverDev* st, const double* partial, cudaStream_t s);
+int launch_solver_beta(SolverDev* st, const double* p_rz, const double* p_flex, cudaStream_t s);
 int launch_update_p(double* p, const double* z, int64_t n, const SolverDev* st, cudaStream_t s);
 
 template <typename T> int fft2_plan_init(Fft2Plan& p, int ny, int nx);

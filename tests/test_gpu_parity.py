@@ -283,3 +283,104 @@ def test_full_size_symmetry_and_rhs(cmm, ctx):
     b1 = host(op.rhs(op.project(m, dtype=torch.float32)))
     b2 = host(op.apply(m))
     assert rel(b1, b2) < 1e-5
+
+
+# ---------------------------------------------------------------- precision modes (config 3)
+
+@pytest.fixture(scope="module")
+def cfg1_solution():
+    """Config 1, noise-free data: the FP64 oracle's tightly converged solution."""
+    scan, noise = gen.config1()
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=1)
+    d = om.project(oop, m)
+    b = om.rhs(oop, d)
+    x, info = om.pcg(lambda v: om.apply_A(oop, v), om.BlockPrecon(oop), b, tol=1e-11, maxit=2000)
+    assert info.converged
+    return scan, noise, d, b, x, info
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("cg_f32", [False, True])
+def test_precision_grid_config1(cmm, ctx, cfg1_solution, prec, cg_f32):
+    """TOD/filter in FP32 or BF16 storage x CG in FP64 or FP32 with residual
+    replacement every 50 iterations: converges to 1e-6 with the stated errors."""
+    scan, noise, d, b_ref, x_ref, info_ref = cfg1_solution
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    b = op.rhs(torch.as_tensor(d, dtype=torch.float32, device="cuda:0"))
+    pc = cmm.Precon(op, cmm.PRECON_BINNED)
+    x, info, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=600, cg_f32=cg_f32,
+                              resid_replace=50 if cg_f32 else 0)
+    assert info.status == 0
+    err = rel(host(x), x_ref)
+    _, io = om.pcg(lambda v: om.apply_A(om.make_operator(scan, noise), v), om.BlockPrecon(om.make_operator(scan, noise)),
+                   b_ref, tol=1e-6, maxit=600)
+    assert abs(info.iterations - io.iterations) <= 0.2 * io.iterations + 2
+    assert err < (2e-5 if prec == 1 else 2e-2)
+
+
+def test_flexible_cg_matches_pcg_gpu(cmm, ctx, cfg1_solution):
+    scan, noise, d, b_ref, x_ref, _ = cfg1_solution
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    pc = cmm.Precon(op, cmm.PRECON_BINNED)
+    b = dev(b_ref)
+    x1, i1, _, _ = cmm.solve(op, pc, b, tol=1e-9, maxit=600)
+    x2, i2, _, _ = cmm.solve(op, pc, b, tol=1e-9, maxit=600, flexible=True)
+    assert i1.status == 0 and i2.status == 0
+    assert abs(i1.iterations - i2.iterations) <= 1
+    assert rel(host(x2), host(x1)) < 1e-7
+    assert rel(host(x1), x_ref) < 1e-6
+
+
+# ---------------------------------------------------------------- batched solves and tuning (config 4)
+
+def test_batch_solve_matches_individual_solves(cmm):
+    """Uneven problems solved together in one graph per check interval give the same
+    iterates as solving each alone (FP64), and the oracle's solutions."""
+    probs = []
+    for k, (ny, nx, log_nt, ncols) in enumerate([(16, 20, 12, 3), (24, 18, 13, 4), (12, 12, 11, 2)]):
+        scan = gen.small_scan(cfg=220 + k, ny=ny, nx=nx, n_t=1 << log_nt, ncols=ncols, nrows=2,
+                              throw_px=1.5 * nx)
+        noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=220 + k)
+        probs.append((scan, noise))
+    ops, pcs, bs, xs, refs = [], [], [], [], []
+    for k, (scan, noise) in enumerate(probs):
+        ctx = cmm.Context(0)
+        op = cmm.Operator(ctx, scan, noise, precision=0)
+        oop = om.make_operator(scan, noise)
+        b_ref = om.apply_A(oop, gen.sky_map(scan.ny, scan.nx, cfg=230 + k))
+        kind = cmm.PRECON_CIRCULANT if k != 1 else cmm.PRECON_BINNED
+        pc = cmm.Precon(op, kind, taper_sigma_px=4.0)
+        ops.append(op)
+        pcs.append(pc)
+        bs.append(dev(b_ref))
+        xs.append(op.new_map())
+        mo = om.CirculantPrecon(oop, taper_sigma=4.0) if k != 1 else om.BlockPrecon(oop)
+        refs.append(om.pcg(lambda v, oop=oop: om.apply_A(oop, v), mo, b_ref, tol=1e-9, maxit=500))
+    infos = cmm.cmm_batch_solve([o.h for o in ops], [p.h for p in pcs], bs, xs, tol=1e-9, maxit=500,
+                                check_every=7)
+    for k in range(len(ops)):
+        xi, ii, _, _ = cmm.solve(ops[k], pcs[k], bs[k], tol=1e-9, maxit=500)
+        assert infos[k].status == 0 and ii.status == 0
+        assert infos[k].iterations == ii.iterations
+        assert rel(host(xs[k]), host(xi)) < 1e-12
+        xo, io = refs[k]
+        assert abs(infos[k].iterations - io.iterations) <= max(2, 0.1 * io.iterations)
+        assert rel(host(xs[k]), xo) < 1e-6
+
+
+def test_autotune_keeps_parity(cmm, ctx, tmp_path):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=1)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=1)
+    ref = om.apply_A(oop, m)
+    cache = str(tmp_path / "tune.txt")
+    lr, ms = cmm.cmm_autotune(op.h, 3, cache)
+    assert 6 <= lr <= 8 and ms > 0
+    assert rel(host(op.apply(dev(m))), ref) < TOL[1]
+    op2 = cmm.Operator(ctx, scan, noise, precision=1)
+    lr2, ms2 = cmm.cmm_autotune(op2.h, 3, cache)
+    assert lr2 == lr and ms2 == -1.0
+    assert rel(host(op2.apply(dev(m))), ref) < TOL[1]
+    assert open(cache).read().split()[-1] == str(lr)
