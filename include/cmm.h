@@ -63,6 +63,7 @@ typedef struct cmm_pointing cmm_pointing;
 typedef struct cmm_noise cmm_noise;
 typedef struct cmm_op cmm_op;
 typedef struct cmm_precon cmm_precon;
+typedef struct cmm_unet cmm_unet;
 
 /* Map geometry: ny rows of nx pixels, ncomp Stokes components (1 or 3);
  * periodic != 0 wraps pixel indices instead of cutting samples that fall off
@@ -86,6 +87,8 @@ typedef struct {
   int32_t cg_f32;      /* != 0: CG vectors, dot products and scalars rounded to FP32 */
   int32_t resid_replace; /* > 0: every that many iterations r = b - A x is recomputed */
   int32_t flexible;    /* != 0: flexible CG, beta = z^T (r - r_old) / (z_old^T r_old) */
+  int32_t snapshot_every; /* with a snapshot buffer: keep (x_k, r_k) every that many iterations */
+  int32_t snapshot_max;   /* number of snapshot slots */
 } cmm_solve_opts;
 
 typedef struct {
@@ -193,6 +196,18 @@ int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm
 int cmm_precon_destroy(cmm_precon* pc);
 /* z = M r: device double [ncomp][ny][nx] each. */
 int cmm_precon_apply(cmm_precon* pc, const double* r, double* z);
+/* Attach (net != NULL) or detach the learned correction of a circulant
+ * preconditioner: z = M_C r is followed by z <- mask (z + ||z|| U(z / ||z||)) with
+ * the U-Net `net` (same context and map shape, TQU), and the kind becomes
+ * CIRC_LEARNED (solved with flexible CG).  The paper has no learned component. */
+int cmm_precon_set_correction(cmm_precon* pc, cmm_unet* net);
+/* Training pairs for the learned correction from `count` snapshots (x_k, r_k) of a
+ * solve (layout of cmm_solve's snapshot buffer) and its converged solution x_star:
+ * with z = M r_k (this preconditioner), inputs[k] = z / ||z|| and targets[k] =
+ * (x_star - x_k - z) / ||z|| (device FP32 [count][ncomp][ny][nx]).  Since
+ * A (x_star - x_k) = r_k, the target is what the correction should add. */
+int cmm_harvest_pairs(cmm_precon* pc, const double* snapshots, int32_t count, const double* x_star,
+                      float* inputs, float* targets);
 /* Number of Fourier modes whose eigenvalues were floored (circulant), else 0. */
 int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped);
 
@@ -202,12 +217,44 @@ int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped);
  * solution (and holds x0 if opts->x0_given).  resid_hist (device double
  * [maxit + 1], may be NULL) receives ||r_k|| / ||b||; anorm_terms (device double
  * [maxit], may be NULL) receives alpha_k r_k^T z_k, whose sums over the next d
- * steps estimate the squared error A-norm (Results footnote).  Waits for the
- * result; info->status reports convergence.
+ * steps estimate the squared error A-norm (Results footnote).  snapshots (device
+ * double [snapshot_max][2][ncomp*ny*nx], may be NULL) receives (x_k, r_k) at
+ * k = 0, snapshot_every, 2 snapshot_every, ... (the paper writes intermediate maps
+ * every 5 steps, Sec. Test setup).  Waits for the result; info->status reports
+ * convergence.  A CIRC_LEARNED preconditioner always runs flexible CG.
  */
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x,
               const cmm_solve_opts* opts, double* resid_hist, double* anorm_terms,
-              cmm_solve_info* info);
+              double* snapshots, cmm_solve_info* info);
+
+/* ---------------------------------------------------------------- learned correction
+ * A U-Net (no counterpart in the paper) that refines the circulant preconditioner
+ * inside flexible CG.  widths[levels] (levels 1..4): encoder level l has two 3x3
+ * convolutions with ReLU to widths[l] channels and 2x2 average pooling between
+ * levels; decoder level l has a 2x2 stride-2 transposed convolution, the
+ * concatenation [up, skip] and two 3x3 convolutions with ReLU; a 1x1 convolution
+ * maps widths[0] to 3 channels.  Weights and activations are BF16, accumulation,
+ * biases and gradients FP32.  Parameters are one flat FP32 vector, per layer
+ * weights then biases, conv weights [cout][cin][k][k], transposed [cin][cout][2][2].
+ * Maps are FP32 device arrays [batch][3][ny][nx], nx <= 64, ny and nx divisible by
+ * 2^(levels-1).  Training minimises 0.5 mean((U(in) - target)^2) with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).
+ */
+int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const int32_t* widths,
+                    int32_t batch_max, cmm_unet** out);
+int cmm_unet_destroy(cmm_unet* net);
+int cmm_unet_param_count(cmm_unet* net, int64_t* n);
+/* Copies FP32 parameters (device) in, refreshes the BF16 copy, resets Adam. */
+int cmm_unet_set_params(cmm_unet* net, const float* params);
+int cmm_unet_get_params(cmm_unet* net, float* params);
+int cmm_unet_forward(cmm_unet* net, int32_t batch, const float* in, float* out);
+/* Loss and its gradient w.r.t. the parameters (grad: device FP32 [n], may be NULL);
+ * *loss_host (may be NULL) receives the loss and makes the call wait. */
+int cmm_unet_loss_grad(cmm_unet* net, int32_t batch, const float* in, const float* target, float* grad,
+                       double* loss_host);
+/* One Adam step with learning rate lr on the batch. */
+int cmm_unet_train_step(cmm_unet* net, int32_t batch, const float* in, const float* target, float lr,
+                        double* loss_host);
 
 /* ---------------------------------------------------------------- batches and tuning
  * Batched solves (many Monte-Carlo realisations or patches of uneven size): n

@@ -42,7 +42,8 @@ class PreconOpts(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
-                ("resid_replace", C.c_int32), ("flexible", C.c_int32)]
+                ("resid_replace", C.c_int32), ("flexible", C.c_int32), ("snapshot_every", C.c_int32),
+                ("snapshot_max", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -78,7 +79,17 @@ _SIGS = {
     "cmm_precon_destroy": [_vp],
     "cmm_precon_apply": [_vp, _vp, _vp],
     "cmm_precon_clamped": [_vp, C.POINTER(_i64)],
-    "cmm_solve": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveInfo)],
+    "cmm_solve": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), _vp, _vp, _vp, C.POINTER(SolveInfo)],
+    "cmm_precon_set_correction": [_vp, _vp],
+    "cmm_harvest_pairs": [_vp, _vp, _i32, _vp, _vp, _vp],
+    "cmm_unet_create": [_vp, _i32, _i32, _i32, _vp, _i32, _PP],
+    "cmm_unet_destroy": [_vp],
+    "cmm_unet_param_count": [_vp, C.POINTER(_i64)],
+    "cmm_unet_set_params": [_vp, _vp],
+    "cmm_unet_get_params": [_vp, _vp],
+    "cmm_unet_forward": [_vp, _i32, _vp, _vp],
+    "cmm_unet_loss_grad": [_vp, _i32, _vp, _vp, _vp, C.POINTER(_d)],
+    "cmm_unet_train_step": [_vp, _i32, _vp, _vp, C.c_float, C.POINTER(_d)],
     "cmm_batch_solve": [_i32, _vp, _vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)],
     "cmm_autotune": [_vp, _i32, C.c_char_p, C.POINTER(_i32), C.POINTER(_d)],
 }
@@ -253,14 +264,78 @@ def cmm_precon_clamped(pc):
 
 
 def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
-              resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False):
+              resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False,
+              snapshots=None, snapshot_every=1):
+    snap_max = 0 if snapshots is None else snapshots.shape[0]
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0,
-                     1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0)
+                     1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0, int(snapshot_every),
+                     int(snap_max))
     info = SolveInfo()
     _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
                           _dev(resid_hist, numel=None, name="resid_hist"),
-                          _dev(anorm_terms, numel=None, name="anorm_terms"), C.byref(info)))
+                          _dev(anorm_terms, numel=None, name="anorm_terms"),
+                          _dev(snapshots, name="snapshots"), C.byref(info)))
     return info
+
+
+def cmm_harvest_pairs(pc, snapshots, count, x_star, inputs, targets):
+    import torch
+    _check(_lib.cmm_harvest_pairs(pc, _dev(snapshots, torch.float64, name="snapshots"), int(count),
+                                  _dev(x_star, torch.float64, name="x_star"), _dev(inputs, torch.float32, name="inputs"),
+                                  _dev(targets, torch.float32, name="targets")))
+
+
+def cmm_precon_set_correction(pc, net):
+    _check(_lib.cmm_precon_set_correction(pc, net))
+
+
+def cmm_unet_create(ctx, ny, nx, widths, batch_max):
+    w = (C.c_int32 * len(widths))(*widths)
+    h = C.c_void_p()
+    _check(_lib.cmm_unet_create(ctx, ny, nx, len(widths), w, batch_max, C.byref(h)))
+    return h
+
+
+def cmm_unet_destroy(h):
+    _check(_lib.cmm_unet_destroy(h))
+
+
+def cmm_unet_param_count(h):
+    n = C.c_int64()
+    _check(_lib.cmm_unet_param_count(h, C.byref(n)))
+    return int(n.value)
+
+
+def cmm_unet_set_params(h, params):
+    import torch
+    _check(_lib.cmm_unet_set_params(h, _dev(params, torch.float32, name="params")))
+
+
+def cmm_unet_get_params(h, params):
+    import torch
+    _check(_lib.cmm_unet_get_params(h, _dev(params, torch.float32, name="params")))
+
+
+def cmm_unet_forward(h, x, out):
+    import torch
+    _check(_lib.cmm_unet_forward(h, x.shape[0], _dev(x, torch.float32, name="in"), _dev(out, torch.float32, name="out")))
+
+
+def cmm_unet_loss_grad(h, x, target, grad=None):
+    import torch
+    loss = C.c_double()
+    _check(_lib.cmm_unet_loss_grad(h, x.shape[0], _dev(x, torch.float32, name="in"),
+                                   _dev(target, torch.float32, name="target"),
+                                   _dev(grad, torch.float32, name="grad"), C.byref(loss)))
+    return loss.value
+
+
+def cmm_unet_train_step(h, x, target, lr):
+    import torch
+    loss = C.c_double()
+    _check(_lib.cmm_unet_train_step(h, x.shape[0], _dev(x, torch.float32, name="in"),
+                                    _dev(target, torch.float32, name="target"), float(lr), C.byref(loss)))
+    return loss.value
 
 
 def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f32=False, flexible=False):
@@ -384,6 +459,37 @@ class Precon:
     def __del__(self):
         if getattr(self, "h", None):
             cmm_precon_destroy(self.h)
+            self.h = None
+
+
+class UNet:
+    """Owner of a cmm_unet handle (the learned correction of the circulant preconditioner)."""
+
+    def __init__(self, ctx: Context, ny, nx, widths=(16, 32, 48, 96), batch_max=32):
+        self.ctx = ctx
+        self.shape = (3, ny, nx)
+        self.widths = tuple(widths)
+        self.h = cmm_unet_create(ctx.h, ny, nx, widths, batch_max)
+        self.n_params = cmm_unet_param_count(self.h)
+
+    def set_params(self, params):
+        cmm_unet_set_params(self.h, params)
+
+    def params(self):
+        import torch
+        p = torch.empty(self.n_params, dtype=torch.float32, device=f"cuda:{self.ctx.device}")
+        cmm_unet_get_params(self.h, p)
+        return p
+
+    def __call__(self, x):
+        import torch
+        out = torch.empty_like(x, dtype=torch.float32)
+        cmm_unet_forward(self.h, x, out)
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            cmm_unet_destroy(self.h)
             self.h = None
 
 

@@ -84,6 +84,22 @@ __global__ void k_rot2(const int4* __restrict__ bore, long long n, float2* __res
 
 __global__ void k_set_unit(double* __restrict__ v, long long idx) { v[idx] = 1.0; }
 
+// inputs = z / ||z||, targets = (x* - x_k - z) / ||z|| (FP32), ||z||^2 from partials
+__global__ void k_pair(const double* __restrict__ z, const double* __restrict__ xs, const double* __restrict__ xk,
+                       const double* __restrict__ partial, float* __restrict__ in, float* __restrict__ tgt, long long n) {
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kRedBlocks; ++k) s += partial[k];
+    s_inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    in[t] = (float)(z[t] * s_inv);
+    tgt[t] = (float)((xs[t] - xk[t] - z[t]) * s_inv);
+  }
+}
+
 }  // namespace cmm
 
 using namespace cmm;
@@ -101,6 +117,7 @@ struct cmm_precon {
   int64_t n_clamped = 0;
   int64_t ref = -1;
   double taper = 0.0;
+  cmm_unet* unet = nullptr;    // learned correction (CIRC_LEARNED)
 };
 
 extern "C" {
@@ -685,6 +702,12 @@ static int precon_apply_dev(cmm_precon* pc, const double* r, double* z, double* 
     case CMM_PRECON_CIRCULANT:
       return op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, partial, done)
                                       : circulant_apply<float>(pc, r, z, partial, done);
+    case CMM_PRECON_CIRC_LEARNED:
+      CMM_TRY(op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, nullptr, done)
+                                       : circulant_apply<float>(pc, r, z, nullptr, done));
+      CMM_TRY(unet_correct(pc->unet, z, op->pt->mask, npix, nc, done, st));
+      if (partial) CMM_TRY(launch_dot_partial(r, z, nc * npix, partial, done, st));
+      return CMM_OK;
     default:
       CMM_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * nc * npix, cudaMemcpyDeviceToDevice, st));
       if (partial) CMM_TRY(launch_dot_partial(r, z, nc * npix, partial, done, st));
@@ -697,6 +720,43 @@ int cmm_precon_apply(cmm_precon* pc, const double* r, double* z) {
   if (r == z) return fail(CMM_ERR_ARG, "r and z must not alias");
   CMM_CUDA(cudaSetDevice(pc->op->ctx->device));
   return precon_apply_dev(pc, r, z, nullptr, nullptr);
+}
+
+int cmm_precon_set_correction(cmm_precon* pc, cmm_unet* net) {
+  if (!pc) return fail(CMM_ERR_ARG, "null preconditioner");
+  if (pc->kind != CMM_PRECON_CIRCULANT && pc->kind != CMM_PRECON_CIRC_LEARNED)
+    return fail(CMM_ERR_ARG, "the learned correction follows the circulant preconditioner");
+  if (!net) {
+    pc->unet = nullptr;
+    pc->kind = CMM_PRECON_CIRCULANT;
+    return CMM_OK;
+  }
+  if (!unet_matches(net, pc->op->ctx, pc->op->pt->ny, pc->op->pt->nx) || pc->op->pt->ncomp != 3)
+    return fail(CMM_ERR_ARG, "the U-Net must share the operator's context and its TQU map shape");
+  pc->unet = net;
+  pc->kind = CMM_PRECON_CIRC_LEARNED;
+  return CMM_OK;
+}
+
+int cmm_harvest_pairs(cmm_precon* pc, const double* snapshots, int32_t count, const double* x_star, float* inputs,
+                      float* targets) {
+  if (!pc || !snapshots || !x_star || !inputs || !targets || count < 0) return fail(CMM_ERR_ARG, "bad argument");
+  cmm_op* op = pc->op;
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = op->ctx->stream;
+  const long long n = (long long)op->pt->ncomp * op->pt->npix;
+  double* z = op->tmp_b;
+  for (int k = 0; k < count; ++k) {
+    const double* xk = snapshots + (long long)k * 2 * n;
+    const double* rk = xk + n;
+    CMM_TRY(precon_apply_dev(pc, rk, z, nullptr, nullptr));
+    CMM_TRY(launch_dot_partial(z, z, n, op->ctx->d_partial, nullptr, st));
+    k_pair<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(z, x_star, xk, op->ctx->d_partial,
+                                                                             inputs + (long long)k * n,
+                                                                             targets + (long long)k * n, n);
+    CMM_LAUNCH_CHECK();
+  }
+  return CMM_OK;
 }
 
 int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped) {
@@ -719,8 +779,13 @@ static int precon_step(cmm_op* op, cmm_precon* pc, const SolveBufs& v, SolverDev
   return launch_solver_z(v.z, v.r, flexible ? v.r_old : nullptr, n, dst, v.p1, flexible ? v.p3 : nullptr, st);
 }
 
+struct Snap {
+  double* buf = nullptr;
+  int every = 0, max = 0;
+};
+
 static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBufs& v, SolverDev* dst,
-                           double* hist, double* anorm, bool flexible) {
+                           double* hist, double* anorm, bool flexible, const Snap& snap = Snap()) {
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   cudaStream_t st = op->ctx->stream;
   CMM_TRY(apply_A_dev(op, v.p, v.q));
@@ -728,6 +793,7 @@ static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBuf
   CMM_TRY(launch_solver_alpha(dst, v.p1, anorm, st));
   CMM_TRY(launch_update_xr(x, v.r, flexible ? v.r_old : nullptr, v.p, v.q, n, dst, v.p2, st));
   CMM_TRY(launch_solver_check(dst, v.p2, hist, st));
+  if (snap.buf) CMM_TRY(launch_snapshot(x, v.r, n, dst, snap.every, snap.max, snap.buf, st));
   CMM_TRY(precon_step(op, pc, v, dst, flexible));
   CMM_TRY(launch_solver_beta(dst, v.p1, flexible ? v.p3 : nullptr, st));
   CMM_TRY(launch_update_p(v.p, v.z, n, dst, st));
@@ -735,8 +801,15 @@ static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBuf
 }
 
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_solve_opts* opts,
-              double* resid_hist, double* anorm_terms, cmm_solve_info* info) {
+              double* resid_hist, double* anorm_terms, double* snapshots, cmm_solve_info* info) {
   if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
+  if (snapshots && (opts->snapshot_every < 1 || opts->snapshot_max < 1)) return fail(CMM_ERR_ARG, "bad snapshot options");
+  Snap snap;
+  if (snapshots) {
+    snap.buf = snapshots;
+    snap.every = opts->snapshot_every;
+    snap.max = opts->snapshot_max;
+  }
   if (pc->op != op) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
   if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace < 0) return fail(CMM_ERR_ARG, "bad solve options");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
@@ -785,6 +858,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   CMM_CUDA(cudaMemcpyAsync(v.r_old, v.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   CMM_TRY(precon_step(op, pc, v, dst, false));
   CMM_TRY(launch_solver_init(dst, v.p1, v.p2, resid_hist, st));
+  if (snap.buf) CMM_TRY(launch_snapshot(x, v.r, n, dst, snap.every, snap.max, snap.buf, st));
   CMM_CUDA(cudaMemcpyAsync(v.p, v.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   int per = std::max(1, opts->check_every);
   if (opts->resid_replace > 0) per = std::min(per, opts->resid_replace);
@@ -798,7 +872,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
       CMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       int s2 = CMM_OK;
       for (int i = 0; i < per && s2 == CMM_OK; ++i)
-        s2 = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible);
+        s2 = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap);
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       if (s2 != CMM_OK) return s2;
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
@@ -818,7 +892,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
       }
     } else {
       for (int i = 0; i < per && status == CMM_OK; ++i)
-        status = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible);
+        status = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap);
       if (status != CMM_OK) break;
     }
     launched += per;

@@ -150,6 +150,11 @@ int op_init_twiddles(cmm_op* op);
 int op_prepare_kernels(cmm_op* op);
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
 
+// ---- learned correction (unet.cu)
+int unet_correct(cmm_unet* u, double* z, const uint8_t* mask, int64_t npix, int ncomp, const int* done,
+                 cudaStream_t st);
+bool unet_matches(const cmm_unet* u, const cmm_ctx* ctx, int ny, int nx);
+
 // ---- launchers implemented in map.cu
 int launch_mask_from_hits(cmm_pointing* pt, const double* blocks);
 int launch_block_inverse(int ncomp, int64_t npix, const double* blocks, const uint8_t* mask,

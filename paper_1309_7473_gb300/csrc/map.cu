@@ -375,6 +375,22 @@ __global__ void k_solver_init(SolverDev* st, const double* __restrict__ partial_
   }
 }
 
+// Iterate snapshots: at iterations k = 0, every, 2 every, ... (slot k / every < max)
+// (x_k, r_k) are copied to snaps[slot][0] and snaps[slot][1].
+__global__ void k_snapshot(const double* __restrict__ x, const double* __restrict__ r, long long n,
+                           const SolverDev* st, int every, int max, double* __restrict__ snaps) {
+  const int it = st->iter;
+  if (it % every) return;
+  const int slot = it / every;
+  if (slot >= max) return;
+  double* dst = snaps + (long long)slot * 2 * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    dst[i] = x[i];
+    dst[n + i] = r[i];
+  }
+}
+
 // Residual replacement: r = b - A x (already in q as A x), rounded for FP32 CG.
 __global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q,
                            long long n, const SolverDev* st, double* __restrict__ partial) {
@@ -761,6 +777,13 @@ int launch_solver_z(double* z, const double* r, const double* r_old, int64_t n, 
 int launch_residual(double* r, const double* b, const double* q, int64_t n, const SolverDev* st, double* partial,
                     cudaStream_t s) {
   k_residual<<<kRedBlocks, 256, 0, s>>>(r, b, q, n, st, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_snapshot(const double* x, const double* r, int64_t n, const SolverDev* st, int every, int max,
+                    double* snaps, cudaStream_t s) {
+  k_snapshot<<<grid_for(n), 256, 0, s>>>(x, r, n, st, every, max, snaps);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }

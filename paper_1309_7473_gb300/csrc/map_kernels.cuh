@@ -66,6 +66,8 @@ int launch_solver_z(double* z, const double* r, const double* r_old, int64_t n, 
 int launch_residual(double* r, const double* b, const double* q, int64_t n, const SolverDev* st, double* partial,
                     cudaStream_t s);
 int launch_solver_rho(SolverDev* st, const double* p_rz, cudaStream_t s);
+int launch_snapshot(const double* x, const double* r, int64_t n, const SolverDev* st, int every, int max,
+                    double* snaps, cudaStream_t s);
 int launch_solver_check(SolverDev* st, const double* partial, double* hist, cudaStream_t s);
 int launch_solver_beta(SolverDev* st, const double* p_rz, const double* p_flex, cudaStream_t s);
 int launch_update_p(double* p, const double* z, int64_t n, const SolverDev* st, cudaStream_t s);

@@ -1,0 +1,157 @@
+"""The learned correction: GPU U-Net forward and gradients against the FP64
+oracle, training, and flexible PCG with M_C followed by the trained network
+against plain PCG with M_C on held-out configuration-1 realisations.
+
+Tolerances: the GPU network keeps weights and activations in BF16 (8 mantissa
+bits, relative rounding 2^-9 = 2e-3 per stored value) with FP32 accumulation;
+over ~20 layers the output error against an FP64 evaluation of the same
+(BF16-rounded) weights is a few 1e-3 relative, so outputs are compared at 3e-2
+and gradients by cosine similarity >= 0.999 and relative L2 error <= 5e-2.
+"""
+import numpy as np
+import pytest
+
+import gen
+from oracle import mapmaker as om
+from oracle import unet as ou
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+WIDTHS = (16, 32, 48, 96)
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm as c
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(cmm):
+    return cmm.Context(0)
+
+
+def bf16_round(a):
+    """Round float values to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def rounded_params(p, widths):
+    """Weights rounded to BF16 as the GPU stores them; biases kept in FP32."""
+    q = p.astype(np.float32).astype(np.float64)
+    o = 0
+    for kind, ci, co in ou.layer_specs(widths):
+        nw = int(np.prod(ou.weight_shape(kind, ci, co)))
+        q[o:o + nw] = bf16_round(q[o:o + nw])
+        o += nw + co
+    return q
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_param_count(cmm, ctx):
+    net = cmm.UNet(ctx, 64, 64, WIDTHS, batch_max=4)
+    assert net.n_params == ou.param_count(WIDTHS) == 299651
+
+
+@pytest.mark.parametrize("widths,hw", [(WIDTHS, 64), ((8, 12), 32)])
+def test_unet_forward_and_gradient_match_oracle(cmm, ctx, widths, hw):
+    g = np.random.default_rng(5)
+    p = ou.init_params(widths, seed=11)
+    p += 0.02 * g.standard_normal(p.size)
+    # make the output layer as large as the others so the comparison is not trivial
+    B = 2
+    x = g.standard_normal((B, 3, hw, hw))
+    t = g.standard_normal((B, 3, hw, hw)) * 0.1
+    net = cmm.UNet(ctx, hw, hw, widths, batch_max=B)
+    pt = torch.as_tensor(p, dtype=torch.float32, device="cuda:0")
+    net.set_params(pt)
+    xt = torch.as_tensor(x, dtype=torch.float32, device="cuda:0")
+    tt = torch.as_tensor(t, dtype=torch.float32, device="cuda:0")
+    y = net(xt).cpu().numpy()
+    pr = rounded_params(p, widths)
+    xr = bf16_round(x)
+    y_ref = ou.forward(pr, xr, widths)
+    assert rel(y, y_ref) < 3e-2
+    grad = torch.zeros_like(pt)
+    loss = cmm.cmm_unet_loss_grad(net.h, xt, tt, grad)
+    loss_ref, grad_ref = ou.loss_and_grad(pr, xr, t.astype(np.float32).astype(np.float64), widths)
+    assert loss == pytest.approx(loss_ref, rel=3e-2)
+    gg = grad.cpu().numpy().astype(np.float64)
+    cos = float(gg @ grad_ref / (np.linalg.norm(gg) * np.linalg.norm(grad_ref)))
+    assert cos >= 0.999
+    assert rel(gg, grad_ref) <= 5e-2
+
+
+def test_training_reduces_loss(cmm, ctx):
+    g = np.random.default_rng(6)
+    widths = (8, 12)
+    net = cmm.UNet(ctx, 32, 32, widths, batch_max=8)
+    net.set_params(torch.as_tensor(ou.init_params(widths, seed=1), dtype=torch.float32, device="cuda:0"))
+    x = torch.as_tensor(g.standard_normal((8, 3, 32, 32)), dtype=torch.float32, device="cuda:0")
+    t = torch.as_tensor(0.3 * g.standard_normal((8, 3, 32, 32)), dtype=torch.float32, device="cuda:0") + 0.5 * x
+    l0 = cmm.cmm_unet_loss_grad(net.h, x, t)
+    for _ in range(200):
+        cmm.cmm_unet_train_step(net.h, x, t, 3e-3)
+    l1 = cmm.cmm_unet_loss_grad(net.h, x, t)
+    assert l1 < 0.6 * l0
+
+
+def realisation(scan, noise, oop, real):
+    m = gen.sky_map(scan.ny, scan.nx, cfg=5, real=real)
+    d = om.project(oop, m) + gen.noise_tod(noise, scan.n_t, scan.f_samp, cfg=5, real=real)
+    return d
+
+
+def test_learned_correction_gain_config1(cmm, ctx):
+    """Config 5 (reduced): pairs from FP64 M_C solves of 6 seeded config-1
+    realisations, a short training, then flexible PCG with M_C + U against PCG
+    with M_C on two held-out realisations: fewer iterations to 1e-6, and the
+    solution agrees with the FP64 oracle's."""
+    from paper_1309_7473_gb300 import learned
+    scan, noise = gen.config1()
+    oop = om.make_operator(scan, noise)
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+    ins, tgts = [], []
+    for real in range(6):
+        d = torch.as_tensor(realisation(scan, noise, oop, real), device="cuda:0")
+        b = op.rhs(d)
+        i, t, info = learned.harvest_pairs(op, pc, b, max_iter=200)
+        assert info.status == 0
+        ins.append(i)
+        tgts.append(t)
+    ins = torch.cat(ins)
+    tgts = torch.cat(tgts)
+    net = cmm.UNet(ctx, 64, 64, WIDTHS, batch_max=32)
+    net.set_params(torch.as_tensor(ou.init_params(WIDTHS, seed=2), dtype=torch.float32, device="cuda:0"))
+    hist = learned.train(net, ins, tgts, epochs=8, batch=32, lr=1e-3)
+    assert hist[-1][1] < hist[0][1]
+    gains = []
+    for real in (100, 101):
+        d_np = realisation(scan, noise, oop, real)
+        b = op.rhs(torch.as_tensor(d_np, device="cuda:0"))
+        x0, i0, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=500)
+        pcl = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+        cmm.cmm_precon_set_correction(pcl.h, net.h)
+        x1, i1, _, _ = cmm.solve(op, pcl, b, tol=1e-6, maxit=500)
+        assert i0.status == 0 and i1.status == 0
+        b_ref = om.rhs(oop, d_np)
+        xo, io = om.pcg(lambda v: om.apply_A(oop, v), om.CirculantPrecon(oop, taper_sigma=8.0), b_ref,
+                        tol=1e-10, maxit=2000)
+        assert rel(x1.cpu().numpy(), xo) < 1e-4
+        assert rel(x0.cpu().numpy(), xo) < 1e-4
+        gains.append((i0.iterations, i1.iterations))
+    print("iterations plain M_C vs learned:", gains)
+    assert sum(g[1] for g in gains) < sum(g[0] for g in gains)
