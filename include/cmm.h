@@ -10,7 +10,11 @@
  *   the last error of the calling thread is returned by cmm_last_error().
  * - Handles (cmm_ctx, cmm_pointing, cmm_noise, cmm_op, cmm_precon) are created and
  *   freed by the library; each *_destroy frees the device memory the handle owns.
- *   Handles must be destroyed before the context they were made from.
+ *   A handle keeps the handles it was made from alive (an operator its context,
+ *   pointing and noise; a preconditioner its operator and correction network), so
+ *   handles may be destroyed in any order: memory is released when the last
+ *   handle that needs it is destroyed.  Destroying a handle twice is an error the
+ *   library cannot detect.
  * - "host" arguments are ordinary host memory that the call reads (or writes)
  *   before it returns.  "device" arguments are caller-owned device memory on the
  *   context's device, at least 16-byte aligned; the library never frees them.

@@ -66,6 +66,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra += os.environ.get("CMM_NVCC_FLAGS", "").split()   # developer tuning hook (e.g. -DCMM_FILTER_MINB=3)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))

@@ -84,6 +84,18 @@ __global__ void k_rot2(const int4* __restrict__ bore, long long n, float2* __res
 
 __global__ void k_set_unit(double* __restrict__ v, long long idx) { v[idx] = 1.0; }
 
+}  // namespace cmm
+
+extern "C" {
+static void free_ctx(cmm_ctx* c);
+}
+
+namespace cmm {
+void ctx_retain(cmm_ctx* c) { c->refs++; }
+void ctx_release(cmm_ctx* c) {
+  if (--c->refs == 0) free_ctx(c);
+}
+
 // inputs = z / ||z||, targets = (x* - x_k - z) / ||z|| (FP32), ||z||^2 from partials
 __global__ void k_pair(const double* __restrict__ z, const double* __restrict__ xs, const double* __restrict__ xk,
                        const double* __restrict__ partial, float* __restrict__ in, float* __restrict__ tgt, long long n) {
@@ -105,6 +117,7 @@ __global__ void k_pair(const double* __restrict__ z, const double* __restrict__ 
 using namespace cmm;
 
 struct cmm_precon {
+  int refs = 1;
   cmm_op* op = nullptr;
   int kind = 0;
   double* inv = nullptr;       // binned / Jacobi: inverse blocks
@@ -156,8 +169,7 @@ int cmm_ctx_create(int device, void* stream, cmm_ctx** out) {
   return CMM_OK;
 }
 
-int cmm_ctx_destroy(cmm_ctx* c) {
-  if (!c) return CMM_OK;
+static void free_ctx(cmm_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_partial);
@@ -165,12 +177,15 @@ int cmm_ctx_destroy(cmm_ctx* c) {
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+int cmm_ctx_destroy(cmm_ctx* c) {
+  if (c) ctx_release(c);
   return CMM_OK;
 }
 
 // ------------------------------------------------------------------ pointing
-int cmm_pointing_destroy(cmm_pointing* pt) {
-  if (!pt) return CMM_OK;
+static void free_pointing(cmm_pointing* pt) {
   cudaSetDevice(pt->ctx->device);
   cudaStreamSynchronize(pt->ctx->stream);
   dfree(pt->bore);
@@ -179,7 +194,17 @@ int cmm_pointing_destroy(cmm_pointing* pt) {
   dfree(pt->det_pol32);
   dfree(pt->rot2);
   dfree(pt->mask);
+  cmm_ctx* c = pt->ctx;
   delete pt;
+  ctx_release(c);
+}
+
+static void pointing_release(cmm_pointing* pt) {
+  if (--pt->refs == 0) free_pointing(pt);
+}
+
+int cmm_pointing_destroy(cmm_pointing* pt) {
+  if (pt) pointing_release(pt);
   return CMM_OK;
 }
 
@@ -204,6 +229,7 @@ int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, c
   CMM_CUDA(cudaSetDevice(ctx->device));
   cmm_pointing* pt = new cmm_pointing();
   pt->ctx = ctx;
+  ctx_retain(ctx);
   pt->ny = geom->ny;
   pt->nx = geom->nx;
   pt->ncomp = geom->ncomp;
@@ -263,14 +289,23 @@ int cmm_pointing_mask(cmm_pointing* pt, uint8_t* mask_host, int64_t* n_good) {
 }
 
 // ------------------------------------------------------------------ noise
-int cmm_noise_destroy(cmm_noise* nz) {
-  if (!nz) return CMM_OK;
+static void free_noise(cmm_noise* nz) {
   cudaSetDevice(nz->ctx->device);
   cudaStreamSynchronize(nz->ctx->stream);
   dfree(nz->coef64);
   dfree(nz->coef32);
   dfree(nz->diag);
+  cmm_ctx* c = nz->ctx;
   delete nz;
+  ctx_release(c);
+}
+
+static void noise_release(cmm_noise* nz) {
+  if (--nz->refs == 0) free_noise(nz);
+}
+
+int cmm_noise_destroy(cmm_noise* nz) {
+  if (nz) noise_release(nz);
   return CMM_OK;
 }
 
@@ -295,6 +330,7 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
   CMM_CUDA(cudaSetDevice(ctx->device));
   cmm_noise* nz = new cmm_noise();
   nz->ctx = ctx;
+  ctx_retain(ctx);
   nz->n_det = n_det;
   nz->n_t = n_samp;
   nz->f_samp = f_samp;
@@ -332,8 +368,7 @@ int cmm_noise_diag(cmm_noise* nz, double* diag_host) {
 }
 
 // ------------------------------------------------------------------ operator
-int cmm_op_destroy(cmm_op* op) {
-  if (!op) return CMM_OK;
+static void free_op(cmm_op* op) {
   cudaSetDevice(op->ctx->device);
   cudaStreamSynchronize(op->ctx->stream);
   dfree(op->spec);
@@ -345,7 +380,21 @@ int cmm_op_destroy(cmm_op* op) {
   dfree(op->tmp_b);
   dfree(op->sol);
   dfree(op->sol_state);
+  cmm_ctx* c = op->ctx;
+  cmm_pointing* pt = op->pt;
+  cmm_noise* nz = op->nz;
   delete op;
+  pointing_release(pt);
+  noise_release(nz);
+  ctx_release(c);
+}
+
+static void op_release(cmm_op* op) {
+  if (--op->refs == 0) free_op(op);
+}
+
+int cmm_op_destroy(cmm_op* op) {
+  if (op) op_release(op);
   return CMM_OK;
 }
 
@@ -363,6 +412,9 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   op->ctx = ctx;
   op->pt = pt;
   op->nz = nz;
+  ctx_retain(ctx);
+  pt->refs++;
+  nz->refs++;
   op->prec = precision;
   op->N = n_t / 2;
   int logN = 0;
@@ -532,6 +584,7 @@ int cmm_dot(cmm_op* op, const double* x, const double* y, int64_t n, double* res
 // ------------------------------------------------------------------ preconditioners
 int cmm_precon_destroy(cmm_precon* pc) {
   if (!pc) return CMM_OK;
+  if (--pc->refs > 0) return CMM_OK;
   cudaSetDevice(pc->op->ctx->device);
   cudaStreamSynchronize(pc->op->ctx->stream);
   dfree(pc->inv);
@@ -541,7 +594,11 @@ int cmm_precon_destroy(cmm_precon* pc) {
   dfree(pc->planes);
   dfree(pc->tmp);
   dfree(pc->plan.tw);
+  cmm_op* op = pc->op;
+  cmm_unet* net = pc->unet;
   delete pc;
+  if (net) unet_release(net);
+  op_release(op);
   return CMM_OK;
 }
 
@@ -639,6 +696,7 @@ int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   cmm_precon* pc = new cmm_precon();
   pc->op = op;
+  op->refs++;
   pc->kind = kind;
   cmm_pointing* pt = op->pt;
   const int nb = pt->ncomp == 1 ? 1 : 6;
@@ -705,7 +763,7 @@ static int precon_apply_dev(cmm_precon* pc, const double* r, double* z, double* 
     case CMM_PRECON_CIRC_LEARNED:
       CMM_TRY(op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, nullptr, done)
                                        : circulant_apply<float>(pc, r, z, nullptr, done));
-      CMM_TRY(unet_correct(pc->unet, z, op->pt->mask, npix, nc, done, st));
+      CMM_TRY(unet_correct(pc->unet, r, z, op->pt->mask, npix, nc, done, st));
       if (partial) CMM_TRY(launch_dot_partial(r, z, nc * npix, partial, done, st));
       return CMM_OK;
     default:
@@ -727,12 +785,15 @@ int cmm_precon_set_correction(cmm_precon* pc, cmm_unet* net) {
   if (pc->kind != CMM_PRECON_CIRCULANT && pc->kind != CMM_PRECON_CIRC_LEARNED)
     return fail(CMM_ERR_ARG, "the learned correction follows the circulant preconditioner");
   if (!net) {
+    if (pc->unet) unet_release(pc->unet);
     pc->unet = nullptr;
     pc->kind = CMM_PRECON_CIRCULANT;
     return CMM_OK;
   }
   if (!unet_matches(net, pc->op->ctx, pc->op->pt->ny, pc->op->pt->nx) || pc->op->pt->ncomp != 3)
     return fail(CMM_ERR_ARG, "the U-Net must share the operator's context and its TQU map shape");
+  unet_retain(net);
+  if (pc->unet) unet_release(pc->unet);
   pc->unet = net;
   pc->kind = CMM_PRECON_CIRC_LEARNED;
   return CMM_OK;

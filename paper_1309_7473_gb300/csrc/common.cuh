@@ -66,6 +66,7 @@ struct Scratch {
 }  // namespace cmm
 
 struct cmm_ctx {
+  int refs = 1;                // owner reference + one per dependent handle
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -75,6 +76,7 @@ struct cmm_ctx {
 };
 
 struct cmm_pointing {
+  int refs = 1;                // owner reference + one per dependent handle
   cmm_ctx* ctx = nullptr;
   int ny = 0, nx = 0, ncomp = 0, periodic = 0;
   int n_det = 0;
@@ -88,6 +90,7 @@ struct cmm_pointing {
 };
 
 struct cmm_noise {
+  int refs = 1;                // owner reference + one per dependent handle
   cmm_ctx* ctx = nullptr;
   int n_det = 0;
   int64_t n_t = 0;
@@ -100,6 +103,7 @@ struct cmm_noise {
 };
 
 struct cmm_op {
+  int refs = 1;                // owner reference + one per dependent handle
   cmm_ctx* ctx = nullptr;
   cmm_pointing* pt = nullptr;
   cmm_noise* nz = nullptr;
@@ -150,9 +154,16 @@ int op_init_twiddles(cmm_op* op);
 int op_prepare_kernels(cmm_op* op);
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
 
+// ---- handle lifetimes: a handle stays alive while handles made from it exist, so
+// they may be destroyed in any order (api.cu, unet.cu)
+void ctx_retain(cmm_ctx* c);
+void ctx_release(cmm_ctx* c);
+void unet_retain(cmm_unet* u);
+void unet_release(cmm_unet* u);
+
 // ---- learned correction (unet.cu)
-int unet_correct(cmm_unet* u, double* z, const uint8_t* mask, int64_t npix, int ncomp, const int* done,
-                 cudaStream_t st);
+int unet_correct(cmm_unet* u, const double* r, double* z, const uint8_t* mask, int64_t npix, int ncomp,
+                 const int* done, cudaStream_t st);
 bool unet_matches(const cmm_unet* u, const cmm_ctx* ctx, int ny, int nx);
 
 // ---- launchers implemented in map.cu

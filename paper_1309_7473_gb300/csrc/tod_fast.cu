@@ -28,7 +28,22 @@
 
 namespace cmm {
 
-constexpr int kDetsPerCta = 2;
+// Tuning knobs (compile-time; the defaults are the measured best on GB300).
+#ifndef CMM_DETS_PER_CTA
+#define CMM_DETS_PER_CTA 2
+#endif
+#ifndef CMM_COL_THREADS_PER_SM
+#define CMM_COL_THREADS_PER_SM 768
+#endif
+#ifndef CMM_FILTER_MINB
+#define CMM_FILTER_MINB 2
+#endif
+#ifndef CMM_GEN_UNROLL
+#define CMM_GEN_UNROLL 2
+#endif
+
+constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
+constexpr int kGenUnroll = CMM_GEN_UNROLL;
 constexpr int kFlushDets = 128;
 constexpr int kE = 16;     // elements per thread in the column FFT
 
@@ -38,7 +53,7 @@ constexpr int kE = 16;     // elements per thread in the column FFT
 template <int R> struct ColShape {
   static constexpr int J = R >= 256 ? 16 : 32;
   static constexpr int THREADS = J * R / kE;
-  static constexpr int MINB = 768 / THREADS;
+  static constexpr int MINB = CMM_COL_THREADS_PER_SM / THREADS > 0 ? CMM_COL_THREADS_PER_SM / THREADS : 1;
 };
 
 // GB300's FP64 unit also executes int <-> float conversions, at a small fraction
@@ -135,7 +150,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
     // samples into the tile (the previous detector's last reads are fenced first)
     __syncthreads();
-#pragma unroll 2
+#pragma unroll kGenUnroll
     for (int e = 0; e < kE; ++e) {
       const long long j = (long long)c + ((long long)(i + e * TPC) << a.logC);
       ad.st(i + e * TPC, make_float2(project_fast<NC>(a, off, pol, 2 * j), project_fast<NC>(a, off, pol, 2 * j + 1)));
@@ -159,7 +174,7 @@ template <int C, int E> struct FilterShape {
   static constexpr int TPR = C / E;
   static constexpr int THREADS = 2 * TPR > 256 ? 2 * TPR : 256;
   static constexpr int ROWS = THREADS / TPR;
-  static constexpr int MINB = THREADS > 256 ? 1 : 2;
+  static constexpr int MINB = THREADS > 256 ? 1 : CMM_FILTER_MINB;
 };
 
 template <typename S, int E, int... RC>

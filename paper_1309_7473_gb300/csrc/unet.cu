@@ -400,19 +400,43 @@ __global__ void k_corr_prep(const double* __restrict__ z, const double* __restri
     in[t] = (float)(z[t] * inv);
 }
 
+// Per-block sums of r.z and r.y over unmasked entries (z: M_C r, y: the network
+// output); written to partial[kRedBlocks + b] and partial[2 kRedBlocks + b].
+__global__ void k_corr_dots(const double* __restrict__ r, const double* __restrict__ z, const float* __restrict__ y,
+                            const uint8_t* __restrict__ mask, long long npix, int ncomp, double* __restrict__ partial,
+                            const int* done) {
+  if (stopped(done)) return;
+  const long long n = npix * ncomp;
+  double rz = 0.0, ry = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    if (mask[t % npix]) {
+      rz += r[t] * z[t];
+      ry += r[t] * (double)y[t];
+    }
+  block_sum_store(rz, partial + kRedBlocks);
+  block_sum_store(ry, partial + 2 * kRedBlocks);
+}
+
+// z <- mask(z + theta s y), s = ||z||.  theta = 1 unless that would leave
+// r.z_new < kCorrKeep r.z; then theta shrinks the correction to make
+// r.z_new = kCorrKeep r.z, so the corrected direction stays a descent direction
+// whatever the network outputs (flexible CG needs r.z > 0 to make progress).
+constexpr double kCorrKeep = 0.25;
+
 __global__ void k_corr_apply(double* __restrict__ z, const double* __restrict__ partial, const float* __restrict__ out,
                              const uint8_t* __restrict__ mask, long long npix, int ncomp, const int* done) {
   if (stopped(done)) return;
-  __shared__ double s_norm;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kRedBlocks; ++k) s += partial[k];
-    s_norm = s > 0.0 ? sqrt(s) : 1.0;
-  }
-  __syncthreads();
+  const double zz = block_sum_all(partial, kRedBlocks);
+  const double rz = block_sum_all(partial + kRedBlocks, kRedBlocks);
+  const double ry = block_sum_all(partial + 2 * kRedBlocks, kRedBlocks);
+  const double s = zz > 0.0 ? sqrt(zz) : 1.0;
+  double theta = 1.0;
+  if (rz > 0.0 && rz + s * ry < kCorrKeep * rz) theta = (kCorrKeep - 1.0) * rz / (s * ry);
+  if (!(rz > 0.0)) theta = 0.0;
+  const double f = theta * s;
   const long long n = npix * ncomp;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    z[t] = mask[t % npix] ? z[t] + s_norm * (double)out[t] : 0.0;
+    z[t] = mask[t % npix] ? z[t] + f * (double)out[t] : 0.0;
 }
 
 }  // namespace cmm
@@ -429,6 +453,7 @@ struct Layer {
 }  // namespace
 
 struct cmm_unet {
+  int refs = 1;
   cmm_ctx* ctx = nullptr;
   int ny = 0, nx = 0, L = 0, batch_max = 0;
   int widths[4] = {0, 0, 0, 0};
@@ -650,8 +675,7 @@ int unet_backward(cmm_unet* u, int B) {
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
-int cmm_unet_destroy(cmm_unet* u) {
-  if (!u) return CMM_OK;
+static void free_unet(cmm_unet* u) {
   cudaSetDevice(u->ctx->device);
   cudaStreamSynchronize(u->ctx->stream);
   for (void* p : {(void*)u->master, (void*)u->wbf, (void*)u->grad, (void*)u->m, (void*)u->v, (void*)u->x_in,
@@ -662,7 +686,24 @@ int cmm_unet_destroy(cmm_unet* u) {
       if (p) cudaFree(p);
   for (auto* p : u->gskip)
     if (p) cudaFree(p);
+  cmm_ctx* c = u->ctx;
   delete u;
+  ctx_release(c);
+}
+
+}  // extern "C"
+
+namespace cmm {
+void unet_retain(cmm_unet* u) { u->refs++; }
+void unet_release(cmm_unet* u) {
+  if (--u->refs == 0) free_unet(u);
+}
+}  // namespace cmm
+
+extern "C" {
+
+int cmm_unet_destroy(cmm_unet* u) {
+  if (u) unet_release(u);
   return CMM_OK;
 }
 
@@ -679,6 +720,7 @@ int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const 
   CMM_CUDA(cudaSetDevice(ctx->device));
   cmm_unet* u = new cmm_unet();
   u->ctx = ctx;
+  ctx_retain(ctx);
   u->ny = ny;
   u->nx = nx;
   u->L = levels;
@@ -697,7 +739,7 @@ int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const 
   A(&u->v, sizeof(float) * u->n_params);
   A(&u->x_in, sizeof(bf16) * B * 3 * ny * nx);
   A(&u->y_out, sizeof(float) * B * 3 * ny * nx);
-  A(&u->partial, sizeof(double) * kRedBlocks);
+  A(&u->partial, sizeof(double) * 3 * kRedBlocks);
   long long gmax = 3;
   u->enc_a.assign(levels, nullptr);
   u->enc_b.assign(levels, nullptr);
@@ -815,8 +857,8 @@ bool unet_matches(const cmm_unet* u, const cmm_ctx* ctx, int ny, int nx) {
 }
 
 // z <- mask (z + ||z|| U(z / ||z||)) for a batch of one map, all on the device.
-int unet_correct(cmm_unet* u, double* z, const uint8_t* mask, int64_t npix, int ncomp, const int* done,
-                 cudaStream_t st) {
+int unet_correct(cmm_unet* u, const double* r, double* z, const uint8_t* mask, int64_t npix, int ncomp,
+                 const int* done, cudaStream_t st) {
   if (ncomp != 3 || npix != (int64_t)u->ny * u->nx) return fail(CMM_ERR_ARG, "U-Net shape does not match the map");
   const long long n = 3 * npix;
   CMM_TRY(launch_dot_partial(z, z, n, u->partial, done, st));
@@ -826,6 +868,8 @@ int unet_correct(cmm_unet* u, double* z, const uint8_t* mask, int64_t npix, int 
   k_to_bf16<<<grid_n(n), 256, 0, st>>>(in, u->x_in, n, done);
   CMM_LAUNCH_CHECK();
   CMM_TRY(unet_forward(u, 1, done));
+  k_corr_dots<<<kRedBlocks, 256, 0, st>>>(r, z, u->y_out, mask, npix, ncomp, u->partial, done);
+  CMM_LAUNCH_CHECK();
   k_corr_apply<<<grid_n(n), 256, 0, st>>>(z, u->partial, u->y_out, mask, npix, ncomp, done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;

@@ -99,6 +99,29 @@ def test_apply_A_small(cmm, ctx, prec, ncomp, chunk):
     assert rel(y, om.apply_A(oop, m)) < TOL[prec]
 
 
+def test_handles_destroyed_out_of_order(cmm):
+    """An operator and preconditioner stay usable after the context, pointing and
+    noise handles they were made from are destroyed first."""
+    scan, noise = small(3)
+    c = cmm.Context(0)
+    op = cmm.Operator(c, scan, noise, precision=0)
+    pc = cmm.Precon(op, cmm.PRECON_BINNED)
+    for owner in (c, op.pointing, op.noise):
+        {cmm.Context: cmm.cmm_ctx_destroy, cmm.Pointing: cmm.cmm_pointing_destroy,
+         cmm.Noise: cmm.cmm_noise_destroy}[type(owner)](owner.h)
+        owner.h = None
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=203)[0]
+    y = host(op.apply(dev(m)))
+    assert rel(y, om.apply_A(oop, m)) < TOL[0]
+    cmm.cmm_op_destroy(op.h)
+    op.h = None
+    z = host(pc.apply(dev(y)))
+    assert np.isfinite(z).all()
+    cmm.cmm_precon_destroy(pc.h)
+    pc.h = None
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_apply_A_periodic(cmm, ctx, prec):
     scan, noise = small(3, periodic=True)
