@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--taper", type=float, default=20.0)
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-6 solves")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", choices=["apply", "learned"], default="apply",
+                    help="apply: the A-application inside circulant PCG (default); learned: the learned "
+                         "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
+    ap.add_argument("--learned-reals", type=int, default=100)
+    ap.add_argument("--learned-epochs", type=int, default=15)
     return ap.parse_args()
 
 
@@ -274,6 +279,68 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_learned(args):
+    """Learned correction on the 32-detector 64x64 patch: pairs from FP64 M_C solves
+    (to 1e-12) of the first 90% of the training realisations, Adam on the U-Net,
+    then PCG(M_C) and flexible PCG(M_C + U) to 1e-6 on 20 held-out realisations."""
+    import torch
+
+    import gen
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm, learned
+    widths = (16, 32, 48, 96)
+    ctx = cmm.Context(0)
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F64)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+
+    def rhs(real):
+        m = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=5, real=real), device="cuda:0")
+        d = op.project(m, dtype=torch.float64)
+        d += torch.as_tensor(gen.noise_tod(noise, scan.n_t, scan.f_samp, cfg=5, real=real), device="cuda:0")
+        return op.rhs(d)
+
+    t0 = time.perf_counter()
+    n_train = max(1, (9 * args.learned_reals) // 10)
+    parts = [learned.harvest_pairs(op, pc, rhs(r), max_iter=200, tol=1e-12)[:2] for r in range(args.learned_reals)]
+    torch.cuda.synchronize()
+    harvest_s = time.perf_counter() - t0
+    ti = torch.cat([p[0] for p in parts[:n_train]])
+    tt = torch.cat([p[1] for p in parts[:n_train]])
+    vi = torch.cat([p[0] for p in parts[n_train:]]) if n_train < len(parts) else ti[:32]
+    vt = torch.cat([p[1] for p in parts[n_train:]]) if n_train < len(parts) else tt[:32]
+    ti, tt = torch.cat([ti, -ti]), torch.cat([tt, -tt])      # the ideal correction is odd in its input
+    net = cmm.UNet(ctx, scan.ny, scan.nx, widths, batch_max=32)
+    net.init(seed=2)
+    t0 = time.perf_counter()
+    hist = learned.train(net, ti, tt, epochs=args.learned_epochs, batch=32, lr=1e-3, val=(vi, vt))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    pcl = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+    cmm.cmm_precon_set_correction(pcl.h, net.h)
+    rows = []
+    for real in range(10_000, 10_020):
+        b = rhs(real)
+        _, i0, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=1000)
+        _, i1, _, _ = cmm.solve(op, pcl, b, tol=1e-6, maxit=1000)
+        rows.append((i0.iterations, i0.seconds, i1.iterations, i1.seconds, i1.status))
+    n = len(rows)
+    return {
+        "metric": "iterations to 1e-6, flexible PCG(M_C + U-Net) vs PCG(M_C)", "unit": "iterations",
+        "higher_is_better": False, "value": sum(r[2] for r in rows) / n, "n_gpus": 1, "steps": n,
+        "warmup": 0, "dtype": "f64 solve, bf16 network", "data": "synthetic",
+        "config": {"workload": "32 det x 2^16 samples, 64x64 TQU, taper 8 px; U-Net widths 16/32/48/96",
+                   "realisations": args.learned_reals, "train_realisations": n_train,
+                   "pairs_train": int(ti.shape[0]), "epochs": args.learned_epochs},
+        "plain_mc": {"iterations_mean": sum(r[0] for r in rows) / n, "seconds_mean": sum(r[1] for r in rows) / n},
+        "learned": {"iterations_mean": sum(r[2] for r in rows) / n, "seconds_mean": sum(r[3] for r in rows) / n,
+                    "all_converged": all(r[4] == 0 for r in rows)},
+        "val_loss": {"zero_output": float(0.5 * (vt.double() ** 2).mean()), "trained": hist[-1][2]},
+        "harvest_seconds": round(harvest_s, 2), "train_seconds": round(train_s, 2),
+    }
+
+
 def op_chunk(op, scan, args):
     if args.det_chunk > 0:
         return args.det_chunk
@@ -307,6 +374,10 @@ def main():
             "data": "synthetic", "config": workload(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+    if args.workload == "learned":
+        if rank == 0:
+            print(json.dumps(run_learned(args)))
         return 0
     if world > 1:
         import torch

@@ -251,6 +251,11 @@ int cmm_unet_param_count(cmm_unet* net, int64_t* n);
 /* Copies FP32 parameters (device) in, refreshes the BF16 copy, resets Adam. */
 int cmm_unet_set_params(cmm_unet* net, const float* params);
 int cmm_unet_get_params(cmm_unet* net, float* params);
+/* Seeded He-normal initialisation (std sqrt(2 / fan_in), fan_in = c_in x kernel
+ * taps; zero biases; the output layer scaled by 1e-2 so that an untrained
+ * correction starts near zero); resets Adam.  Draws on the host (64-bit Mersenne
+ * twister), uploads, and waits. */
+int cmm_unet_init(cmm_unet* net, uint64_t seed);
 int cmm_unet_forward(cmm_unet* net, int32_t batch, const float* in, float* out);
 /* Loss and its gradient w.r.t. the parameters (grad: device FP32 [n], may be NULL);
  * *loss_host (may be NULL) receives the loss and makes the call wait. */

@@ -87,6 +87,7 @@ _SIGS = {
     "cmm_unet_param_count": [_vp, C.POINTER(_i64)],
     "cmm_unet_set_params": [_vp, _vp],
     "cmm_unet_get_params": [_vp, _vp],
+    "cmm_unet_init": [_vp, C.c_uint64],
     "cmm_unet_forward": [_vp, _i32, _vp, _vp],
     "cmm_unet_loss_grad": [_vp, _i32, _vp, _vp, _vp, C.POINTER(_d)],
     "cmm_unet_train_step": [_vp, _i32, _vp, _vp, C.c_float, C.POINTER(_d)],
@@ -311,6 +312,10 @@ def cmm_unet_set_params(h, params):
     _check(_lib.cmm_unet_set_params(h, _dev(params, torch.float32, name="params")))
 
 
+def cmm_unet_init(h, seed=0):
+    _check(_lib.cmm_unet_init(h, int(seed)))
+
+
 def cmm_unet_get_params(h, params):
     import torch
     _check(_lib.cmm_unet_get_params(h, _dev(params, torch.float32, name="params")))
@@ -474,6 +479,9 @@ class UNet:
 
     def set_params(self, params):
         cmm_unet_set_params(self.h, params)
+
+    def init(self, seed=0):
+        cmm_unet_init(self.h, seed)
 
     def params(self):
         import torch

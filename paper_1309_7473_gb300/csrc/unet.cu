@@ -11,6 +11,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -791,6 +793,31 @@ int cmm_unet_set_params(cmm_unet* u, const float* params) {
   CMM_CUDA(cudaMemsetAsync(u->v, 0, sizeof(float) * u->n_params, st));
   u->step = 0;
   return CMM_OK;
+}
+
+int cmm_unet_init(cmm_unet* u, uint64_t seed) {
+  if (!u) return fail(CMM_ERR_ARG, "null argument");
+  std::vector<float> h((size_t)u->n_params, 0.0f);
+  std::mt19937_64 gen(seed);
+  std::normal_distribution<double> normal(0.0, 1.0);
+  for (size_t i = 0; i < u->layers.size(); ++i) {
+    const Layer& a = u->layers[i];
+    const long long fan_in = (long long)a.cin * (a.kind == 0 ? 9 : a.kind == 1 ? 4 : 1);
+    const long long nw = a.boff - a.woff;
+    const double scale = std::sqrt(2.0 / (double)fan_in) * (i + 1 == u->layers.size() ? 1e-2 : 1.0);
+    for (long long k = 0; k < nw; ++k) h[a.woff + k] = (float)(normal(gen) * scale);
+  }
+  float* d = nullptr;
+  CMM_CUDA(cudaSetDevice(u->ctx->device));
+  CMM_CUDA(cudaMalloc(&d, sizeof(float) * u->n_params));
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(float) * u->n_params, cudaMemcpyHostToDevice, u->ctx->stream);
+  int st = e == cudaSuccess ? cmm_unet_set_params(u, d) : cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+  if (st == CMM_OK) {
+    e = cudaStreamSynchronize(u->ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  }
+  cudaFree(d);
+  return st;
 }
 
 int cmm_unet_get_params(cmm_unet* u, float* params) {
