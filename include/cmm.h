@@ -168,6 +168,26 @@ int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out);
 /* Same with host buffers: copies m_in to the device, applies A, copies the result
  * back and waits. */
 int cmm_apply_A_host(cmm_op* op, const double* m_in_host, double* m_out_host);
+/* m_out = A m_in exactly as cmm_apply_A, but with no allocation: the paper has no
+ * counterpart; this is a library service for callers that cannot have device
+ * memory allocated or freed around the call (cudaMalloc/cudaFree may block on
+ * other streams and fail when memory is short).  The call makes no cudaMalloc,
+ * cudaFree or other allocating call; its temporaries live in one static device
+ * array of 32 MiB per device, held by every GPU that loads the library until the
+ * process exits.
+ * - Size limit: the map buffers (npix x (8 B FP64 + 4 B FP32 accumulator) x 4 for
+ *   TQU, x 1 for T, plus the gather copy) and the spectrum of at least one
+ *   detector (n_samp x 4 B in F32) must fit in 32 MiB; larger operators get
+ *   CMM_ERR_UNSUPPORTED.  Detectors are processed in chunks that fit.
+ * - Set-up: the first call on each device looks up the array's device address
+ *   (with that device current) and caches it; make that first call before any
+ *   stream capture.
+ * - Sharing: all calls in the process use the same array, which keeps the last
+ *   call's contents (each call clears what must start at zero).  Calls that
+ *   overlap on one device (from several threads, or on streams of different
+ *   contexts) race on it and give wrong results; order them.
+ * m_in, m_out: device double [ncomp][ny][nx]; must not alias. */
+int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out);
 /* Profiling: runs `reps` applications of A (as cmm_apply_A) with CUDA events
  * between its kernels and waits.  ms_host (host double [5]) receives the mean
  * duration in milliseconds of one launch of the forward pass (pointing, gather,

@@ -71,6 +71,7 @@ _SIGS = {
     "cmm_op_destroy": [_vp],
     "cmm_apply_A": [_vp, _vp, _vp],
     "cmm_apply_A_host": [_vp, _vp, _vp],
+    "cmm_apply_A_noalloc": [_vp, _vp, _vp],
     "cmm_profile_apply": [_vp, _vp, _vp, _i32, _vp],
     "cmm_project": [_vp, _vp, _vp, _i32],
     "cmm_rhs": [_vp, _vp, _i32, _vp],
@@ -206,6 +207,11 @@ def cmm_op_destroy(h):
 
 def cmm_apply_A(op, m_in, m_out):
     _check(_lib.cmm_apply_A(op, _dev(m_in, name="m_in"), _dev(m_out, name="m_out")))
+
+
+def cmm_apply_A_noalloc(op, m_in, m_out):
+    """As cmm_apply_A, with the temporaries in the library's static scratch array."""
+    _check(_lib.cmm_apply_A_noalloc(op, _dev(m_in, name="m_in"), _dev(m_out, name="m_out")))
 
 
 def cmm_apply_A_host(op, m_in: np.ndarray, m_out: np.ndarray):

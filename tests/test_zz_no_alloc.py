@@ -1,0 +1,84 @@
+"""cmm_apply_A_noalloc (A with its temporaries in the library's static scratch
+array) against cmm_apply_A on the same operator and map, over consecutive calls
+that leave the shared array holding another operator's data in between.
+
+Collected last so it also runs after every other GPU test in one process; it
+builds its own context and passes alone in a fresh process too.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# same tolerances as the A-application parity tests: F64 1e-10, F32 1e-5
+TOL = {0: 1e-10, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm as c
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(cmm):
+    return cmm.Context(0)
+
+
+def rel(a, b):
+    return float((a - b).norm() / b.norm())
+
+
+def operator(cmm, ctx, prec, ncomp, cfg, ny, nx, n_t, chunk=0):
+    scan = gen.small_scan(cfg=cfg, ny=ny, nx=nx, n_t=n_t, ncols=4, nrows=2, throw_px=30.0, ncomp=ncomp)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=cfg)
+    return cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=chunk), scan
+
+
+def maps(scan, cfg):
+    m = gen.random_maps(scan.ncomp, scan.ny, scan.nx, 1, cfg=cfg)[0]
+    return torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float64, device="cuda:0")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_apply_A_on_consecutive_calls(cmm, ctx, prec):
+    op1, s1 = operator(cmm, ctx, prec, 3, 301, 24, 20, 1 << 12, chunk=3)
+    op2, s2 = operator(cmm, ctx, prec, 1, 302, 40, 36, 1 << 13)
+    m1, m2 = maps(s1, 303), maps(s2, 304)
+    ref1, ref2 = op1.apply(m1), op2.apply(m2)
+    for _ in range(2):
+        for op, m, ref in ((op1, m1, ref1), (op2, m2, ref2)):
+            out = torch.full_like(ref, float("nan"))
+            cmm.cmm_apply_A_noalloc(op.h, m, out)
+            torch.cuda.synchronize()
+            assert torch.isfinite(out).all()
+            assert rel(out, ref) < TOL[prec]
+
+
+def test_noalloc_config1(cmm, ctx):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=1)
+    m = maps(scan, 305)
+    ref = op.apply(m)
+    for _ in range(2):
+        out = torch.zeros_like(ref)
+        cmm.cmm_apply_A_noalloc(op.h, m, out)
+        torch.cuda.synchronize()
+        assert rel(out, ref) < TOL[1]
+
+
+def test_noalloc_rejects_oversize(cmm, ctx):
+    # a 1024 x 1024 TQU map needs 64 MiB of map buffers alone
+    op, scan = operator(cmm, ctx, 1, 3, 306, 1024, 1024, 1 << 10)
+    m = torch.zeros((3, 1024, 1024), dtype=torch.float64, device="cuda:0")
+    out = torch.zeros_like(m)
+    with pytest.raises(cmm.CmmError, match="static scratch"):
+        cmm.cmm_apply_A_noalloc(op.h, m, out)
