@@ -435,10 +435,12 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   op->acc_stride = nc == 1 ? 1 : 4;
   const size_t gel = precision == CMM_PREC_F64 ? 8 : 4;
   int s = dalloc(&op->spec, per_det * chunk);
-  if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * npix);
-  if (s == CMM_OK) s = dalloc(&op->acc, sizeof(double) * op->acc_stride * npix);
-  if (s == CMM_OK) s = dalloc(&op->acc32, sizeof(float) * op->acc_stride * npix);
-  if (s == CMM_OK) s = (cudaMemset(op->acc32, 0, sizeof(float) * op->acc_stride * npix) == cudaSuccess) ? CMM_OK : fail(CMM_ERR_CUDA, "memset");
+  // map-sized buffers carry one extra pixel (index npix): the fast kernels send
+  // samples outside the map there (zero in the gather copy, never read back)
+  if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * (npix + 1));
+  if (s == CMM_OK) s = dalloc(&op->acc, sizeof(double) * op->acc_stride * (npix + 1));
+  if (s == CMM_OK) s = dalloc(&op->acc32, sizeof(float) * op->acc_stride * (npix + 1));
+  if (s == CMM_OK) s = (cudaMemset(op->acc32, 0, sizeof(float) * op->acc_stride * (npix + 1)) == cudaSuccess) ? CMM_OK : fail(CMM_ERR_CUDA, "memset");
   if (s == CMM_OK) s = dalloc(&op->tmp_a, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = dalloc(&op->tmp_b, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = op_init_twiddles(op);

@@ -57,6 +57,22 @@ __host__ __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y -
 template <typename V>
 __host__ __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
 
+// Complex add / subtract for butterflies: FP32 pairs use the packed two-wide
+// FP32 instructions of sm_100+ (one instruction for both components).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return double2{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return double2{a.x * b.x, a.y * b.y}; }
+
 // ------------------------------------------------------------------ handles
 struct Scratch {
   void* ptr = nullptr;

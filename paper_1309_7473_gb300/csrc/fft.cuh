@@ -77,8 +77,8 @@ __device__ __forceinline__ void dft_reg(V2<T>* x) {
       for (int j = 0; j < half; ++j) {
         const V2<T> t = rot32<T, SIGN>(x[start + j + half], j * (32 / (2 * half)));
         const V2<T> u = x[start + j];
-        x[start + j] = V2<T>{u.x + t.x, u.y + t.y};
-        x[start + j + half] = V2<T>{u.x - t.x, u.y - t.y};
+        x[start + j] = padd(u, t);
+        x[start + j + half] = psub(u, t);
       }
     }
   }

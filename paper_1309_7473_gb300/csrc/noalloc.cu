@@ -56,9 +56,9 @@ int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out) {
   const int nc = op->pt->ncomp;
   const size_t elt = op->prec == CMM_PREC_F64 ? 16 : (op->prec == CMM_PREC_BF16 ? 4 : 8);
   const size_t gel = op->prec == CMM_PREC_F64 ? 8 : 4;
-  const size_t acc_bytes = round_up(sizeof(double) * op->acc_stride * npix);
-  const size_t acc32_bytes = round_up(sizeof(float) * op->acc_stride * npix);
-  const size_t gather_bytes = round_up(gel * (nc == 1 ? 1 : 4) * npix);
+  const size_t acc_bytes = round_up(sizeof(double) * op->acc_stride * (npix + 1));
+  const size_t acc32_bytes = round_up(sizeof(float) * op->acc_stride * (npix + 1));
+  const size_t gather_bytes = round_up(gel * (nc == 1 ? 1 : 4) * (npix + 1));
   const size_t per_det = elt * (size_t)op->N;
   const size_t fixed = acc_bytes + acc32_bytes + gather_bytes;
   if (fixed + per_det > kNoAllocScratchBytes)
@@ -78,7 +78,7 @@ int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out) {
 
   // The array keeps whatever the previous call left: the FP32 partial map must
   // start at zero (the FP64 accumulator is cleared by the gather kernel).
-  CMM_CUDA(cudaMemsetAsync(v.acc32, 0, sizeof(float) * op->acc_stride * npix, op->ctx->stream));
+  CMM_CUDA(cudaMemsetAsync(v.acc32, 0, sizeof(float) * op->acc_stride * (npix + 1), op->ctx->stream));
   CMM_TRY(launch_map_to_gather(&v, m_in));
   for (int d0 = 0; d0 < op->pt->n_det; d0 += v.chunk) {
     const int nd = std::min(v.chunk, op->pt->n_det - d0);

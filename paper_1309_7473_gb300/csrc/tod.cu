@@ -177,6 +177,12 @@ __global__ void k_map_to_gather(const double* __restrict__ m, const uint8_t* __r
                                 void* gather, double* acc, int acc_stride, long long npix,
                                 const int* done) {
   if (done && *done) return;
+  // the extra pixel npix: zero in the gather copy, accumulator cleared
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (NC == 1) reinterpret_cast<T*>(gather)[npix] = (T)0;
+    else reinterpret_cast<V4<T>*>(gather)[npix] = V4<T>{(T)0, (T)0, (T)0, (T)0};
+    for (int c = 0; c < acc_stride; ++c) acc[npix * acc_stride + c] = 0.0;
+  }
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
     const bool ok = mask[p] != 0;

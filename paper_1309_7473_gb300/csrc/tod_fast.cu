@@ -30,13 +30,13 @@ namespace cmm {
 
 // Tuning knobs (compile-time; the defaults are the measured best on GB300).
 #ifndef CMM_DETS_PER_CTA
-#define CMM_DETS_PER_CTA 2
+#define CMM_DETS_PER_CTA 1
 #endif
 #ifndef CMM_COL_THREADS_PER_SM
-#define CMM_COL_THREADS_PER_SM 768
+#define CMM_COL_THREADS_PER_SM 1024
 #endif
 #ifndef CMM_FILTER_MINB
-#define CMM_FILTER_MINB 2
+#define CMM_FILTER_MINB 3
 #endif
 #ifndef CMM_GEN_UNROLL
 #define CMM_GEN_UNROLL 2
@@ -74,29 +74,50 @@ __device__ __forceinline__ float filter_weight_fast(const float4 cf, int k) {
 }
 
 // (cos 2a, sin 2a) of sample t, a = psi_d + phi_t, from the FP32 (cos 2phi, sin 2phi)
-__device__ __forceinline__ void response_fast(const TodArgs& a, long long t, const float2 pol, float& c,
+__device__ __forceinline__ void response_fast(const TodArgs& a, int t, const float2 pol, float& c,
                                               float& s) {
   const float2 r2 = __ldg(a.rot2 + t);
   c = pol.x * r2.x - pol.y * r2.y;
   s = pol.y * r2.x + pol.x * r2.y;
 }
 
-__device__ __forceinline__ float2 tw_N(const TodArgs& a, const float2* __restrict__ tw, long long e) {
+// w_N^e, 0 <= e < N, from the two tables w_N^(e mod C) and w_R^(e div C)
+__device__ __forceinline__ float2 tw_N(const TodArgs& a, const float2* __restrict__ tw, int e) {
   const float2 lo = __ldg(tw + a.twl.Nlo_off + (e & (a.C - 1)));
   const float2 hi = __ldg(tw + a.twl.R_off + (e >> a.logC));
   return cmul(lo, hi);
 }
 
-template <int NC>
-__device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, const float2 pol, long long t) {
+// Pixel of a sample for the fast kernels (the rule of sample_pixel).  A sample
+// outside the map gets index npix: an extra pixel that is zero in the gather copy
+// and whose accumulator is never read, so the kernels take no branch on it.
+template <bool PERIODIC>
+__device__ __forceinline__ int pixel_fast(const int4 b, const int2 o, int ny, int nx, int npix) {
+  const int ox = b.z * o.x - b.w * o.y;
+  const int oy = b.w * o.x + b.z * o.y;
+  int ix = (b.x + (1 << 15) + (ox >> 6)) >> 16;
+  int iy = (b.y + (1 << 15) + (oy >> 6)) >> 16;
+  if (PERIODIC) {
+    ix %= nx;
+    ix += ix < 0 ? nx : 0;
+    iy %= ny;
+    iy += iy < 0 ? ny : 0;
+    return iy * nx + ix;
+  }
+  const bool in = (unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny;
+  return in ? iy * nx + ix : npix;
+}
+
+// (P m) at sample t of a detector: gather from the FP32 map copy at the sample's pixel
+template <int NC, bool PERIODIC>
+__device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, const float2 pol, int t) {
   const int4 b = __ldg(a.bore + t);
-  const int p = sample_pixel(b, off, a.ny, a.nx, a.periodic);
-  if (p < 0) return 0.0f;
+  const int p = pixel_fast<PERIODIC>(b, off, a.ny, a.nx, (int)a.npix);
   if (NC == 1) return __ldg((const float*)a.gather + p);
   const float4 g = __ldg((const float4*)a.gather + p);
   float c, s;
   response_fast(a, t, pol, c, s);
-  return g.x + c * g.y + s * g.z;
+  return fmaf(s, g.z, fmaf(c, g.y, g.x));
 }
 
 // J interleaved columns: position pos of column cl at J pos + cl, so every access
@@ -130,7 +151,7 @@ template <> struct ColPlan<256> {
 };
 
 // ------------------------------------------------------------------ pass T (forward)
-template <int NC, typename S, int R>
+template <int NC, typename S, int R, bool PERIODIC>
 __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_fwd(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
   constexpr int J = ColShape<R>::J;
@@ -141,6 +162,10 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
   const int c = blockIdx.x * J + cl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
   const ColJ<J> ad{smf, cl};
+  // element e of the thread: column position kr = i + e TPC, complex index c + kr C,
+  // samples t0 + e dt and t0 + e dt + 1
+  const int t0 = 2 * (c + i * a.C);
+  const int dt = 2 * TPC * a.C;
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
     const int dl = dl0 + dd;
@@ -152,19 +177,23 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
     __syncthreads();
 #pragma unroll kGenUnroll
     for (int e = 0; e < kE; ++e) {
-      const long long j = (long long)c + ((long long)(i + e * TPC) << a.logC);
-      ad.st(i + e * TPC, make_float2(project_fast<NC>(a, off, pol, 2 * j), project_fast<NC>(a, off, pol, 2 * j + 1)));
+      const int t = t0 + e * dt;
+      ad.st(i + e * TPC, make_float2(project_fast<NC, PERIODIC>(a, off, pol, t),
+                                     project_fast<NC, PERIODIC>(a, off, pol, t + 1)));
     }
     __syncthreads();
     float2 x[kE];
 #pragma unroll
     for (int e = 0; e < kE; ++e) x[e] = ad.ld(i + e * TPC);
     ColPlan<R>::template run<-1>(x, i, tw + a.twl.R_off, ad);
-    S* Y = reinterpret_cast<S*>(a.spec) + (long long)dl * a.N;
+    // four-step twiddle w_N^(c kr), kr = i + e TPC, by recurrence over e
+    float2 w = tw_N(a, tw, c * i);
+    const float2 step = tw_N(a, tw, c * TPC);
+    S* Y = reinterpret_cast<S*>(a.spec) + (size_t)dl * a.N + c + i * a.C;
 #pragma unroll
     for (int e = 0; e < kE; ++e) {
-      const int kr = i + e * TPC;
-      Store<float, S>::st(Y + ((long long)kr << a.logC) + c, cmul(x[e], tw_N(a, tw, (long long)c * kr)));
+      Store<float, S>::st(Y + e * (TPC * a.C), cmul(x[e], w));
+      w = cmul(w, step);
     }
   }
 }
@@ -203,12 +232,12 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
   const int dl = blockIdx.y;
   const int d = a.d0 + dl;
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  S* Y = reinterpret_cast<S*>(a.spec) + (long long)dl * a.N;
+  S* Y = reinterpret_cast<S*>(a.spec) + (size_t)dl * a.N;
   const RowAddr<PS> ad{smf + rs * ROWLEN};
   float2 x[E];
 #pragma unroll
   for (int e = 0; e < E; ++e)
-    x[e] = active ? Store<float, S>::ld(Y + (long long)row * C + i + e * TPR) : make_float2(0.f, 0.f);
+    x[e] = active ? Store<float, S>::ld(Y + row * C + i + e * TPR) : make_float2(0.f, 0.f);
   rfft<-1, E, RC...>(x, i, tw + a.twl.C_off, ad);
   __syncthreads();
 #pragma unroll
@@ -238,17 +267,18 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
       const int k = ra + a.R * kc;   // < N <= 2^19
       const float2 A = r0[i1];
       const float2 B = cconj(r1[i2]);
-      const float2 Ev{(A.x + B.x) * 0.5f, (A.y + B.y) * 0.5f};
-      const float2 Dv{(A.x - B.x) * 0.5f, (A.y - B.y) * 0.5f};
+      const float2 half2{0.5f, 0.5f};
+      const float2 Ev = pmul(padd(A, B), half2);
+      const float2 Dv = pmul(psub(A, B), half2);
       const float2 O{Dv.y, -Dv.x};
       const float2 W = cmul(wrow, __ldg(tw + a.twl.C2_off + kc));
       const float wk = filter_weight_fast(cf, k);
       const float wm = filter_weight_fast(cf, (int)a.N - k);
       const float ws = 0.5f * (wk + wm), wd = 0.5f * (wk - wm);
       const float2 WO = cmul(W, O);
-      const float2 Ep{ws * Ev.x + wd * WO.x, ws * Ev.y + wd * WO.y};
+      const float2 Ep = __ffma2_rn(make_float2(ws, ws), Ev, pmul(make_float2(wd, wd), WO));
       const float2 cWE = cmulc(Ev, W);
-      const float2 Op{wd * cWE.x + ws * O.x, wd * cWE.y + ws * O.y};
+      const float2 Op = __ffma2_rn(make_float2(wd, wd), cWE, pmul(make_float2(ws, ws), O));
       r0[i1] = make_float2(Ep.x - Op.y, Ep.y + Op.x);
       if (!(single && i2 == i1)) r1[i2] = make_float2(Ep.x + Op.y, Op.x - Ep.y);
     }
@@ -258,11 +288,14 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
   for (int e = 0; e < E; ++e) x[e] = ad.ld(i + e * TPR);
   rfft<1, E, RC...>(x, i, tw + a.twl.C_off, ad);
   if (active) {
+    // w_N^(row c), c = i + e TPR, by recurrence over e
+    float2 w = tw_N(a, tw, row * i);
+    const float2 step = tw_N(a, tw, row * TPR);
+    S* Yr = Y + row * C + i;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int c = i + e * TPR;
-      const float2 w = tw_N(a, tw, (long long)c * row);
-      Store<float, S>::st(Y + (long long)row * C + c, cmulc(x[e], w));
+      Store<float, S>::st(Yr + e * TPR, cmulc(x[e], w));
+      w = cmul(w, step);
     }
   }
 }
@@ -281,9 +314,10 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
 // holds 2G consecutive samples in lane order (lane l of a group: samples 2l, 2l + 1).
 // Items with equal pixels that are adjacent in time are summed (in-lane, then across
 // the lanes of a group by a segmented suffix scan); the first item of every run
-// issues one reduction.
+// issues one reduction.  Runs in the extra pixel `skip` (samples outside the map)
+// issue none: every warp would otherwise hit that one address.
 template <int NC, int G>
-__device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0, float3 v1) {
+__device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0, float3 v1, int skip) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const bool group_end = (lane % G) == G - 1;
@@ -295,7 +329,7 @@ __device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0
   }
   const int g = two ? p1 : p0;                 // pixel of the lane's last item
   const int fnext = __shfl_down_sync(full, p0, 1);
-  const bool link = !group_end && g >= 0 && g == fnext;   // next lane's first item continues my last run
+  const bool link = !group_end && g == fnext;   // next lane's first item continues my last run
   const unsigned linkmask = __ballot_sync(full, link);
   const bool linkprev = lane > 0 && ((linkmask >> (lane - 1)) & 1u);
   // y_l = A_l + (single_l && link_l ? y_{l+1} : 0), by a segmented suffix scan
@@ -324,21 +358,21 @@ __device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0
   carry.z = __shfl_down_sync(full, y.z, 1);
   if (!link) carry = make_float3(0.f, 0.f, 0.f);
   if (two) {
-    if (!linkprev && p0 >= 0) {
+    if (!linkprev && p0 != skip) {
       if (NC == 1) red_add(acc32 + p0, v0.x);
-      else red_add4(acc32 + 4 * (long long)p0, v0.x, v0.y, v0.z);
+      else red_add4(acc32 + 4 * p0, v0.x, v0.y, v0.z);
     }
-    if (p1 >= 0) {
+    if (p1 != skip) {
       if (NC == 1) red_add(acc32 + p1, v1.x + carry.x);
-      else red_add4(acc32 + 4 * (long long)p1, v1.x + carry.x, v1.y + carry.y, v1.z + carry.z);
+      else red_add4(acc32 + 4 * p1, v1.x + carry.x, v1.y + carry.y, v1.z + carry.z);
     }
-  } else if (!linkprev && p0 >= 0) {
+  } else if (!linkprev && p0 != skip) {
     if (NC == 1) red_add(acc32 + p0, y.x);
-    else red_add4(acc32 + 4 * (long long)p0, y.x, y.y, y.z);
+    else red_add4(acc32 + 4 * p0, y.x, y.y, y.z);
   }
 }
 
-template <int NC, typename S, int R>
+template <int NC, typename S, int R, bool PERIODIC>
 __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
   constexpr int J = ColShape<R>::J;
@@ -350,15 +384,18 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
   const ColJ<J> ad{smf, cl};
   const float scale = 1.0f / (float)a.N;
+  const int t0 = 2 * (c + i * a.C);
+  const int dt = 2 * TPC * a.C;
+  const int npix = (int)a.npix;
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
     const int dl = dl0 + dd;
     if (dl >= nd) break;
     const int d = a.d0 + dl;
-    const S* Y = reinterpret_cast<const S*>(a.spec) + (long long)dl * a.N;
+    const S* Y = reinterpret_cast<const S*>(a.spec) + (size_t)dl * a.N + c + i * a.C;
     float2 x[kE];
 #pragma unroll
-    for (int e = 0; e < kE; ++e) x[e] = Store<float, S>::ld(Y + ((long long)(i + e * TPC) << a.logC) + c);
+    for (int e = 0; e < kE; ++e) x[e] = Store<float, S>::ld(Y + e * (TPC * a.C));
     __syncthreads();   // the previous detector's binning reads of the tile are done
     ColPlan<R>::template run<1>(x, i, tw + a.twl.R_off, ad);
     __syncthreads();
@@ -369,25 +406,24 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
 #pragma unroll 2
     for (int e = 0; e < kE; ++e) {
-      const long long j = (long long)c + ((long long)(i + e * TPC) << a.logC);
-      const long long t0 = 2 * j;
-      const int4 b0 = __ldg(a.bore + t0);
-      const int4 b1 = __ldg(a.bore + t0 + 1);
-      const int p0 = sample_pixel(b0, off, a.ny, a.nx, a.periodic);
-      const int p1 = sample_pixel(b1, off, a.ny, a.nx, a.periodic);
+      const int t = t0 + e * dt;
+      const int4 b0 = __ldg(a.bore + t);
+      const int4 b1 = __ldg(a.bore + t + 1);
+      const int p0 = pixel_fast<PERIODIC>(b0, off, a.ny, a.nx, npix);
+      const int p1 = pixel_fast<PERIODIC>(b1, off, a.ny, a.nx, npix);
       const float2 xe = ad.ld(i + e * TPC);
       const float u0 = xe.x * scale, u1 = xe.y * scale;
       float3 v0 = make_float3(u0, 0.f, 0.f), v1 = make_float3(u1, 0.f, 0.f);
       if (NC == 3) {
         float c0, s0, c1, s1;
-        response_fast(a, t0, pol, c0, s0);
-        response_fast(a, t0 + 1, pol, c1, s1);
+        response_fast(a, t, pol, c0, s0);
+        response_fast(a, t + 1, pol, c1, s1);
         v0.y = c0 * u0;
         v0.z = s0 * u0;
         v1.y = c1 * u1;
         v1.z = s1 * u1;
       }
-      warp_bin<NC, J>(a.acc32, p0, p1, v0, v1);
+      warp_bin<NC, J>(a.acc32, p0, p1, v0, v1, npix);
     }
   }
 }
@@ -433,28 +469,35 @@ bool fast_path_ok(const cmm_op* op) {
   return fast_path_sizes(op->logR + op->logC, op->prec, &lr, &lc) && lr == op->logR;
 }
 
-template <int NC, typename S, int R>
+template <int NC, typename S, int R, bool PERIODIC>
 static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
   constexpr int J = ColShape<R>::J;
   constexpr int NT = ColShape<R>::THREADS;
   const int smem = (int)(sizeof(float2) * R * J);
   if (attr_only) {
-    CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem));
     return CMM_OK;
   }
   const dim3 g(a.C / J, (nd + kDetsPerCta - 1) / kDetsPerCta);
-  if (pass == 0) k_fast_fwd<NC, S, R><<<g, NT, smem, st>>>(a, nd);
-  else k_fast_inv_bin<NC, S, R><<<g, NT, smem, st>>>(a, nd);
+  if (pass == 0) k_fast_fwd<NC, S, R, PERIODIC><<<g, NT, smem, st>>>(a, nd);
+  else k_fast_inv_bin<NC, S, R, PERIODIC><<<g, NT, smem, st>>>(a, nd);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
 
+template <int NC, typename S, bool PERIODIC>
+static int dispatch_T_p(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
+  if (a.logR == 6) return run_T<NC, S, 64, PERIODIC>(a, nd, pass, st, attr_only);
+  if (a.logR == 7) return run_T<NC, S, 128, PERIODIC>(a, nd, pass, st, attr_only);
+  return run_T<NC, S, 256, PERIODIC>(a, nd, pass, st, attr_only);
+}
+
 template <int NC, typename S>
 static int dispatch_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
-  if (a.logR == 6) return run_T<NC, S, 64>(a, nd, pass, st, attr_only);
-  if (a.logR == 7) return run_T<NC, S, 128>(a, nd, pass, st, attr_only);
-  return run_T<NC, S, 256>(a, nd, pass, st, attr_only);
+  return a.periodic ? dispatch_T_p<NC, S, true>(a, nd, pass, st, attr_only)
+                    : dispatch_T_p<NC, S, false>(a, nd, pass, st, attr_only);
 }
 
 template <typename S, int E, int... RC>
@@ -489,9 +532,10 @@ static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
 }
 
 static int flush(const TodArgs& a, int nc, cudaStream_t st) {
-  const int blocks = (int)std::min<long long>((a.npix + 255) / 256, 4096);
-  if (nc == 1) k_fast_flush<1><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix, a.done);
-  else k_fast_flush<3><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix, a.done);
+  // npix + 1 entries: the extra pixel is cleared too, so its FP32 sum stays bounded
+  const int blocks = (int)std::min<long long>((a.npix + 256) / 256, 4096);
+  if (nc == 1) k_fast_flush<1><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix + 1, a.done);
+  else k_fast_flush<3><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix + 1, a.done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
