@@ -163,6 +163,15 @@ int cmm_noise_diag(cmm_noise* nz, double* diag_host);
 int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precision,
                   int32_t det_chunk, cmm_op** out);
 int cmm_op_destroy(cmm_op* op);
+/* Pointing cache (no counterpart in the paper, which recomputes nothing on a GPU):
+ * enable != 0 stores the pixel index of every sample, computed once by the same
+ * rule as the on-the-fly pointing, in a device array owned by the handle
+ * (4 bytes x n_det x n_samp; 4.3 GB at 1024 x 2^20).  The FP32/BF16 applications
+ * of A then read one index per sample instead of recomputing the pointing: more
+ * HBM traffic (8 bytes per sample per application) for fewer instructions.
+ * enable == 0 frees it.  Results are identical either way.  Only for the FP32 and
+ * BF16 operators of non-periodic maps (else CMM_ERR_UNSUPPORTED). */
+int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable);
 /* m_out = A m_in (Eq. 2).  device double [ncomp][ny][nx] each; must not alias. */
 int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out);
 /* Same with host buffers: copies m_in to the device, applies A, copies the result

@@ -69,6 +69,7 @@ _SIGS = {
     "cmm_noise_diag": [_vp, _vp],
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
     "cmm_op_destroy": [_vp],
+    "cmm_op_set_pixel_cache": [_vp, _i32],
     "cmm_apply_A": [_vp, _vp, _vp],
     "cmm_apply_A_host": [_vp, _vp, _vp],
     "cmm_apply_A_noalloc": [_vp, _vp, _vp],
@@ -203,6 +204,10 @@ def cmm_op_create(ctx, pointing, noise, precision=PREC_F32, det_chunk=0):
 
 def cmm_op_destroy(h):
     _check(_lib.cmm_op_destroy(h))
+
+
+def cmm_op_set_pixel_cache(op, enable=True):
+    _check(_lib.cmm_op_set_pixel_cache(op, 1 if enable else 0))
 
 
 def cmm_apply_A(op, m_in, m_out):
@@ -426,6 +431,9 @@ class Operator:
         self.shape = self.pointing.shape
         self.n_det, self.n_t = scan.n_det, scan.n_t
         self.h = cmm_op_create(ctx.h, self.pointing.h, self.noise.h, precision, det_chunk)
+
+    def set_pixel_cache(self, enable=True):
+        cmm_op_set_pixel_cache(self.h, enable)
 
     def new_map(self):
         import torch

@@ -378,6 +378,7 @@ static void free_op(cmm_op* op) {
   dfree(op->tw);
   dfree(op->tmp_a);
   dfree(op->tmp_b);
+  dfree(op->pix);
   dfree(op->sol);
   dfree(op->sol_state);
   cmm_ctx* c = op->ctx;
@@ -469,6 +470,30 @@ static int op_set_split(cmm_op* op, int logR) {
   op->C = 1 << op->logC;
   CMM_TRY(op_init_twiddles(op));
   return op_prepare_kernels(op);
+}
+
+int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable) {
+  if (!op) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  if (!enable) {
+    if (op->pix) {
+      CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+      dfree(op->pix);
+      op->pix = nullptr;
+    }
+    return CMM_OK;
+  }
+  if (op->pix) return CMM_OK;
+  if (!fast_path_ok(op) || op->pt->periodic)
+    return fail(CMM_ERR_UNSUPPORTED, "the pixel cache needs the FP32/BF16 fast path and a non-periodic map");
+  const size_t bytes = sizeof(int32_t) * (size_t)op->pt->n_det * (size_t)op->pt->n_t;
+  CMM_TRY(dalloc(&op->pix, bytes));
+  const int s = launch_fill_pixels(op);
+  if (s != CMM_OK) {
+    dfree(op->pix);
+    op->pix = nullptr;
+  }
+  return s;
 }
 
 static int apply_A_dev(cmm_op* op, const double* m_in, double* m_out) {

@@ -133,6 +133,7 @@ struct cmm_op {
   float* acc32 = nullptr;      // [npix][acc_stride] FP32 partial accumulator (fast path)
   int acc_stride = 0;
   void* tw = nullptr;          // twiddle tables in the op's compute type
+  int32_t* pix = nullptr;      // optional [n_det][n_samp] pixel index per sample (npix: outside)
   double* tmp_a = nullptr;     // [ncomp*npix] device temporaries
   double* tmp_b = nullptr;
   const int* done = nullptr;   // solver stop flag seen by every kernel (nullptr: none)
@@ -168,6 +169,8 @@ int launch_hit_blocks(cmm_pointing* pt, const double* det_weight, const uint8_t*
                       double* blocks, const int* done);
 int op_init_twiddles(cmm_op* op);
 int op_prepare_kernels(cmm_op* op);
+int launch_fill_pixels(cmm_op* op);
+bool fast_path_ok(const cmm_op* op);
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
 
 // ---- handle lifetimes: a handle stays alive while handles made from it exist, so

@@ -49,15 +49,17 @@ __device__ __forceinline__ void rfft_stages(float2 (&x)[E], const int i, const f
 #pragma unroll
       for (int q = 0; q < R; ++q) x[u + q * NB] = z[q];
     } else {
-      const int base = (ib - k) * R + k;
+      // outputs at (ib - k) R + k + q P: one base index, constant offsets
+      const int b = ad.base((ib - k) * R + k);
 #pragma unroll
-      for (int q = 0; q < R; ++q) ad.st(base + q * P, z[q]);
+      for (int q = 0; q < R; ++q) ad.st_at(b, q * P, z[q]);
     }
   }
   if constexpr (!LAST) {
     __syncthreads();
+    const int b = ad.base(i);
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = ad.ld(i + e * (L / E));
+    for (int e = 0; e < E; ++e) x[e] = ad.ld_at(b, e * (L / E));
     rfft_stages<SIGN, E, L, P * R, Addr, REST...>(x, i, tw, ad);
   }
 }
@@ -78,16 +80,27 @@ struct ColAddr {
   __device__ __forceinline__ int idx(int pos) const { return ((pos + (pos >> 3)) << 3) + (cl ^ (pos & 7)); }
   __device__ __forceinline__ void st(int pos, float2 v) const { buf[idx(pos)] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return buf[idx(pos)]; }
+  __device__ __forceinline__ int base(int pos) const { return pos; }
+  __device__ __forceinline__ void st_at(int b, int o, float2 v) const { st(b + o, v); }
+  __device__ __forceinline__ float2 ld_at(int b, int o) const { return ld(b + o); }
 };
 __host__ __device__ constexpr int col_tile_elems(int L) { return 8 * (L + L / 8); }
 
 // One contiguous row (pass F), padded by one element every 2^PS positions.
+// st_at / ld_at address position pos + o from base(pos) with a constant offset o;
+// exact whenever the low PS bits of pos and o do not carry into each other, which
+// holds for every access of the register FFT (either pos is a multiple of 2^PS
+// and o < 2^PS, or o is a multiple of 2^PS, or o is a multiple of a power of two
+// p < 2^PS and pos < p).
 template <int PS>
 struct RowAddr {
   float2* buf;
   __device__ __forceinline__ int idx(int pos) const { return pos + (pos >> PS); }
   __device__ __forceinline__ void st(int pos, float2 v) const { buf[idx(pos)] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return buf[idx(pos)]; }
+  __device__ __forceinline__ int base(int pos) const { return idx(pos); }
+  __device__ __forceinline__ void st_at(int b, int o, float2 v) const { buf[b + o + (o >> PS)] = v; }
+  __device__ __forceinline__ float2 ld_at(int b, int o) const { return buf[b + o + (o >> PS)]; }
 };
 
 }  // namespace cmm

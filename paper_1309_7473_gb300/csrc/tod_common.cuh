@@ -82,6 +82,7 @@ struct TodArgs {
   float* acc32;         // [npix][acc_stride] FP32 partials (fast path)
   long long npix;
   const void* tod;      // float / double [n_det][n_t]
+  const int* pix;       // cached pixel indices [n_det][n_t] or nullptr
   int d0;
   const int* done;
 };
@@ -168,6 +169,7 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   a.acc32 = op->acc32;
   a.npix = pt->npix;
   a.tod = nullptr;
+  a.pix = op->pix;
   a.d0 = d0;
   a.done = op->done;
   return a;

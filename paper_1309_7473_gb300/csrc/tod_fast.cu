@@ -41,9 +41,13 @@ namespace cmm {
 #ifndef CMM_GEN_UNROLL
 #define CMM_GEN_UNROLL 2
 #endif
+#ifndef CMM_BIN_UNROLL
+#define CMM_BIN_UNROLL 1
+#endif
 
 constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
 constexpr int kGenUnroll = CMM_GEN_UNROLL;
+constexpr int kBinUnroll = CMM_BIN_UNROLL;
 constexpr int kFlushDets = 128;
 constexpr int kE = 16;     // elements per thread in the column FFT
 
@@ -128,6 +132,9 @@ struct ColJ {
   int cl;
   __device__ __forceinline__ void st(int pos, float2 v) const { buf[pos * J + cl] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return buf[pos * J + cl]; }
+  __device__ __forceinline__ int base(int pos) const { return pos * J + cl; }
+  __device__ __forceinline__ void st_at(int b, int o, float2 v) const { buf[b + o * J] = v; }
+  __device__ __forceinline__ float2 ld_at(int b, int o) const { return buf[b + o * J]; }
 };
 
 template <int R> struct ColPlan;
@@ -151,7 +158,17 @@ template <> struct ColPlan<256> {
 };
 
 // ------------------------------------------------------------------ pass T (forward)
-template <int NC, typename S, int R, bool PERIODIC>
+// Gather with a known pixel (cached pointing).
+template <int NC>
+__device__ __forceinline__ float gather_fast(const TodArgs& a, int p, const float2 pol, int t) {
+  if (NC == 1) return __ldg((const float*)a.gather + p);
+  const float4 g = __ldg((const float4*)a.gather + p);
+  float c, s;
+  response_fast(a, t, pol, c, s);
+  return fmaf(s, g.z, fmaf(c, g.y, g.x));
+}
+
+template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
 __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_fwd(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
   constexpr int J = ColShape<R>::J;
@@ -175,11 +192,24 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
     // samples into the tile (the previous detector's last reads are fenced first)
     __syncthreads();
+    if constexpr (CACHED) {
+      // all pixel pairs first (independent loads), then the gathers
+      const int2* pp = reinterpret_cast<const int2*>(a.pix + (size_t)d * a.n_t + t0);
+      int2 pq[kE];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) pq[e] = __ldcs(pp + e * (dt / 2));
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        const int t = t0 + e * dt;
+        ad.st(i + e * TPC, make_float2(gather_fast<NC>(a, pq[e].x, pol, t), gather_fast<NC>(a, pq[e].y, pol, t + 1)));
+      }
+    } else {
 #pragma unroll kGenUnroll
-    for (int e = 0; e < kE; ++e) {
-      const int t = t0 + e * dt;
-      ad.st(i + e * TPC, make_float2(project_fast<NC, PERIODIC>(a, off, pol, t),
-                                     project_fast<NC, PERIODIC>(a, off, pol, t + 1)));
+      for (int e = 0; e < kE; ++e) {
+        const int t = t0 + e * dt;
+        ad.st(i + e * TPC, make_float2(project_fast<NC, PERIODIC>(a, off, pol, t),
+                                       project_fast<NC, PERIODIC>(a, off, pol, t + 1)));
+      }
     }
     __syncthreads();
     float2 x[kE];
@@ -240,8 +270,9 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
     x[e] = active ? Store<float, S>::ld(Y + row * C + i + e * TPR) : make_float2(0.f, 0.f);
   rfft<-1, E, RC...>(x, i, tw + a.twl.C_off, ad);
   __syncthreads();
+  const int bi = ad.base(i);
 #pragma unroll
-  for (int e = 0; e < E; ++e) ad.st(i + e * TPR, x[e]);
+  for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
   __syncthreads();
   if (pair_ok) {
     const float4 cf = reinterpret_cast<const float4*>(a.coef)[d];
@@ -285,7 +316,7 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
   }
   __syncthreads();
 #pragma unroll
-  for (int e = 0; e < E; ++e) x[e] = ad.ld(i + e * TPR);
+  for (int e = 0; e < E; ++e) x[e] = ad.ld_at(bi, e * TPR);
   rfft<1, E, RC...>(x, i, tw + a.twl.C_off, ad);
   if (active) {
     // w_N^(row c), c = i + e TPR, by recurrence over e
@@ -310,69 +341,44 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
                : "memory");
 }
 
-// Bins the two samples of every lane of a warp.  Each group of G consecutive lanes
-// holds 2G consecutive samples in lane order (lane l of a group: samples 2l, 2l + 1).
-// Items with equal pixels that are adjacent in time are summed (in-lane, then across
-// the lanes of a group by a segmented suffix scan); the first item of every run
-// issues one reduction.  Runs in the extra pixel `skip` (samples outside the map)
-// issue none: every warp would otherwise hit that one address.
-template <int NC, int G>
-__device__ __forceinline__ void warp_bin(float* acc32, int p0, int p1, float3 v0, float3 v1, int skip) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const bool group_end = (lane % G) == G - 1;
-  const bool two = p1 != p0;
-  if (!two) {
-    v0.x += v1.x;
-    v0.y += v1.y;
-    v0.z += v1.z;
+// Bins 8 consecutive samples of one lane: runs of equal pixels are summed in
+// registers and each run issues one reduction into the FP32 partial map.  Runs in
+// the extra pixel `skip` (samples outside the map) issue none: every warp would
+// otherwise hit that one address.
+template <int NC>
+__device__ __forceinline__ void bin_run8(float* acc32, const int (&p)[8], const float (&u)[8], const float (&c)[8],
+                                         const float (&s)[8], int skip) {
+  int cur = p[0];
+  float ax = u[0], ay = 0.f, az = 0.f;
+  if (NC == 3) {
+    ay = c[0] * u[0];
+    az = s[0] * u[0];
   }
-  const int g = two ? p1 : p0;                 // pixel of the lane's last item
-  const int fnext = __shfl_down_sync(full, p0, 1);
-  const bool link = !group_end && g == fnext;   // next lane's first item continues my last run
-  const unsigned linkmask = __ballot_sync(full, link);
-  const bool linkprev = lane > 0 && ((linkmask >> (lane - 1)) & 1u);
-  // y_l = A_l + (single_l && link_l ? y_{l+1} : 0), by a segmented suffix scan
-  float3 y = v0;
-  bool cont = !two && link;
-  unsigned contmask = __ballot_sync(full, cont);
-  for (int dist = 1; contmask != 0u && dist < 32; dist <<= 1) {
-    const float yx = __shfl_down_sync(full, y.x, dist);
-    const float yy = __shfl_down_sync(full, y.y, dist);
-    const float yz = __shfl_down_sync(full, y.z, dist);
-    const bool other = lane + dist < 32 && ((contmask >> (lane + dist)) & 1u);
-    if (cont && lane + dist < 32) {
-      y.x += yx;
-      y.y += yy;
-      y.z += yz;
-      cont = other;
-    } else {
-      cont = false;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    if (p[k] != cur) {
+      if (cur != skip) {
+        if (NC == 1) red_add(acc32 + cur, ax);
+        else red_add4(acc32 + 4 * cur, ax, ay, az);
+      }
+      cur = p[k];
+      ax = 0.f;
+      ay = 0.f;
+      az = 0.f;
     }
-    contmask = __ballot_sync(full, cont);
+    ax += u[k];
+    if (NC == 3) {
+      ay = fmaf(c[k], u[k], ay);
+      az = fmaf(s[k], u[k], az);
+    }
   }
-  // carry_l = link_l ? y_{l+1} : 0
-  float3 carry;
-  carry.x = __shfl_down_sync(full, y.x, 1);
-  carry.y = __shfl_down_sync(full, y.y, 1);
-  carry.z = __shfl_down_sync(full, y.z, 1);
-  if (!link) carry = make_float3(0.f, 0.f, 0.f);
-  if (two) {
-    if (!linkprev && p0 != skip) {
-      if (NC == 1) red_add(acc32 + p0, v0.x);
-      else red_add4(acc32 + 4 * p0, v0.x, v0.y, v0.z);
-    }
-    if (p1 != skip) {
-      if (NC == 1) red_add(acc32 + p1, v1.x + carry.x);
-      else red_add4(acc32 + 4 * p1, v1.x + carry.x, v1.y + carry.y, v1.z + carry.z);
-    }
-  } else if (!linkprev && p0 != skip) {
-    if (NC == 1) red_add(acc32 + p0, y.x);
-    else red_add4(acc32 + 4 * p0, y.x, y.y, y.z);
+  if (cur != skip) {
+    if (NC == 1) red_add(acc32 + cur, ax);
+    else red_add4(acc32 + 4 * cur, ax, ay, az);
   }
 }
 
-template <int NC, typename S, int R, bool PERIODIC>
+template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
 __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
   constexpr int J = ColShape<R>::J;
@@ -384,9 +390,16 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
   const float2* tw = reinterpret_cast<const float2*>(a.tw);
   const ColJ<J> ad{smf, cl};
   const float scale = 1.0f / (float)a.N;
-  const int t0 = 2 * (c + i * a.C);
-  const int dt = 2 * TPC * a.C;
   const int npix = (int)a.npix;
+  // binning layout: BS = row stride of the tile (the 2-complex pad spreads the
+  // rows' 16-byte reads over all banks), LPR lanes per row, RPP rows per pass
+  constexpr int BS = J + 2;
+  constexpr int LPR = J / 4;
+  constexpr int RPP = ColShape<R>::THREADS / LPR;
+  constexpr int PSTR = 2 * J + 4;   // ints per staged pixel row (the pad spreads 16-byte reads over the banks)
+  const int bq = threadIdx.x % LPR;
+  const int br = threadIdx.x / LPR;
+  const int c0 = blockIdx.x * J;
   const int dl0 = blockIdx.y * kDetsPerCta;
   for (int dd = 0; dd < kDetsPerCta; ++dd) {
     const int dl = dl0 + dd;
@@ -399,31 +412,59 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
     __syncthreads();   // the previous detector's binning reads of the tile are done
     ColPlan<R>::template run<1>(x, i, tw + a.twl.R_off, ad);
     __syncthreads();
+    // filtered samples into a tile of rows kr (stride J + 2 complex) for the binning
 #pragma unroll
-    for (int e = 0; e < kE; ++e) ad.st(i + e * TPC, x[e]);
+    for (int e = 0; e < kE; ++e) smf[(i + e * TPC) * BS + cl] = x[e];
     __syncthreads();
     const int2 off = a.det_off[d];
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
-#pragma unroll 2
-    for (int e = 0; e < kE; ++e) {
-      const int t = t0 + e * dt;
-      const int4 b0 = __ldg(a.bore + t);
-      const int4 b1 = __ldg(a.bore + t + 1);
-      const int p0 = pixel_fast<PERIODIC>(b0, off, a.ny, a.nx, npix);
-      const int p1 = pixel_fast<PERIODIC>(b1, off, a.ny, a.nx, npix);
-      const float2 xe = ad.ld(i + e * TPC);
-      const float u0 = xe.x * scale, u1 = xe.y * scale;
-      float3 v0 = make_float3(u0, 0.f, 0.f), v1 = make_float3(u1, 0.f, 0.f);
-      if (NC == 3) {
-        float c0, s0, c1, s1;
-        response_fast(a, t, pol, c0, s0);
-        response_fast(a, t + 1, pol, c1, s1);
-        v0.y = c0 * u0;
-        v0.z = s0 * u0;
-        v1.y = c1 * u1;
-        v1.z = s1 * u1;
+    const int* pixd = CACHED ? a.pix + (size_t)d * a.n_t : nullptr;
+    int* pst = reinterpret_cast<int*>(smf + R * BS);   // pixel staging of one pass (on-the-fly pointing)
+    // each lane bins 8 consecutive samples: 4 complex of row kr from column 4 q
+#pragma unroll kBinUnroll
+    for (int kr0 = 0; kr0 < R; kr0 += RPP) {
+      const int kr = kr0 + br;
+      const int t = 2 * (c0 + 4 * bq + kr * a.C);
+      int p[8];
+      if constexpr (!CACHED) {
+        // pixels of the pass's RPP rows x 2J samples, lanes on consecutive samples
+        // (coalesced boresight reads), staged in shared memory
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int sidx = threadIdx.x + k * ColShape<R>::THREADS;
+          const int rr = sidx / (2 * J), col = sidx % (2 * J);
+          const int ts = 2 * (c0 + (kr0 + rr) * a.C) + col;
+          pst[rr * PSTR + col] = pixel_fast<PERIODIC>(__ldg(a.bore + ts), off, a.ny, a.nx, npix);
+        }
+        __syncthreads();
+        const int4 P0 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * bq);
+        const int4 P1 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * bq + 4);
+        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
+        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
+      } else {
+        const int4 P0 = __ldcs(reinterpret_cast<const int4*>(pixd + t));
+        const int4 P1 = __ldcs(reinterpret_cast<const int4*>(pixd + t + 4));
+        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
+        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
       }
-      warp_bin<NC, J>(a.acc32, p0, p1, v0, v1, npix);
+      const float4 A = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * bq);
+      const float4 B = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * bq + 2);
+      float u[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+      float cc[8], ss[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) u[k] *= scale;
+      if (NC == 3) {
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          const float4 r2 = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k));
+          cc[k] = pol.x * r2.x - pol.y * r2.y;
+          ss[k] = pol.y * r2.x + pol.x * r2.y;
+          cc[k + 1] = pol.x * r2.z - pol.y * r2.w;
+          ss[k + 1] = pol.y * r2.z + pol.x * r2.w;
+        }
+      }
+      bin_run8<NC>(a.acc32, p, u, cc, ss, npix);
+      if constexpr (!CACHED) __syncthreads();   // the staging is rewritten by the next pass
     }
   }
 }
@@ -453,6 +494,30 @@ __global__ void k_fast_flush(float* __restrict__ acc32, double* __restrict__ acc
   }
 }
 
+// ------------------------------------------------------------------ pointing cache
+// pix[d][t] = pixel of sample t of detector d (npix outside the map), by the rule
+// of the on-the-fly kernels.
+template <bool PERIODIC>
+__global__ void k_fill_pixels(const TodArgs a, int n_det, int* __restrict__ pix) {
+  const long long total = (long long)n_det * a.n_t;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int d = (int)(q / a.n_t);
+    const int t = (int)(q - (long long)d * a.n_t);
+    pix[q] = pixel_fast<PERIODIC>(__ldg(a.bore + t), a.det_off[d], a.ny, a.nx, (int)a.npix);
+  }
+}
+
+int launch_fill_pixels(cmm_op* op) {
+  TodArgs a = make_args(op, 0);
+  const long long total = (long long)op->pt->n_det * op->pt->n_t;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  if (a.periodic) k_fill_pixels<true><<<blocks, 256, 0, op->ctx->stream>>>(a, op->pt->n_det, op->pix);
+  else k_fill_pixels<false><<<blocks, 256, 0, op->ctx->stream>>>(a, op->pt->n_det, op->pix);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
 // ------------------------------------------------------------------ dispatch
 
 // Fast-path split of N = 2^logN: R = 64 below 2^16, 128 for 2^16 and 2^17, 256 for
@@ -469,22 +534,37 @@ bool fast_path_ok(const cmm_op* op) {
   return fast_path_sizes(op->logR + op->logC, op->prec, &lr, &lc) && lr == op->logR;
 }
 
-template <int NC, typename S, int R, bool PERIODIC>
-static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
+template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
+static int run_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
   constexpr int J = ColShape<R>::J;
   constexpr int NT = ColShape<R>::THREADS;
-  const int smem = (int)(sizeof(float2) * R * J);
+  // forward: FFT tile R x J complex.  inverse: binning tile R x (J + 2) complex,
+  // then the pixel staging of one binning pass, (threads / (J / 4)) rows x (2 J + 4) ints
+  const int smem_f = (int)(sizeof(float2) * R * J);
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * (NT / (J / 4)) * (2 * J + 4));
   if (attr_only) {
-    CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  smem));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_f));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_inv_bin<NC, S, R, PERIODIC, CACHED>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_i));
     return CMM_OK;
   }
   const dim3 g(a.C / J, (nd + kDetsPerCta - 1) / kDetsPerCta);
-  if (pass == 0) k_fast_fwd<NC, S, R, PERIODIC><<<g, NT, smem, st>>>(a, nd);
-  else k_fast_inv_bin<NC, S, R, PERIODIC><<<g, NT, smem, st>>>(a, nd);
+  if (pass == 0) k_fast_fwd<NC, S, R, PERIODIC, CACHED><<<g, NT, smem_f, st>>>(a, nd);
+  else k_fast_inv_bin<NC, S, R, PERIODIC, CACHED><<<g, NT, smem_i, st>>>(a, nd);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
+}
+
+// The cached-pixel kernels exist only for the non-periodic map (the periodic
+// boundary is a test geometry).
+template <int NC, typename S, int R, bool PERIODIC>
+static int run_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
+  if constexpr (!PERIODIC) {
+    if (attr_only) CMM_TRY((run_T_c<NC, S, R, false, true>(a, nd, pass, st, true)));
+    else if (a.pix) return run_T_c<NC, S, R, false, true>(a, nd, pass, st, false);
+  }
+  return run_T_c<NC, S, R, PERIODIC, false>(a, nd, pass, st, attr_only);
 }
 
 template <int NC, typename S, bool PERIODIC>

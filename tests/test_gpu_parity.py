@@ -122,6 +122,36 @@ def test_handles_destroyed_out_of_order(cmm):
     pc.h = None
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_pixel_cache_same_result(cmm, ctx, prec, ncomp):
+    """A with the cached pixel indices equals A with on-the-fly pointing (same pixels,
+    same arithmetic; only the order of the FP32 atomic additions into the partial
+    map differs between runs, so agreement is to FP32 rounding), including samples
+    outside the map."""
+    scan = gen.small_scan(cfg=211, ny=20, nx=18, n_t=1 << 13, ncols=4, nrows=2, throw_px=40.0, ncomp=ncomp)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=211)
+    op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=3)
+    m = dev(gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=212)[0])
+    y0 = host(op.apply(m))
+    op.set_pixel_cache(True)
+    y1 = host(op.apply(m))
+    assert rel(y1, y0) < 1e-6
+    op.set_pixel_cache(False)
+    assert rel(host(op.apply(m)), y0) < 1e-6
+    oop = om.make_operator(scan, noise)
+    assert rel(y1, om.apply_A(oop, gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=212)[0])) < TOL[prec]
+
+
+def test_pixel_cache_rejected_where_unsupported(cmm, ctx):
+    scan, noise = small(3)
+    with pytest.raises(cmm.CmmError):
+        cmm.Operator(ctx, scan, noise, precision=0).set_pixel_cache(True)
+    scan, noise = small(3, periodic=True)
+    with pytest.raises(cmm.CmmError):
+        cmm.Operator(ctx, scan, noise, precision=1).set_pixel_cache(True)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_apply_A_periodic(cmm, ctx, prec):
     scan, noise = small(3, periodic=True)
@@ -276,6 +306,8 @@ def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
     m = gen.sky_map(scan.ny, scan.nx, cfg=2)
     y = host(op.apply(dev(m)))
     assert rel(y, om.apply_A(oop, m)) < TOL[prec]
+    op.set_pixel_cache(True)
+    assert rel(host(op.apply(dev(m))), y) < 1e-6
 
 
 @pytest.mark.parametrize("ncomp", [1, 3])
@@ -306,6 +338,8 @@ def test_full_size_symmetry_and_rhs(cmm, ctx):
     b1 = host(op.rhs(op.project(m, dtype=torch.float32)))
     b2 = host(op.apply(m))
     assert rel(b1, b2) < 1e-5
+    op.set_pixel_cache(True)
+    assert rel(host(op.apply(m)), b2) < 1e-6
 
 
 # ---------------------------------------------------------------- precision modes (config 3)
