@@ -8,7 +8,8 @@
 // u + m E/R), so only the outputs of non-final stages go through shared memory:
 // a sequence of S stages costs S - 1 exchanges, each one store and one load per
 // element, instead of a load and a store per stage.  Twiddles w_{PR}^{mk} come
-// from a table of w_L^e, e < L (forward sign, conjugated for SIGN > 0).
+// from a table of w_L^e, e < L (forward sign, conjugated for SIGN > 0): the powers
+// of two are loaded and the other exponents formed as products.
 #pragma once
 
 #include "common.cuh"
@@ -37,12 +38,21 @@ __device__ __forceinline__ void rfft_stages(float2 (&x)[E], const int i, const f
 #pragma unroll
     for (int m = 0; m < R; ++m) z[m] = x[u + m * NB];
     if constexpr (P > 1) {
+      // w^m for m < R from the table entries w^1, w^2, w^4, w^8 and products of
+      // them (at most three roundings deep): four L1 loads per butterfly instead of
+      // R - 1, the rest on the FP32 pipe
+      float2 wp[R];
+      const int b = k * (L / (P * R));
 #pragma unroll
-      for (int m = 1; m < R; ++m) {
-        float2 w = __ldg(tw + (m * k) * (L / (P * R)));
-        if (SIGN > 0) w.y = -w.y;
-        z[m] = cmul(z[m], w);
+      for (int m = 1; m < R; m *= 2) {
+        wp[m] = __ldg(tw + m * b);
+        if (SIGN > 0) wp[m].y = -wp[m].y;
       }
+#pragma unroll
+      for (int m = 3; m < R; ++m)
+        if (m & (m - 1)) wp[m] = cmul(wp[m & (m - 1)], wp[m & -m]);
+#pragma unroll
+      for (int m = 1; m < R; ++m) z[m] = cmul(z[m], wp[m]);
     }
     dft_reg<float, clog2(R), SIGN>(z);
     if constexpr (LAST) {

@@ -36,7 +36,7 @@ namespace cmm {
 #define CMM_COL_THREADS_PER_SM 1024
 #endif
 #ifndef CMM_FILTER_MINB
-#define CMM_FILTER_MINB 3
+#define CMM_FILTER_MINB 4
 #endif
 #ifndef CMM_GEN_UNROLL
 #define CMM_GEN_UNROLL 2
