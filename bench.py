@@ -42,8 +42,13 @@ def parse():
     ap.add_argument("--n-det", type=int, default=1024)
     ap.add_argument("--n-t", type=int, default=1 << 20)
     ap.add_argument("--det-chunk", type=int, default=0)
-    ap.add_argument("--taper", type=float, default=20.0)
+    ap.add_argument("--taper", type=float, default=10.0,
+                    help="Gaussian taper of the circulant preconditioner in pixels (10: best of the sweep "
+                         "{5, 10, 20, 40, inf} on this scan; the paper's ACT value 20 is solved beside it)")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-6 solves")
+    ap.add_argument("--pointing", choices=["cached", "on-the-fly"], default="cached",
+                    help="cached: pixel index per sample stored once (4 B/sample); on-the-fly: recomputed "
+                         "in both column passes of every application")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--workload", choices=["apply", "learned"], default="apply",
                     help="apply: the A-application inside circulant PCG (default); learned: the learned "
@@ -57,7 +62,7 @@ def workload(args):
     return {"workload": f"ACT-like patch: {args.n_det} det hex 1 deg, {args.n_t} samples/det at 400 Hz, "
                         f"10 deg throw rising+setting, 1200x900 TQU CAR 0.5'",
             "n_det": args.n_det, "n_samp": args.n_t, "map": [3, 900, 1200],
-            "precon": "circulant", "taper_sigma_px": args.taper,
+            "precon": "circulant", "taper_sigma_px": args.taper, "pointing": args.pointing,
             "l2": "no flush: 4.3 GB of spectra streamed per step exceed the 129 MB L2"}
 
 
@@ -169,6 +174,8 @@ def run_ours(args, rank, world):
     with torch.cuda.stream(stream):
         ctx = cmm.Context(dev, stream=stream.cuda_stream)
         op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=args.det_chunk)
+        if args.pointing == "cached" and prec != cmm.PREC_F64:
+            op.set_pixel_cache(True)
         m_sky = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=2, real=rank), device=f"cuda:{dev}")
         tod = op.project(m_sky)                 # noise-free TOD, as in the paper's test
         b = op.rhs(tod)
@@ -209,6 +216,11 @@ def run_ours(args, rank, world):
     with torch.cuda.stream(stream):
         mo = op.new_map()
         prof = cmm.cmm_profile_apply(op.h, b, mo, 5)
+        prof_otf = None
+        if args.pointing == "cached" and prec != cmm.PREC_F64:
+            op.set_pixel_cache(False)
+            prof_otf = cmm.cmm_profile_apply(op.h, b, mo, 3)
+            op.set_pixel_cache(True)
     names = ["k_tod_fwd (pointing+gather+FFT pass 1)", "k_tod_filter (FFT pass 2 + N^-1)",
              "k_tod_inv_bin (inverse FFT pass + P^T)"]
     chunk_dets = min(op_chunk(op, scan, args), scan.n_det)
@@ -221,6 +233,8 @@ def run_ours(args, rank, world):
     achieved = per_launch_bytes[dom] / (prof[dom] / 1e3) / 1e9
     apply_bytes = 2 * elt * n_s + 16 * scan.n_t + scan.npix * (3 * 8 * 2 + 16 * 2)
     apply_gbs = apply_bytes / (prof[4] / 1e3) / 1e9
+
+    cufft = cufft_filter_ms(scan, noise, dev, stream) if args.prec == "f32" else None
 
     # end to end through the host-buffer entry point: H2D map, A, D2H map per step
     m_host = torch.empty((3, scan.ny, scan.nx), dtype=torch.float64).pin_memory()
@@ -240,13 +254,15 @@ def run_ours(args, rank, world):
         solves = {}
         with torch.cuda.stream(stream):
             for name, kind, kw in (("binned", cmm.PRECON_BINNED, {}),
-                                   ("circulant", cmm.PRECON_CIRCULANT, {"taper_sigma_px": args.taper})):
+                                   ("jacobi", cmm.PRECON_JACOBI, {}),
+                                   ("circulant", cmm.PRECON_CIRCULANT, {"taper_sigma_px": args.taper}),
+                                   ("circulant_taper20", cmm.PRECON_CIRCULANT, {"taper_sigma_px": 20.0})):
+                if name == "circulant_taper20" and args.taper == 20.0:
+                    continue
                 t1 = time.perf_counter()
                 p2 = pc if name == "circulant" else cmm.Precon(op, kind, **kw)
                 torch.cuda.synchronize()
-                build_s = 0.0 if name == "circulant" else time.perf_counter() - t1
-                if name == "circulant":
-                    build_s = t_pc
+                build_s = t_pc if name == "circulant" else time.perf_counter() - t1
                 x, info, _, _ = cmm.solve(op, p2, b, tol=1e-6, maxit=1000, check_every=10)
                 solves[name] = {"iterations": info.iterations, "status": cmm.STATUS[info.status],
                                 "seconds": round(info.seconds, 4), "build_seconds": round(build_s, 4),
@@ -260,22 +276,23 @@ def run_ours(args, rank, world):
                    "global_batch": world, "seq_len": scan.n_t},
         "gpu_launches": None,
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(dom, chunk_dets, args),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                      "algorithmic_bytes_per_launch": per_launch_bytes[dom]},
         "apply": {"ms": prof[4], "samples_per_s": n_s / (prof[4] / 1e3), "algorithmic_GBps": apply_gbs,
                   "frac_of_measured_hbm": apply_gbs / peak,
                   "ms_per_pass": {"fwd": prof[0], "filter": prof[1], "inv_bin": prof[2], "map_copies": prof[3]},
-                  "det_chunk": chunk_dets},
+                  "det_chunk": chunk_dets,
+                  "on_the_fly_pointing_ms": None if prof_otf is None else prof_otf[4]},
         "e2e": {"value": n_s / e2e_s, "unit": UNIT, "h2d_bytes_per_step": map_bytes, "d2h_bytes_per_step": map_bytes,
                 "step": "cmm_apply_A_host: H2D map, A, D2H map"},
         "solves_to_1e-6": solves,
+        "cufft_comparison": cufft,
         "setup_seconds": round(setup_s, 2),
         "clocks": clocks,
     }
-    nchunks = math.ceil(scan.n_det / chunk_dets)
-    it_launches = 3 * nchunks + 2 + 6 + 12   # A (3 per chunk + 2 map copies), CG kernels, circulant apply
-    out["gpu_launches"] = it_launches * args.steps
+    out["gpu_launches"] = launches_per_iteration(scan.n_det, chunk_dets) * args.steps
     return out
 
 
@@ -339,6 +356,76 @@ def run_learned(args):
         "val_loss": {"zero_output": float(0.5 * (vt.double() ** 2).mean()), "trained": hist[-1][2]},
         "harvest_seconds": round(harvest_s, 2), "train_seconds": round(train_s, 2),
     }
+
+
+def cufft_filter_ms(scan, noise, dev, stream):
+    """Timed comparison only: the noise filter N^-1 alone (rfft, multiply by w_d(f),
+    irfft) on the same [n_det][n_samp] FP32 time-ordered data through cuFFT
+    (torch.fft), without the pointing, the gather and the binning that the
+    library's three passes also do."""
+    import torch
+    with torch.cuda.stream(stream):
+        g = torch.Generator(device=f"cuda:{dev}").manual_seed(0)
+        d = torch.randn((scan.n_det, scan.n_t), device=f"cuda:{dev}", dtype=torch.float32, generator=g)
+        f = torch.arange(scan.n_t // 2 + 1, device=f"cuda:{dev}", dtype=torch.float32) * (scan.f_samp / scan.n_t)
+        f[0] = f[1]
+        sig = torch.as_tensor(noise.sigma, device=f"cuda:{dev}", dtype=torch.float32)[:, None]
+        fk = torch.as_tensor(noise.fknee, device=f"cuda:{dev}", dtype=torch.float32)[:, None]
+        al = torch.as_tensor(noise.alpha, device=f"cuda:{dev}", dtype=torch.float32)[:, None]
+        w = (1.0 / sig ** 2) / (1.0 + (f[None, :] / fk) ** (-al))
+        def run():
+            return torch.fft.irfft(torch.fft.rfft(d, dim=1) * w, n=scan.n_t, dim=1)
+        for _ in range(2):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        del d, w
+        torch.cuda.empty_cache()
+    return {"what": "N^-1 only via cuFFT (torch.fft rfft * w irfft), FP32, same n_det x n_samp; "
+                    "excludes P and P^T", "ms": ms}
+
+
+def launches_per_iteration(n_det, chunk):
+    """Kernels of one circulant-PCG iteration: the A-application (map copy in, per
+    chunk one forward and one filter launch and per 128 detectors one inverse +
+    binning launch and one flush, map copy out), the CG update kernels and the
+    circulant preconditioner (Sigma^-1, 2-D FFTs, per-mode solve)."""
+    a = 2
+    for d0 in range(0, n_det, chunk):
+        nd = min(chunk, n_det - d0)
+        a += 2 + 2 * math.ceil(nd / 128)
+    return a + CG_LAUNCHES + CIRC_LAUNCHES
+
+
+# kernels per iteration outside the A-application, from the launch list of this
+# bench (profiles/apply_kernels_1024x2p20.md)
+CG_LAUNCHES = 7
+CIRC_LAUNCHES = 12
+
+
+def measured_traffic(dom, chunk_dets, args):
+    """DRAM bytes of the dominant pass over one chunk of detectors (one launch for
+    the forward and filter passes; the inverse pass is one launch per 128
+    detectors), from the committed ncu summary (bytes per detector, scaled to the
+    chunk); None if the kernels have changed since it was taken or no summary
+    covers this configuration."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1309_7473_gb300", "csrc", "tod_fast.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    key = f"{args.prec}/{args.pointing}/{args.n_t}"
+    if rec.get("tod_fast_sha256") != digest or key not in rec.get("bytes_per_detector", {}):
+        return None
+    return rec["bytes_per_detector"][key][dom] * chunk_dets
 
 
 def op_chunk(op, scan, args):
