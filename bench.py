@@ -263,7 +263,7 @@ def run_ours(args, rank, world):
                 p2 = pc if name == "circulant" else cmm.Precon(op, kind, **kw)
                 torch.cuda.synchronize()
                 build_s = t_pc if name == "circulant" else time.perf_counter() - t1
-                x, info, _, _ = cmm.solve(op, p2, b, tol=1e-6, maxit=1000, check_every=10)
+                x, info, _, _ = cmm.solve(op, p2, b, tol=1e-6, maxit=2000, check_every=10)
                 solves[name] = {"iterations": info.iterations, "status": cmm.STATUS[info.status],
                                 "seconds": round(info.seconds, 4), "build_seconds": round(build_s, 4),
                                 "rel_resid": info.rel_resid}
