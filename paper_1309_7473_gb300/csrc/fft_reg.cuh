@@ -15,6 +15,13 @@
 #include "common.cuh"
 #include "fft.cuh"
 
+// Stage twiddles w^m, m < R: 1 (default) by recurrence from one loaded w (two live
+// registers, relative error growing to ~R ulp); 0 from the loaded w, w^2, w^4, w^8
+// and products (at most three roundings, more live registers).
+#ifndef CMM_TW_MODE
+#define CMM_TW_MODE 1
+#endif
+
 namespace cmm {
 
 constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
@@ -38,11 +45,20 @@ __device__ __forceinline__ void rfft_stages(float2 (&x)[E], const int i, const f
 #pragma unroll
     for (int m = 0; m < R; ++m) z[m] = x[u + m * NB];
     if constexpr (P > 1) {
-      // w^m for m < R from the table entries w^1, w^2, w^4, w^8 and products of
-      // them (at most three roundings deep): four L1 loads per butterfly instead of
-      // R - 1, the rest on the FP32 pipe
-      float2 wp[R];
+      // one or four L1 loads per butterfly instead of R - 1, the rest on the FP32 pipe
       const int b = k * (L / (P * R));
+#if CMM_TW_MODE == 1
+      // w^m by recurrence from w (two live twiddles)
+      float2 w1 = __ldg(tw + b);
+      if (SIGN > 0) w1.y = -w1.y;
+      float2 wm = w1;
+#pragma unroll
+      for (int m = 1; m < R; ++m) {
+        z[m] = cmul(z[m], wm);
+        if (m + 1 < R) wm = cmul(wm, w1);
+      }
+#else
+      float2 wp[R];
 #pragma unroll
       for (int m = 1; m < R; m *= 2) {
         wp[m] = __ldg(tw + m * b);
@@ -53,6 +69,7 @@ __device__ __forceinline__ void rfft_stages(float2 (&x)[E], const int i, const f
         if (m & (m - 1)) wp[m] = cmul(wp[m & (m - 1)], wp[m & -m]);
 #pragma unroll
       for (int m = 1; m < R; ++m) z[m] = cmul(z[m], wp[m]);
+#endif
     }
     dft_reg<float, clog2(R), SIGN>(z);
     if constexpr (LAST) {

@@ -35,6 +35,9 @@ namespace cmm {
 #ifndef CMM_COL_THREADS_PER_SM
 #define CMM_COL_THREADS_PER_SM 1024
 #endif
+#ifndef CMM_INV_THREADS_PER_SM
+#define CMM_INV_THREADS_PER_SM 768
+#endif
 #ifndef CMM_FILTER_MINB
 #define CMM_FILTER_MINB 4
 #endif
@@ -58,6 +61,7 @@ template <int R> struct ColShape {
   static constexpr int J = R >= 256 ? 16 : 32;
   static constexpr int THREADS = J * R / kE;
   static constexpr int MINB = CMM_COL_THREADS_PER_SM / THREADS > 0 ? CMM_COL_THREADS_PER_SM / THREADS : 1;
+  static constexpr int MINB_INV = CMM_INV_THREADS_PER_SM / THREADS > 0 ? CMM_INV_THREADS_PER_SM / THREADS : 1;
 };
 
 // GB300's FP64 unit also executes int <-> float conversions, at a small fraction
@@ -379,7 +383,7 @@ __device__ __forceinline__ void bin_run8(float* acc32, const int (&p)[8], const 
 }
 
 template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
-__global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fast_inv_bin(const TodArgs a, int nd) {
+__global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
   constexpr int J = ColShape<R>::J;
   if (a.done && *a.done) return;
