@@ -50,9 +50,11 @@ def parse():
                     help="cached: pixel index per sample stored once (4 B/sample); on-the-fly: recomputed "
                          "in both column passes of every application")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["apply", "learned"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "learned", "batch"], default="apply",
                     help="apply: the A-application inside circulant PCG (default); learned: the learned "
                          "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
+    ap.add_argument("--batch", type=int, default=64, help="solves of the batch workload")
+    ap.add_argument("--batch-iters", type=int, default=20, help="PCG iterations timed per solve")
     ap.add_argument("--learned-reals", type=int, default=100)
     ap.add_argument("--learned-epochs", type=int, default=15)
     return ap.parse_args()
@@ -428,6 +430,67 @@ def measured_traffic(dom, chunk_dets, args):
     return rec["bytes_per_detector"][key][dom] * chunk_dets
 
 
+def run_batch(args):
+    """Batched Monte-Carlo solves: args.batch seeded problems of uneven size (detectors,
+    samples, map), each with its own sky, circulant preconditioner and context;
+    args.batch_iters PCG iterations of all of them through cmm_batch_solve (one CUDA
+    graph per check interval, problems as parallel branches) against the same
+    iterations solved one after another."""
+    import torch
+
+    import gen
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm
+    probs = [gen.config4(k) for k in range(args.batch)]
+    n_s = [sc.n_det * sc.n_t for sc, _ in probs]
+    # device memory: spectrum chunk (4 B/sample, at most 8 GB) per operator + tables
+    need = sum(min(4 * n, 8 << 30) + 32 * sc.n_t + 200 * sc.npix for n, (sc, _) in zip(n_s, probs))
+    free, _ = torch.cuda.mem_get_info()
+    if need > 0.6 * free:
+        raise SystemExit(f"batch needs ~{need / 1e9:.0f} GB, more than 60% of the {free / 1e9:.0f} GB free")
+    t0 = time.perf_counter()
+    ctxs, ops, pcs, bs, xs = [], [], [], [], []
+    for k, (scan, noise) in enumerate(probs):
+        ctx = cmm.Context(0)
+        op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F32)
+        m = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=4, real=k), device="cuda:0")
+        bs.append(op.rhs(op.project(m)))
+        pcs.append(cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=args.taper))
+        ctxs.append(ctx)
+        ops.append(op)
+        xs.append(op.new_map())
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    it = args.batch_iters
+    hs = [o.h for o in ops]
+    ph = [p.h for p in pcs]
+    cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=2, check_every=2)   # warm-up (graph, kernels)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=it, check_every=it)
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for o, p, b in zip(ops, pcs, bs):
+        cmm.solve(o, p, b, tol=0.0, maxit=it, check_every=it)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    total = sum(n_s) * it
+    return {
+        "metric": "samples/s per batched P^T N^-1 P apply (circulant PCG, uneven solves)",
+        "value": total / batched_s, "unit": "samples/s", "higher_is_better": True, "n_gpus": 1,
+        "steps": it, "warmup": 2, "dtype": "f32 (FP64 CG)", "data": "synthetic",
+        "config": {"workload": f"{args.batch} seeded solves: n_det in {{128..1024}}, n_samp in {{2^18..2^20}}, "
+                               f"maps 256x256..1200x900 TQU, circulant taper {args.taper} px",
+                   "samples_per_iteration": sum(n_s),
+                   "sizes": sorted({(sc.n_det, sc.n_t, sc.ny, sc.nx) for sc, _ in probs})[:8]},
+        "batched_seconds": batched_s, "sequential_seconds": seq_s,
+        "sequential_samples_per_s": total / seq_s, "speedup": seq_s / batched_s,
+        "setup_seconds": round(setup_s, 1),
+    }
+
+
 def op_chunk(op, scan, args):
     if args.det_chunk > 0:
         return args.det_chunk
@@ -465,6 +528,10 @@ def main():
     if args.workload == "learned":
         if rank == 0:
             print(json.dumps(run_learned(args)))
+        return 0
+    if args.workload == "batch":
+        if rank == 0:
+            print(json.dumps(run_batch(args)))
         return 0
     if world > 1:
         import torch

@@ -3,10 +3,10 @@
 No map-making arithmetic lives here: only scan tables, focal planes, noise
 parameters and random skies / noise streams (see ``gen.inputs``).
 """
-from .inputs import (QB, QD, QR, Noise, Scan, bccb_scan, config1, config2, config2_noise,
+from .inputs import (QB, QD, QR, Noise, Scan, bccb_scan, config1, config2, config2_noise, config4,
                      grid_focal_plane, hex_focal_plane, make_scan, noise_params, noise_tod,
                      random_maps, rng, sky_map, small_scan)
 
-__all__ = ["QB", "QD", "QR", "Noise", "Scan", "bccb_scan", "config1", "config2", "config2_noise",
+__all__ = ["QB", "QD", "QR", "Noise", "Scan", "bccb_scan", "config1", "config2", "config2_noise", "config4",
            "grid_focal_plane", "hex_focal_plane", "make_scan", "noise_params", "noise_tod",
            "random_maps", "rng", "sky_map", "small_scan"]

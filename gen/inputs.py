@@ -232,6 +232,31 @@ def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3):
     return scan, config2_noise(real, n_det)
 
 
+CONFIG4_MAPS = ((256, 256), (240, 320), (360, 480), (450, 600), (600, 800), (750, 1000), (900, 1200))
+
+
+def config4(k, real=0, ncomp=3):
+    """Problem k of the batched Monte-Carlo workload: seeded n_det from
+    {128, 256, 512, 1024}, n_t from {2^18, 2^19, 2^20} and a 5-smooth map size from
+    256x256 to 1200x900 (ny x nx) at 0.5'; hex focal plane at 1.667', the config-2
+    scan law (rising and setting halves) with a throw of 0.8 of the map width; the
+    config-1 noise law (sigma 1, f_knee 2 Hz, alpha 3.5)."""
+    g = rng(4, 1000 * real + k, "misc")
+    n_det = int(g.choice([128, 256, 512, 1024]))
+    n_t = int(g.choice([1 << 18, 1 << 19, 1 << 20]))
+    ny, nx = CONFIG4_MAPS[int(g.integers(len(CONFIG4_MAPS)))]
+    rings = 1
+    while 3 * rings * (rings + 1) + 1 < n_det:
+        rings += 1
+    focal = hex_focal_plane(n_det, rings, (60.0 / 36.0) / PIX_ARCMIN)
+    px_per_deg = 60.0 / PIX_ARCMIN
+    scan = make_scan(cfg=4, real=1000 * real + k, ny=ny, nx=nx, n_t=n_t, focal_px=focal,
+                     speed_px_s=1.0 * px_per_deg, throw_px=0.8 * nx,
+                     segments=((0.5, 10.0, 40.0, True), (0.5, -10.0, -40.0, False)), ncomp=ncomp)
+    noise = Noise(np.ones(n_det), np.full(n_det, 2.0), np.full(n_det, 3.5))
+    return scan, noise
+
+
 def config2_noise(real, n_det):
     s = math.sqrt(math.log(1.04))
     mu = -0.5 * math.log(1.04)
