@@ -449,11 +449,14 @@ def run_batch(args):
     free, _ = torch.cuda.mem_get_info()
     if need > 0.6 * free:
         raise SystemExit(f"batch needs ~{need / 1e9:.0f} GB, more than 60% of the {free / 1e9:.0f} GB free")
+    cache = args.pointing == "cached" and need + 4 * sum(n_s) <= 0.6 * free   # + 4 B/sample of pixel indices
     t0 = time.perf_counter()
     ctxs, ops, pcs, bs, xs = [], [], [], [], []
     for k, (scan, noise) in enumerate(probs):
         ctx = cmm.Context(0)
         op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F32)
+        if cache:
+            op.set_pixel_cache(True)
         m = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=4, real=k), device="cuda:0")
         bs.append(op.rhs(op.project(m)))
         pcs.append(cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=args.taper))
@@ -467,10 +470,13 @@ def run_batch(args):
     ph = [p.h for p in pcs]
     cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=2, check_every=2)   # warm-up (graph, kernels)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=it, check_every=it)
-    torch.cuda.synchronize()
-    batched_s = time.perf_counter() - t0
+    by_width = {}
+    for w in (0, 2, 4):
+        t0 = time.perf_counter()
+        cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=it, check_every=it, width=w)
+        torch.cuda.synchronize()
+        by_width["auto" if w == 0 else w] = time.perf_counter() - t0
+    batched_s = by_width["auto"]
     t0 = time.perf_counter()
     for o, p, b in zip(ops, pcs, bs):
         cmm.solve(o, p, b, tol=0.0, maxit=it, check_every=it)
@@ -483,9 +489,9 @@ def run_batch(args):
         "steps": it, "warmup": 2, "dtype": "f32 (FP64 CG)", "data": "synthetic",
         "config": {"workload": f"{args.batch} seeded solves: n_det in {{128..1024}}, n_samp in {{2^18..2^20}}, "
                                f"maps 256x256..1200x900 TQU, circulant taper {args.taper} px",
-                   "samples_per_iteration": sum(n_s),
+                   "samples_per_iteration": sum(n_s), "pointing": "cached" if cache else "on-the-fly",
                    "sizes": sorted({(sc.n_det, sc.n_t, sc.ny, sc.nx) for sc, _ in probs})[:8]},
-        "batched_seconds": batched_s, "sequential_seconds": seq_s,
+        "batched_seconds": batched_s, "batched_seconds_by_width": by_width, "sequential_seconds": seq_s,
         "sequential_samples_per_s": total / seq_s, "speedup": seq_s / batched_s,
         "setup_seconds": round(setup_s, 1),
     }

@@ -93,6 +93,7 @@ typedef struct {
   int32_t flexible;    /* != 0: flexible CG, beta = z^T (r - r_old) / (z_old^T r_old) */
   int32_t snapshot_every; /* with a snapshot buffer: keep (x_k, r_k) every that many iterations */
   int32_t snapshot_max;   /* number of snapshot slots */
+  int32_t batch_width;    /* cmm_batch_solve: concurrent lanes (<= 0: automatic) */
 } cmm_solve_opts;
 
 typedef struct {
@@ -298,9 +299,13 @@ int cmm_unet_train_step(cmm_unet* net, int32_t batch, const float* in, const flo
  * Batched solves (many Monte-Carlo realisations or patches of uneven size): n
  * independent PCG solves, one per (ops[i], pcs[i], b[i], x[i]), are advanced
  * together; every `check_every` iterations of the whole batch are one CUDA graph
- * launch in which the solves are parallel branches, each on the stream of its own
- * context (give each operator its own context for the solves to overlap).  A solve
- * that has converged keeps returning early inside the graph.  opts as in
+ * launch.  Inside it the solves run in opts->batch_width parallel lanes (solves
+ * assigned largest first to the least loaded lane, one after another within a
+ * lane), each solve on the stream of its own context (give each operator its own
+ * context for the lanes to overlap).  Automatic width: 1 when the solves average
+ * 10^7 samples or more (each alone fills the GPU, and concurrent ones only share
+ * the L2 their maps live in), else up to 8.  A solve that has converged keeps
+ * returning early inside the graph.  opts as in
  * cmm_solve (resid_replace must be 0); infos[i] receives each solve's result, its
  * `seconds` the wall time of the whole batch.  Waits for the result.
  */

@@ -43,7 +43,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
                 ("resid_replace", C.c_int32), ("flexible", C.c_int32), ("snapshot_every", C.c_int32),
-                ("snapshot_max", C.c_int32)]
+                ("snapshot_max", C.c_int32), ("batch_width", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -354,12 +354,14 @@ def cmm_unet_train_step(h, x, target, lr):
     return loss.value
 
 
-def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f32=False, flexible=False):
+def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f32=False, flexible=False,
+                    width=0):
     """Batched PCG over parallel lists of operator / preconditioner handles and
     device maps; returns the list of SolveInfo."""
     n = len(ops)
     arr = lambda items: (C.c_void_p * n)(*[C.c_void_p(v if isinstance(v, int) else v.value) for v in items])
-    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0)
+    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0,
+                     0, 0, int(width))
     infos = (SolveInfo * n)()
     _check(_lib.cmm_batch_solve(n, arr(ops), arr(pcs), arr([t.data_ptr() for t in bs]),
                                 arr([t.data_ptr() for t in xs]), C.byref(opts), infos))

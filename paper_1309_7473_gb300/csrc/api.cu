@@ -1159,7 +1159,25 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
   }
   for (int i = 0; i < n; ++i) CMM_CUDA(cudaStreamSynchronize(ops[i]->ctx->stream));
   const int per = std::max(1, opts->check_every);
-  // one graph per `per` batch iterations: every solve is a parallel branch
+  // lanes: solves sorted by samples, each to the least loaded lane
+  std::vector<long long> work(n);
+  for (int i = 0; i < n; ++i) work[i] = (long long)ops[i]->pt->n_det * ops[i]->pt->n_t;
+  long long total = 0;
+  for (long long w : work) total += w;
+  int width = opts->batch_width > 0 ? opts->batch_width : (total / n >= 10000000LL ? 1 : 8);
+  width = std::max(1, std::min(width, n));
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return work[p] > work[q]; });
+  std::vector<std::vector<int>> lanes(width);
+  std::vector<long long> load(width, 0);
+  for (int i : order) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[l].push_back(i);
+    load[l] += work[i];
+  }
+  // one graph per `per` batch iterations: the lanes are parallel branches, the
+  // solves of a lane follow one another
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev(n + 1, nullptr);
@@ -1168,16 +1186,21 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
     CMM_CUDA(cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal));
     int s2 = CMM_OK;
     cudaError_t e = cudaEventRecord(ev[n], main_st);
-    for (int i = 0; i < n && s2 == CMM_OK && e == cudaSuccess; ++i) {
-      cudaStream_t st = ops[i]->ctx->stream;
-      if (st != main_st) e = cudaStreamWaitEvent(st, ev[n], 0);
-      for (int k = 0; k < per && s2 == CMM_OK && e == cudaSuccess; ++k)
-        s2 = solve_iteration(ops[i], pcs[i], x[i], vb[i], dst[i], nullptr, nullptr, flex[i]);
-      if (e == cudaSuccess && st != main_st) {
-        e = cudaEventRecord(ev[i], st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(main_st, ev[i], 0);
+    for (int l = 0; l < width && s2 == CMM_OK && e == cudaSuccess; ++l) {
+      cudaEvent_t prev = ev[n];   // the lane starts at the fork
+      for (size_t q = 0; q < lanes[l].size() && s2 == CMM_OK && e == cudaSuccess; ++q) {
+        const int i = lanes[l][q];
+        cudaStream_t st = ops[i]->ctx->stream;
+        e = cudaStreamWaitEvent(st, prev, 0);
+        for (int k = 0; k < per && s2 == CMM_OK && e == cudaSuccess; ++k)
+          s2 = solve_iteration(ops[i], pcs[i], x[i], vb[i], dst[i], nullptr, nullptr, flex[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], st);
+        prev = ev[i];
       }
+      if (e == cudaSuccess && prev != ev[n]) e = cudaStreamWaitEvent(main_st, prev, 0);   // join
     }
+    // every stream that took part rejoins the capturing stream
+    for (int i = 0; i < n && s2 == CMM_OK && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(main_st, ev[i], 0);
     cudaError_t e2 = cudaStreamEndCapture(main_st, &graph);
     if (s2 != CMM_OK) return s2;
     if (e != cudaSuccess) return cuda_fail(e, "batch graph capture", __FILE__, __LINE__);

@@ -416,6 +416,13 @@ def test_batch_solve_matches_individual_solves(cmm):
         refs.append(om.pcg(lambda v, oop=oop: om.apply_A(oop, v), mo, b_ref, tol=1e-9, maxit=500))
     infos = cmm.cmm_batch_solve([o.h for o in ops], [p.h for p in pcs], bs, xs, tol=1e-9, maxit=500,
                                 check_every=7)
+    # the same with two lanes (one solve after another inside a lane)
+    xs2 = [op.new_map() for op in ops]
+    infos2 = cmm.cmm_batch_solve([o.h for o in ops], [p.h for p in pcs], bs, xs2, tol=1e-9, maxit=500,
+                                 check_every=5, width=2)
+    for k in range(len(ops)):
+        assert infos2[k].iterations == infos[k].iterations
+        assert rel(host(xs2[k]), host(xs[k])) < 1e-12
     for k in range(len(ops)):
         xi, ii, _, _ = cmm.solve(ops[k], pcs[k], bs[k], tol=1e-9, maxit=500)
         assert infos[k].status == 0 and ii.status == 0
