@@ -50,7 +50,7 @@ def parse():
                     help="cached: pixel index per sample stored once (4 B/sample); on-the-fly: recomputed "
                          "in both column passes of every application")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["apply", "learned", "batch"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "learned", "batch", "anorm"], default="apply",
                     help="apply: the A-application inside circulant PCG (default); learned: the learned "
                          "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
     ap.add_argument("--batch", type=int, default=64, help="solves of the batch workload")
@@ -430,6 +430,48 @@ def measured_traffic(dom, chunk_dets, args):
     return rec["bytes_per_detector"][key][dom] * chunk_dets
 
 
+def run_anorm(args):
+    """Error A-norm against iteration (the paper's Results metric, Fig. 4 analogue)
+    for binned and circulant PCG on the 1024-detector patch, with instant and with
+    finite-acceleration (1.5 deg/s^2) turnarounds.  The squared error A-norm at
+    iteration i is estimated by the sum of the solver's terms alpha_j r_j^T z_j,
+    j = i .. i + 3."""
+    import numpy as np
+    import torch
+
+    import gen
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm
+    marks = [0, 25, 50, 100, 200, 300, 400, 600]
+    out = {"metric": "iterations to 1e-6 and error A-norm^2 estimate vs iteration", "unit": "iterations",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "1024 det x 2^20 samples, 1200x900 TQU, noise-free TOD, FP32 operator, "
+                                  f"circulant taper {args.taper} px", "iterations_marked": marks}, "scans": {}}
+    for label, acc in (("instant", None), ("accel_1.5deg_s2", 1.5)):
+        scan, noise = gen.config2(accel_deg_s2=acc)
+        ctx = cmm.Context(0)
+        op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F32)
+        op.set_pixel_cache(True)
+        m = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=2), device="cuda:0")
+        b = op.rhs(op.project(m))
+        rec = {}
+        for name, kind, kw in (("binned", cmm.PRECON_BINNED, {}),
+                               ("circulant", cmm.PRECON_CIRCULANT, {"taper_sigma_px": args.taper})):
+            pc = cmm.Precon(op, kind, **kw)
+            x, info, hist, terms = cmm.solve(op, pc, b, tol=1e-6, maxit=2000, history=True)
+            t = terms.cpu().numpy()[: info.iterations]
+            an = {i: float(t[i:i + 4].sum()) for i in marks if i + 4 <= len(t)}
+            rec[name] = {"iterations": info.iterations, "seconds": round(info.seconds, 3),
+                         "anorm2": an, "clamped_modes": pc.clamped() if kind == cmm.PRECON_CIRCULANT else None}
+        rec["iteration_ratio"] = rec["circulant"]["iterations"] / rec["binned"]["iterations"]
+        out["scans"][label] = rec
+        del op, pc, b, m
+        torch.cuda.empty_cache()
+    out["value"] = out["scans"]["accel_1.5deg_s2"]["circulant"]["iterations"]
+    return out
+
+
 def run_batch(args):
     """Batched Monte-Carlo solves: args.batch seeded problems of uneven size (detectors,
     samples, map), each with its own sky, circulant preconditioner and context;
@@ -538,6 +580,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             print(json.dumps(run_batch(args)))
+        return 0
+    if args.workload == "anorm":
+        if rank == 0:
+            print(json.dumps(run_anorm(args)))
         return 0
     if world > 1:
         import torch

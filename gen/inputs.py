@@ -124,20 +124,48 @@ def _quantise_bore(bx, by, phi):
     return bore
 
 
-def drift_scan_positions(n_t, ny, nx, f_samp, speed_px_s, throw_px, segments, margin_px):
+def sweep_offsets(t, speed, throw, accel=None):
+    """Azimuth offset a(t) of a back-and-forth sweep of peak-to-peak ``throw`` at
+    cruise ``speed``.  accel None: instant reversal (a triangle wave).  Otherwise the
+    sweep brakes and reverses at constant ``accel`` over the last speed^2/(2 accel)
+    of each end, as a telescope must."""
+    A = 0.5 * throw
+    if accel is None:
+        period = 2.0 * throw / speed
+        ph = np.mod(t / period, 1.0)
+        return A * np.where(ph < 0.5, -1.0 + 4.0 * ph, 3.0 - 4.0 * ph)
+    d = speed * speed / (2.0 * accel)          # braking distance
+    if d > A:
+        raise ValueError("acceleration too low for this throw and speed")
+    tc = (2.0 * A - 2.0 * d) / speed            # cruise time of one leg
+    tr = 2.0 * speed / accel                    # time of one reversal
+    tau = np.mod(t, 2.0 * (tc + tr))
+    a = np.empty_like(tau)
+    s1 = tau < tc
+    s2 = (tau >= tc) & (tau < tc + tr)
+    s3 = (tau >= tc + tr) & (tau < 2 * tc + tr)
+    s4 = tau >= 2 * tc + tr
+    u = tau - tc
+    w = tau - 2 * tc - tr
+    a[s1] = -A + d + speed * tau[s1]
+    a[s2] = (A - d) + speed * u[s2] - 0.5 * accel * u[s2] ** 2
+    a[s3] = (A - d) - speed * (tau[s3] - tc - tr)
+    a[s4] = (-A + d) - speed * w[s4] + 0.5 * accel * w[s4] ** 2
+    return a
+
+
+def drift_scan_positions(n_t, ny, nx, f_samp, speed_px_s, throw_px, segments, margin_px, accel_px_s2=None):
     """Boresight of constant-elevation drift scans in map-pixel coordinates.
 
-    B(t) = C + R(phi(t)) (a(t), 0) + (0, y(t)): a(t) is a triangle wave of
-    peak-to-peak ``throw_px`` at ``speed_px_s``; the sky rotation phi(t) and the
-    drift y(t) are linear within each segment.  ``segments`` is a list of
-    (fraction of samples, phi_start_deg, phi_end_deg, rising) tuples; a rising
-    segment drifts from below the map to above it, a setting one back down.
+    B(t) = C + R(phi(t)) (a(t), 0) + (0, y(t)): a(t) is the sweep of
+    ``sweep_offsets`` (peak-to-peak ``throw_px`` at ``speed_px_s``, reversals at
+    ``accel_px_s2`` or instant); the sky rotation phi(t) and the drift y(t) are
+    linear within each segment.  ``segments`` is a list of (fraction of samples,
+    phi_start_deg, phi_end_deg, rising) tuples; a rising segment drifts from below
+    the map to above it, a setting one back down.
     """
     t = np.arange(n_t, dtype=np.float64) / f_samp
-    period = 2.0 * throw_px / speed_px_s
-    ph = np.mod(t / period, 1.0)
-    tri = np.where(ph < 0.5, -1.0 + 4.0 * ph, 3.0 - 4.0 * ph)
-    a = 0.5 * throw_px * tri
+    a = sweep_offsets(t, speed_px_s, throw_px, accel_px_s2)
     phi = np.empty(n_t)
     yd = np.empty(n_t)
     cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
@@ -157,12 +185,12 @@ def drift_scan_positions(n_t, ny, nx, f_samp, speed_px_s, throw_px, segments, ma
 
 def make_scan(*, cfg, real=0, ny, nx, n_t, focal_px, f_samp=400.0, speed_px_s=120.0,
               throw_px=240.0, segments=((1.0, -15.0, 15.0, True),), ncomp=3,
-              margin_px=None):
+              margin_px=None, accel_px_s2=None):
     focal_px = np.asarray(focal_px, np.float64)
     if margin_px is None:
         margin_px = float(np.abs(focal_px).max()) + 2.0
     bx, by, phi = drift_scan_positions(n_t, ny, nx, f_samp, speed_px_s, throw_px,
-                                       list(segments), margin_px)
+                                       list(segments), margin_px, accel_px_s2)
     bore = _quantise_bore(bx, by, phi)
     det_off = np.round(focal_px * QD).astype(np.int32)
     psi = rng(cfg, real, "psi").uniform(0.0, np.pi, size=focal_px.shape[0])
@@ -218,17 +246,18 @@ def config1(real=0, ncomp=3):
     return scan, noise
 
 
-def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3):
+def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3, accel_deg_s2=None):
     """1024 detectors on a hex focal plane 1 deg across, 2^20 samples at 400 Hz,
     10 deg throw, a rising half at phi = 25 +- 15 deg and a setting half at
     phi = -25 -+ 15 deg, 1200x900 map at 0.5'; sigma lognormal (mean 1, 20 %),
-    f_knee uniform in [1, 5] Hz, alpha = 3.5."""
+    f_knee uniform in [1, 5] Hz, alpha = 3.5.  accel_deg_s2: finite-acceleration
+    turnarounds (None: instant reversal)."""
     px_per_deg = 60.0 / PIX_ARCMIN
     focal = hex_focal_plane(n_det, 18, (60.0 / 36.0) / PIX_ARCMIN)
     scan = make_scan(cfg=2, real=real, ny=ny, nx=nx, n_t=n_t, focal_px=focal,
                      speed_px_s=1.0 * px_per_deg, throw_px=10.0 * px_per_deg,
                      segments=((0.5, 10.0, 40.0, True), (0.5, -10.0, -40.0, False)),
-                     ncomp=ncomp)
+                     ncomp=ncomp, accel_px_s2=None if accel_deg_s2 is None else accel_deg_s2 * px_per_deg)
     return scan, config2_noise(real, n_det)
 
 

@@ -310,6 +310,18 @@ def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
     assert rel(host(op.apply(dev(m))), y) < 1e-6
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_A_turnaround_scan(cmm, ctx, prec):
+    """Config-2 detectors on the scan with finite-acceleration turnarounds."""
+    full, fnoise = gen.config2(n_t=1 << 18, accel_deg_s2=1.5)
+    dets = np.array([3, 500, 1000])
+    scan, noise = full.subset(dets), fnoise.subset(dets)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=2)
+    assert rel(host(op.apply(dev(m))), om.apply_A(oop, m)) < TOL[prec]
+
+
 @pytest.mark.parametrize("ncomp", [1, 3])
 def test_apply_A_fast_small_ragged(cmm, ctx, ncomp):
     scan = gen.small_scan(cfg=210, ny=30, nx=22, n_t=1 << 13, ncols=5, nrows=1, throw_px=33.0, ncomp=ncomp)
