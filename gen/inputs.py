@@ -261,6 +261,43 @@ def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3, accel_deg
     return scan, config2_noise(real, n_det)
 
 
+@dataclasses.dataclass
+class CorrNoise:
+    """Noise correlated between detectors: per frequency N(f) = D(f) + V E(f) V^T with
+    templates V [n_det, r] and mode spectra e_j(f) = amp_j^2 (1 + (f/fknee_j)^-alpha_j)."""
+    modes: np.ndarray    # float64 [n_det, r]
+    amp: np.ndarray      # float64 [r]
+    fknee: np.ndarray    # float64 [r]
+    alpha: np.ndarray    # float64 [r]
+
+    @property
+    def r(self) -> int:
+        return int(self.modes.shape[1])
+
+    def subset(self, dets):
+        return CorrNoise(self.modes[dets].copy(), self.amp.copy(), self.fknee.copy(), self.alpha.copy())
+
+
+def focal_modes(det_off, r=3):
+    """Atmosphere-like templates over the focal plane: the common mode and the x and y
+    offset gradients (each column unit norm), the first r of them."""
+    off = np.asarray(det_off, np.float64) / QD
+    n = off.shape[0]
+    cols = [np.ones(n)]
+    for ax in (0, 1):
+        g = off[:, ax] - off[:, ax].mean()
+        cols.append(g if np.any(g) else np.zeros(n))
+    V = np.stack(cols[:r], axis=1)
+    norms = np.linalg.norm(V, axis=0)
+    return V / np.where(norms > 0, norms, 1.0)
+
+
+def corr_noise(det_off, r=3, amp=(3.0, 1.0, 1.0), fknee=(2.0, 1.0, 1.0), alpha=(3.0, 2.5, 2.5)):
+    """Correlated modes with red spectra, the common mode strongest."""
+    return CorrNoise(focal_modes(det_off, r), np.asarray(amp[:r], float), np.asarray(fknee[:r], float),
+                     np.asarray(alpha[:r], float))
+
+
 CONFIG4_MAPS = ((256, 256), (240, 320), (360, 480), (450, 600), (600, 800), (750, 1000), (900, 1200))
 
 
@@ -366,6 +403,15 @@ def noise_tod(noise: Noise, n_t: int, f_samp: float, *, cfg=1, real=0):
         spec[-1] = amp[-1] * re[-1]
         out[d] = np.fft.irfft(spec, n=n_t)
     return out
+
+
+def corr_noise_tod(noise: Noise, corr: CorrNoise, n_t: int, f_samp: float, *, cfg=1, real=0):
+    """Noise with covariance D + V E V^T per frequency: the independent streams of
+    noise_tod plus sum_j V[:, j] m_j(t), m_j independent streams with PSD e_j."""
+    out = noise_tod(noise, n_t, f_samp, cfg=cfg, real=real)
+    modes = Noise(corr.amp.copy(), corr.fknee.copy(), corr.alpha.copy())
+    m = noise_tod(modes, n_t, f_samp, cfg=cfg, real=real + 7919)
+    return out + corr.modes @ m
 
 
 def random_maps(ncomp, ny, nx, count, *, cfg=1, real=0):

@@ -32,6 +32,11 @@ R10 pointing is the integer fixed-point rule below; polarisation angle on the sk
 R11 PCG starts from x0 = 0 and stops when ||r_k|| / ||b|| <= tol.
 R12 the A-norm error estimate of the Results footnote estimates the SQUARE of
     the error A-norm: ||x_i - x||_A^2 ~ sum_{j=i}^{i+d-1} alpha_j r_j^T z_j.
+R13 noise correlated between detectors (the Test setup section's noise model had
+    inter-detector correlations but the paper states no model): per real-FFT bin
+    N(f) = D(f) + V E(f) V^T, D from R1, V fixed mode templates, E diagonal red mode
+    spectra (DC at the first bin); N^-1 acts on the detectors' Fourier coefficients
+    bin by bin.
 """
 from __future__ import annotations
 
@@ -156,6 +161,64 @@ def apply_ninv(w, tod):
 
 
 # ---------------------------------------------------------------------------
+# Noise correlated between detectors (extension: the paper's test noise model had
+# inter-detector correlations, Sec. Test setup, without stating the model)
+# ---------------------------------------------------------------------------
+#
+# Reading R13: per real-FFT bin k, the detectors' noise covariance is
+#   N(f_k) = D(f_k) + V E(f_k) V^T,
+# D = diag(PSD_d(f_k)) the per-detector law of R1, V [n_det, r] fixed mode templates
+# (common mode, focal-plane gradients), E = diag(e_j(f_k)) with
+# e_j(f) = amp_j^2 (1 + (f / fknee_j)^-alpha_j), DC at the first bin as in R2.
+# N^-1 acts on the vector of the detectors' Fourier coefficients at each bin (the
+# same real matrix at k and n_t - k, so the filtered TOD stays real).  The model's
+# parameters come in a gen.CorrNoise (modes V, amp, fknee, alpha).
+
+def mode_psd(corr, n_t, f_samp):
+    """e_j(f_k), k = 0 .. n_t/2 (R13); [r, n_t/2 + 1]."""
+    k = np.arange(n_t // 2 + 1)
+    f = k * (f_samp / n_t)
+    f[0] = f[1]
+    return np.stack([corr.amp[j] ** 2 * (1.0 + (f / corr.fknee[j]) ** (-corr.alpha[j]))
+                     for j in range(corr.amp.size)])
+
+
+def corr_covariance(w, corr, e):
+    """N(f_k) for every bin: [K, n_det, n_det] = diag(1 / w[:, k]) + V diag(e[:, k]) V^T."""
+    V = corr.modes
+    cov = np.einsum("dj,jk,ej->kde", V, e, V)
+    idx = np.arange(V.shape[0])
+    cov[:, idx, idx] += (1.0 / w).T
+    return cov
+
+
+def apply_ninv_corr(w, corr, e, tod):
+    """N^-1 applied by its definition: per bin k, solve N(f_k) y = x for the vector
+    x of the detectors' rfft coefficients, then irfft (R13)."""
+    n_t = tod.shape[-1]
+    X = np.fft.rfft(tod, axis=-1)
+    cov = corr_covariance(w, corr, e)
+    Y = np.linalg.solve(cov, X.T[:, :, None])[:, :, 0].T
+    return np.fft.irfft(Y, n=n_t, axis=-1)
+
+
+def apply_ninv_corr_woodbury(w, corr, e, tod):
+    """The same by the Woodbury identity, N^-1 = D^-1 - D^-1 V (E^-1 + V^T D^-1 V)^-1
+    V^T D^-1 (r x r solves per bin): the form the GPU path evaluates."""
+    n_t = tod.shape[-1]
+    V = corr.modes
+    X = np.fft.rfft(tod, axis=-1)
+    WX = w * X                                            # D^-1 x
+    t = np.einsum("dj,dk->kj", V, WX)                    # V^T D^-1 x
+    M = np.einsum("dj,dk,dl->kjl", V, w, V)              # V^T D^-1 V
+    r = V.shape[1]
+    M[:, np.arange(r), np.arange(r)] += (1.0 / e).T      # + E^-1
+    s = np.linalg.solve(M, t[:, :, None])[:, :, 0]        # [K, r]
+    Y = WX - w * np.einsum("dj,kj->dk", V, s)
+    return np.fft.irfft(Y, n=n_t, axis=-1)
+
+
+# ---------------------------------------------------------------------------
 # The operator A = P^T N^-1 P (Eq. 2)
 # ---------------------------------------------------------------------------
 
@@ -165,16 +228,25 @@ class Operator:
     noise: object
     mask: np.ndarray
     w: np.ndarray
+    corr: object = None          # CorrNoise or None (independent detectors)
+    e: np.ndarray = None         # mode PSDs of corr
 
     @property
     def shape(self):
         return (self.scan.ncomp, self.scan.ny, self.scan.nx)
 
 
-def make_operator(scan, noise, mask=None):
+def make_operator(scan, noise, mask=None, corr=None):
     if mask is None:
         mask = pixel_mask(scan)
-    return Operator(scan, noise, np.asarray(mask, bool), filter_weights(noise, scan.n_t, scan.f_samp))
+    e = None if corr is None else mode_psd(corr, scan.n_t, scan.f_samp)
+    return Operator(scan, noise, np.asarray(mask, bool), filter_weights(noise, scan.n_t, scan.f_samp), corr, e)
+
+
+def _ninv(op, tod, dets):
+    if op.corr is None:
+        return apply_ninv(op.w[dets], tod)
+    return apply_ninv_corr(op.w, op.corr, op.e, tod)
 
 
 def _pix(op, dets):
@@ -209,22 +281,27 @@ def bin_tod(op, tod, dets=None):
     return out.reshape(op.shape)
 
 
+def _chunks(op):
+    # correlated noise couples the detectors: one chunk holding all of them
+    step = DET_CHUNK if op.corr is None else op.scan.n_det
+    for d0 in range(0, op.scan.n_det, step):
+        yield np.arange(d0, min(op.scan.n_det, d0 + step))
+
+
 def apply_A(op, m):
     """A m = P^T N^-1 P m (Eq. 2), accumulated over detector chunks."""
     out = np.zeros(op.shape)
-    for d0 in range(0, op.scan.n_det, DET_CHUNK):
-        dets = np.arange(d0, min(op.scan.n_det, d0 + DET_CHUNK))
+    for dets in _chunks(op):
         tod = project(op, m, dets)
-        out += bin_tod(op, apply_ninv(op.w[dets], tod), dets)
+        out += bin_tod(op, _ninv(op, tod, dets), dets)
     return out
 
 
 def rhs(op, d):
     """b = P^T N^-1 d (right-hand side of Eq. 2)."""
     out = np.zeros(op.shape)
-    for d0 in range(0, op.scan.n_det, DET_CHUNK):
-        dets = np.arange(d0, min(op.scan.n_det, d0 + DET_CHUNK))
-        out += bin_tod(op, apply_ninv(op.w[dets], d[dets]), dets)
+    for dets in _chunks(op):
+        out += bin_tod(op, _ninv(op, d[dets], dets), dets)
     return out
 
 
