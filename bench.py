@@ -50,6 +50,8 @@ def parse():
                     help="cached: pixel index per sample stored once (4 B/sample); on-the-fly: recomputed "
                          "in both column passes of every application")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--corr-modes", type=int, default=0,
+                    help="noise correlated between detectors: r focal-plane modes (common, x, y gradient)")
     ap.add_argument("--workload", choices=["apply", "learned", "batch", "anorm"], default="apply",
                     help="apply: the A-application inside circulant PCG (default); learned: the learned "
                          "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
@@ -65,6 +67,7 @@ def workload(args):
                         f"10 deg throw rising+setting, 1200x900 TQU CAR 0.5'",
             "n_det": args.n_det, "n_samp": args.n_t, "map": [3, 900, 1200],
             "precon": "circulant", "taper_sigma_px": args.taper, "pointing": args.pointing,
+            "noise": f"correlated, {args.corr_modes} focal-plane modes" if args.corr_modes > 0 else "independent detectors",
             "l2": "no flush: 4.3 GB of spectra streamed per step exceed the 129 MB L2"}
 
 
@@ -175,7 +178,8 @@ def run_ours(args, rank, world):
     n_s = scan.n_det * scan.n_t
     with torch.cuda.stream(stream):
         ctx = cmm.Context(dev, stream=stream.cuda_stream)
-        op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=args.det_chunk)
+        op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=args.det_chunk,
+                          corr=gen.corr_noise(scan.det_off, r=args.corr_modes) if args.corr_modes > 0 else None)
         if args.pointing == "cached" and prec != cmm.PREC_F64:
             op.set_pixel_cache(True)
         m_sky = torch.as_tensor(gen.sky_map(scan.ny, scan.nx, cfg=2, real=rank), device=f"cuda:{dev}")
@@ -227,13 +231,14 @@ def run_ours(args, rank, world):
              "k_tod_inv_bin (inverse FFT pass + P^T)"]
     chunk_dets = min(op_chunk(op, scan, args), scan.n_det)
     elt = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
-    per_launch_bytes = [elt // 2 * chunk_dets * scan.n_t, elt * chunk_dets * scan.n_t,
-                        elt // 2 * chunk_dets * scan.n_t]
+    # filter pass: 8 B/sample; with correlated noise split (r+w) + cross-detector read + merge (r+w)
+    filter_bytes = (elt * 5 // 2 if args.corr_modes > 0 else elt) * chunk_dets * scan.n_t
+    per_launch_bytes = [elt // 2 * chunk_dets * scan.n_t, filter_bytes, elt // 2 * chunk_dets * scan.n_t]
     dom = int(np.argmax(prof[:3]))
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = per_launch_bytes[dom] / (prof[dom] / 1e3) / 1e9
-    apply_bytes = 2 * elt * n_s + 16 * scan.n_t + scan.npix * (3 * 8 * 2 + 16 * 2)
+    apply_bytes = (elt + per_launch_bytes[1] // (chunk_dets * scan.n_t)) * n_s + 16 * scan.n_t + scan.npix * (3 * 8 * 2 + 16 * 2)
     apply_gbs = apply_bytes / (prof[4] / 1e3) / 1e9
 
     cufft = cufft_filter_ms(scan, noise, dev, stream) if args.prec == "f32" else None

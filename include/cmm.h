@@ -151,6 +151,20 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
                      const double* sigma, const double* fknee, const double* alpha,
                      cmm_noise** out);
 int cmm_noise_destroy(cmm_noise* nz);
+/* Noise correlated between detectors (an extension: the paper's test noise model
+ * had inter-detector correlations without stating them).  Per frequency bin the
+ * detectors' covariance becomes N(f) = D(f) + V E(f) V^T: D the per-detector law
+ * above, V [n_det][r] mode templates (host, row-major; e.g. the common mode and
+ * focal-plane gradients), E = diag(amp_j^2 (1 + (f / fknee_j)^-alpha_j)), DC at the
+ * first bin.  N^-1 is applied bin by bin through the Woodbury identity: the filter
+ * pass is split around one cross-detector solve of r x r systems per bin.
+ * r = 0 removes the correlation; r <= 4.  Operators made from this noise pick the
+ * model up at their next call; it needs the FP32/BF16 operator at a fast-path
+ * size with every detector in one chunk (else those calls return
+ * CMM_ERR_UNSUPPORTED), and the preconditioners keep the independent-noise
+ * diagonal.  Waits for the context's stream. */
+int cmm_noise_set_correlated(cmm_noise* nz, int32_t r, const double* modes, const double* amp,
+                             const double* fknee, const double* alpha);
 /* diag(N_d^-1) = mean of w_d over the two-sided DFT grid (host double [n_det]). */
 int cmm_noise_diag(cmm_noise* nz, double* diag_host);
 

@@ -66,6 +66,7 @@ _SIGS = {
     "cmm_pointing_mask": [_vp, _vp, C.POINTER(_i64)],
     "cmm_noise_create": [_vp, _i32, _i64, _d, _vp, _vp, _vp, _PP],
     "cmm_noise_destroy": [_vp],
+    "cmm_noise_set_correlated": [_vp, _i32, _vp, _vp, _vp, _vp],
     "cmm_noise_diag": [_vp, _vp],
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
     "cmm_op_destroy": [_vp],
@@ -184,6 +185,17 @@ def cmm_noise_create(ctx, n_samp, f_samp, sigma, fknee, alpha):
     h = C.c_void_p()
     _check(_lib.cmm_noise_create(ctx, sigma.size, n_samp, f_samp, ps, pf, pa, C.byref(h)))
     return h
+
+
+def cmm_noise_set_correlated(h, corr=None):
+    """corr: gen.CorrNoise-like (modes [n_det, r], amp, fknee, alpha) or None to remove."""
+    if corr is None:
+        _check(_lib.cmm_noise_set_correlated(h, 0, None, None, None, None))
+        return
+    v = np.ascontiguousarray(corr.modes, dtype=np.float64)
+    amp, fk, al = (np.ascontiguousarray(a, dtype=np.float64) for a in (corr.amp, corr.fknee, corr.alpha))
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(_lib.cmm_noise_set_correlated(h, int(v.shape[1]), p(v), p(amp), p(fk), p(al)))
 
 
 def cmm_noise_destroy(h):
@@ -417,6 +429,9 @@ class Noise:
     def diag(self):
         return cmm_noise_diag(self.h, self.n_det)
 
+    def set_correlated(self, corr):
+        cmm_noise_set_correlated(self.h, corr)
+
     def __del__(self):
         if getattr(self, "h", None):
             cmm_noise_destroy(self.h)
@@ -426,10 +441,12 @@ class Noise:
 class Operator:
     """A = P^T N^-1 P for one scan and noise model."""
 
-    def __init__(self, ctx: Context, scan, noise, precision=PREC_F32, det_chunk=0):
+    def __init__(self, ctx: Context, scan, noise, precision=PREC_F32, det_chunk=0, corr=None):
         self.ctx = ctx
         self.pointing = Pointing(ctx, scan)
         self.noise = Noise(ctx, noise, scan.n_t, scan.f_samp)
+        if corr is not None:
+            self.noise.set_correlated(corr)
         self.shape = self.pointing.shape
         self.n_det, self.n_t = scan.n_det, scan.n_t
         self.h = cmm_op_create(ctx.h, self.pointing.h, self.noise.h, precision, det_chunk)

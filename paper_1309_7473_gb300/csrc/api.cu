@@ -295,6 +295,8 @@ static void free_noise(cmm_noise* nz) {
   dfree(nz->coef64);
   dfree(nz->coef32);
   dfree(nz->diag);
+  dfree(nz->corr_V);
+  dfree(nz->corr_par);
   cmm_ctx* c = nz->ctx;
   delete nz;
   ctx_release(c);
@@ -379,6 +381,8 @@ static void free_op(cmm_op* op) {
   dfree(op->tmp_a);
   dfree(op->tmp_b);
   dfree(op->pix);
+  dfree(op->corr_minv);
+  dfree(op->corr_s);
   dfree(op->sol);
   dfree(op->sol_state);
   cmm_ctx* c = op->ctx;
@@ -468,8 +472,40 @@ static int op_set_split(cmm_op* op, int logR) {
   op->logC = logN - logR;
   op->R = 1 << op->logR;
   op->C = 1 << op->logC;
+  op->corr_version = -1;   // the correlated-noise tables are in the old split's slot order
   CMM_TRY(op_init_twiddles(op));
   return op_prepare_kernels(op);
+}
+
+int cmm_noise_set_correlated(cmm_noise* nz, int32_t r, const double* modes, const double* amp, const double* fknee,
+                             const double* alpha) {
+  if (!nz || r < 0 || r > kMaxCorrModes) return fail(CMM_ERR_ARG, "bad noise handle or mode count (0..4)");
+  if (r > 0 && (!modes || !amp || !fknee || !alpha)) return fail(CMM_ERR_ARG, "null argument");
+  for (int j = 0; j < r; ++j)
+    if (!(amp[j] >= 0) || !(fknee[j] > 0) || !std::isfinite(alpha[j])) return fail(CMM_ERR_ARG, "bad mode parameter");
+  CMM_CUDA(cudaSetDevice(nz->ctx->device));
+  CMM_CUDA(cudaStreamSynchronize(nz->ctx->stream));
+  dfree(nz->corr_V);
+  dfree(nz->corr_par);
+  nz->corr_V = nullptr;
+  nz->corr_par = nullptr;
+  nz->corr_r = 0;
+  nz->corr_version++;
+  if (r == 0) return CMM_OK;
+  std::vector<float> v((size_t)nz->n_det * r);
+  for (size_t q = 0; q < v.size(); ++q) v[q] = (float)modes[q];
+  std::vector<double> par(3 * r);
+  for (int j = 0; j < r; ++j) {
+    par[3 * j] = amp[j];
+    par[3 * j + 1] = fknee[j];
+    par[3 * j + 2] = alpha[j];
+  }
+  CMM_TRY(dalloc(&nz->corr_V, sizeof(float) * v.size()));
+  CMM_TRY(dalloc(&nz->corr_par, sizeof(double) * par.size()));
+  CMM_CUDA(cudaMemcpy(nz->corr_V, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+  CMM_CUDA(cudaMemcpy(nz->corr_par, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice));
+  nz->corr_r = r;
+  return CMM_OK;
 }
 
 int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable) {
@@ -496,6 +532,37 @@ int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable) {
   return s;
 }
 
+}  // extern "C"
+
+namespace cmm {
+// Brings the operator's correlated-noise tables up to its noise's current model
+// (allocates; call before any stream capture).
+int op_sync_corr(cmm_op* op) {
+  cmm_noise* nz = op->nz;
+  if (op->corr_version == nz->corr_version) return CMM_OK;
+  CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+  dfree(op->corr_minv);
+  dfree(op->corr_s);
+  op->corr_minv = nullptr;
+  op->corr_s = nullptr;
+  if (nz->corr_r > 0) {
+    if (!fast_path_ok(op))
+      return fail(CMM_ERR_UNSUPPORTED, "correlated noise needs the FP32/BF16 operator at a fast-path size");
+    if (op->chunk < op->pt->n_det)
+      return fail(CMM_ERR_UNSUPPORTED, "correlated noise needs every detector in one chunk (det_chunk)");
+    const int r = nz->corr_r;
+    CMM_TRY(dalloc(&op->corr_minv, sizeof(float) * (size_t)(op->N + 1) * r * r));
+    CMM_TRY(dalloc(&op->corr_s, sizeof(float2) * (size_t)op->N * r));
+    CMM_TRY(launch_corr_minv(op, nz->corr_par, op->corr_minv));
+    CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+  }
+  op->corr_version = nz->corr_version;
+  return CMM_OK;
+}
+}  // namespace cmm
+
+extern "C" {
+
 static int apply_A_dev(cmm_op* op, const double* m_in, double* m_out) {
   CMM_TRY(launch_map_to_gather(op, m_in));
   for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
@@ -509,6 +576,7 @@ int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out) {
   if (!op || !m_in || !m_out) return fail(CMM_ERR_ARG, "null argument");
   if (m_in == m_out) return fail(CMM_ERR_ARG, "m_in and m_out must not alias");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   return apply_A_dev(op, m_in, m_out);
 }
 
@@ -516,6 +584,7 @@ int cmm_profile_apply(cmm_op* op, const double* m_in, double* m_out, int32_t rep
   if (!op || !m_in || !m_out || !ms_host || reps <= 0) return fail(CMM_ERR_ARG, "bad argument");
   if (m_in == m_out) return fail(CMM_ERR_ARG, "m_in and m_out must not alias");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   cudaStream_t st = op->ctx->stream;
   const int nchunk = (op->pt->n_det + op->chunk - 1) / op->chunk;
   const int nev = 2 + reps * (1 + 3 * nchunk + 1);
@@ -571,6 +640,7 @@ int cmm_profile_apply(cmm_op* op, const double* m_in, double* m_out, int32_t rep
 int cmm_apply_A_host(cmm_op* op, const double* m_in_host, double* m_out_host) {
   if (!op || !m_in_host || !m_out_host) return fail(CMM_ERR_ARG, "null argument");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   const size_t bytes = sizeof(double) * op->pt->ncomp * op->pt->npix;
   cudaStream_t st = op->ctx->stream;
   CMM_CUDA(cudaMemcpyAsync(op->tmp_a, m_in_host, bytes, cudaMemcpyHostToDevice, st));
@@ -589,6 +659,7 @@ int cmm_project(cmm_op* op, const double* m, void* tod, int32_t tod_is_f64) {
 int cmm_rhs(cmm_op* op, const void* tod, int32_t tod_is_f64, double* b) {
   if (!op || !tod || !b) return fail(CMM_ERR_ARG, "null argument");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   CMM_CUDA(cudaMemsetAsync(op->acc, 0, sizeof(double) * op->acc_stride * op->pt->npix, op->ctx->stream));
   for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
     const int nd = std::min(op->chunk, op->pt->n_det - d0);
@@ -719,6 +790,8 @@ extern "C" {
 int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm_precon** out) {
   if (!op || !out) return fail(CMM_ERR_ARG, "null argument");
   *out = nullptr;
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   if (kind < CMM_PRECON_BINNED || kind > CMM_PRECON_IDENTITY) return fail(CMM_ERR_ARG, "bad preconditioner kind");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   cmm_precon* pc = new cmm_precon();
@@ -891,6 +964,8 @@ static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBuf
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_solve_opts* opts,
               double* resid_hist, double* anorm_terms, double* snapshots, cmm_solve_info* info) {
   if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_TRY(op_sync_corr(op));
   if (snapshots && (opts->snapshot_every < 1 || opts->snapshot_max < 1)) return fail(CMM_ERR_ARG, "bad snapshot options");
   Snap snap;
   if (snapshots) {
@@ -1113,6 +1188,7 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
   if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace != 0)
     return fail(CMM_ERR_ARG, "bad batch solve options (residual replacement is per solve)");
   CMM_CUDA(cudaSetDevice(ops[0]->ctx->device));
+  for (int i = 0; i < n; ++i) CMM_TRY(op_sync_corr(ops[i]));
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t main_st = ops[0]->ctx->stream;
   std::vector<SolveBufs> vb(n);

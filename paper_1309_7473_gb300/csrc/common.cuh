@@ -116,6 +116,11 @@ struct cmm_noise {
   float4* coef32 = nullptr;
   double* diag = nullptr;      // [n_det] diag(N^-1)
   std::vector<double> diag_host;
+  // noise correlated between detectors: N(f) = D(f) + V E(f) V^T (r modes, 0 = none)
+  int corr_r = 0;
+  int corr_version = 0;        // bumped by every cmm_noise_set_correlated
+  float* corr_V = nullptr;     // [n_det][r] templates V
+  double* corr_par = nullptr;  // [r][3] (amp, fknee, alpha) of the mode spectra
 };
 
 struct cmm_op {
@@ -134,6 +139,9 @@ struct cmm_op {
   int acc_stride = 0;
   void* tw = nullptr;          // twiddle tables in the op's compute type
   int32_t* pix = nullptr;      // optional [n_det][n_samp] pixel index per sample (npix: outside)
+  int corr_version = 0;        // noise correlation version the tables below were built for
+  float* corr_minv = nullptr;  // [N + 1][r][r] per-bin M^-1 in slot order (index N: bin N)
+  float2* corr_s = nullptr;    // [N][r] cross-detector solution per bin slot
   double* tmp_a = nullptr;     // [ncomp*npix] device temporaries
   double* tmp_b = nullptr;
   const int* done = nullptr;   // solver stop flag seen by every kernel (nullptr: none)
@@ -144,6 +152,7 @@ struct cmm_op {
 namespace cmm {
 
 constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
+constexpr int kMaxCorrModes = 4;   // correlated noise modes
 
 // twiddle table offsets inside cmm_op::tw (in elements of V2<T>)
 struct TwLayout {
@@ -170,6 +179,8 @@ int launch_hit_blocks(cmm_pointing* pt, const double* det_weight, const uint8_t*
 int op_init_twiddles(cmm_op* op);
 int op_prepare_kernels(cmm_op* op);
 int launch_fill_pixels(cmm_op* op);
+int launch_corr_minv(cmm_op* op, const double* mode_par_dev, float* minv);
+int op_sync_corr(cmm_op* op);
 bool fast_path_ok(const cmm_op* op);
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
 

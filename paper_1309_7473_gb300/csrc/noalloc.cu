@@ -52,6 +52,7 @@ int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out) {
   if (!op || !m_in || !m_out) return fail(CMM_ERR_ARG, "null argument");
   if (m_in == m_out) return fail(CMM_ERR_ARG, "m_in and m_out must not alias");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
+  if (op->nz->corr_r > 0) return fail(CMM_ERR_UNSUPPORTED, "noise correlated between detectors is not supported here");
   const int64_t npix = op->pt->npix;
   const int nc = op->pt->ncomp;
   const size_t elt = op->prec == CMM_PREC_F64 ? 16 : (op->prec == CMM_PREC_BF16 ? 4 : 8);

@@ -83,6 +83,10 @@ struct TodArgs {
   long long npix;
   const void* tod;      // float / double [n_det][n_t]
   const int* pix;       // cached pixel indices [n_det][n_t] or nullptr
+  int corr_r;           // correlated noise modes (0: independent detectors)
+  const float* corrV;   // [n_det][corr_r]
+  const float* corr_minv;   // [N + 1][r][r] slot order
+  float2* corr_s;       // [N][r]
   int d0;
   const int* done;
 };
@@ -170,6 +174,11 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   a.npix = pt->npix;
   a.tod = nullptr;
   a.pix = op->pix;
+  const bool corr = op->nz->corr_r > 0 && op->corr_minv && op->corr_version == op->nz->corr_version;
+  a.corr_r = corr ? op->nz->corr_r : 0;
+  a.corrV = op->nz->corr_V;
+  a.corr_minv = op->corr_minv;
+  a.corr_s = op->corr_s;
   a.d0 = d0;
   a.done = op->done;
   return a;

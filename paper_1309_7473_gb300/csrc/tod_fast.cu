@@ -240,7 +240,27 @@ template <int C, int E> struct FilterShape {
   static constexpr int MINB = THREADS > 256 ? 1 : CMM_FILTER_MINB;
 };
 
-template <typename S, int E, int... RC>
+// Filter-pass modes: kFilterFull applies the per-detector filter (row FFT, split,
+// w_d(f), merge, inverse row FFT).  With noise correlated between detectors the pass
+// is cut in two around a cross-detector step: kFilterSplit ends after the split and
+// stores the real-FFT spectrum X_d(k) in the slot of bin k (row k mod R, column
+// k div R; slot 0 holds the two real bins 0 and N as (X(0), X(N))); kFilterMerge
+// starts from those slots, applies y = w_d (X - sum_j V_dj s_j) with the
+// correlation solution s of k_fast_corr, merges and inverts.
+constexpr int kFilterFull = 0, kFilterSplit = 1, kFilterMerge = 2;
+
+// sum_j V_dj s_j(slot) for one detector (complex)
+__device__ __forceinline__ float2 corr_mode_sum(const TodArgs& a, const float* vd, int slot) {
+  float2 acc = make_float2(0.f, 0.f);
+  for (int j = 0; j < a.corr_r; ++j) {
+    const float2 sj = a.corr_s[(size_t)slot * a.corr_r + j];
+    acc.x = fmaf(vd[j], sj.x, acc.x);
+    acc.y = fmaf(vd[j], sj.y, acc.y);
+  }
+  return acc;
+}
+
+template <typename S, int MODE, int E, int... RC>
 __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS,
                                   FilterShape<RadProd<RC...>::value, E>::MINB)
     k_fast_filter(const TodArgs a) {
@@ -269,14 +289,21 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
   S* Y = reinterpret_cast<S*>(a.spec) + (size_t)dl * a.N;
   const RowAddr<PS> ad{smf + rs * ROWLEN};
   float2 x[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-    x[e] = active ? Store<float, S>::ld(Y + row * C + i + e * TPR) : make_float2(0.f, 0.f);
-  rfft<-1, E, RC...>(x, i, tw + a.twl.C_off, ad);
-  __syncthreads();
   const int bi = ad.base(i);
+  if constexpr (MODE != kFilterMerge) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
+    for (int e = 0; e < E; ++e)
+      x[e] = active ? Store<float, S>::ld(Y + row * C + i + e * TPR) : make_float2(0.f, 0.f);
+    rfft<-1, E, RC...>(x, i, tw + a.twl.C_off, ad);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
+  } else {
+    // the split spectrum of the row, straight into the padded row buffer
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      ad.st_at(bi, e * TPR, active ? Store<float, S>::ld(Y + row * C + i + e * TPR) : make_float2(0.f, 0.f));
+  }
   __syncthreads();
   if (pair_ok) {
     const float4 cf = reinterpret_cast<const float4*>(a.coef)[d];
@@ -293,6 +320,9 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
       step = TPR;
       npairs = ra == 0 ? C / 2 + 1 : C / 2;
     }
+    float vd[kMaxCorrModes];
+    if constexpr (MODE == kFilterMerge)
+      for (int j = 0; j < a.corr_r; ++j) vd[j] = a.corrV[d * a.corr_r + j];
     for (int kc = kc0; kc < npairs; kc += step) {
       int j2;
       if (!single) j2 = C - 1 - kc;
@@ -300,24 +330,63 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
       else j2 = C - 1 - kc;
       const int i1 = kc + (kc >> PS), i2 = j2 + (j2 >> PS);
       const int k = ra + a.R * kc;   // < N <= 2^19
-      const float2 A = r0[i1];
-      const float2 B = cconj(r1[i2]);
-      const float2 half2{0.5f, 0.5f};
-      const float2 Ev = pmul(padd(A, B), half2);
-      const float2 Dv = pmul(psub(A, B), half2);
-      const float2 O{Dv.y, -Dv.x};
       const float2 W = cmul(wrow, __ldg(tw + a.twl.C2_off + kc));
-      const float wk = filter_weight_fast(cf, k);
-      const float wm = filter_weight_fast(cf, (int)a.N - k);
-      const float ws = 0.5f * (wk + wm), wd = 0.5f * (wk - wm);
-      const float2 WO = cmul(W, O);
-      const float2 Ep = __ffma2_rn(make_float2(ws, ws), Ev, pmul(make_float2(wd, wd), WO));
-      const float2 cWE = cmulc(Ev, W);
-      const float2 Op = __ffma2_rn(make_float2(wd, wd), cWE, pmul(make_float2(ws, ws), O));
-      r0[i1] = make_float2(Ep.x - Op.y, Ep.y + Op.x);
-      if (!(single && i2 == i1)) r1[i2] = make_float2(Ep.x + Op.y, Op.x - Ep.y);
+      const float2 half2{0.5f, 0.5f};
+      if constexpr (MODE == kFilterFull) {
+        const float2 A = r0[i1];
+        const float2 B = cconj(r1[i2]);
+        const float2 Ev = pmul(padd(A, B), half2);
+        const float2 Dv = pmul(psub(A, B), half2);
+        const float2 O{Dv.y, -Dv.x};
+        const float wk = filter_weight_fast(cf, k);
+        const float wm = filter_weight_fast(cf, (int)a.N - k);
+        const float ws = 0.5f * (wk + wm), wd = 0.5f * (wk - wm);
+        const float2 WO = cmul(W, O);
+        const float2 Ep = __ffma2_rn(make_float2(ws, ws), Ev, pmul(make_float2(wd, wd), WO));
+        const float2 cWE = cmulc(Ev, W);
+        const float2 Op = __ffma2_rn(make_float2(wd, wd), cWE, pmul(make_float2(ws, ws), O));
+        r0[i1] = make_float2(Ep.x - Op.y, Ep.y + Op.x);
+        if (!(single && i2 == i1)) r1[i2] = make_float2(Ep.x + Op.y, Op.x - Ep.y);
+      } else if constexpr (MODE == kFilterSplit) {
+        // X(k) = Ev + W O and X(N - k) = conj(Ev - W O) into their bins' slots
+        const float2 A = r0[i1];
+        const float2 B = cconj(r1[i2]);
+        const float2 Ev = pmul(padd(A, B), half2);
+        const float2 Dv = pmul(psub(A, B), half2);
+        const float2 O{Dv.y, -Dv.x};
+        const float2 WO = cmul(W, O);
+        const float2 Xk = padd(Ev, WO);
+        const float2 Xm = cconj(psub(Ev, WO));
+        if (ra == 0 && kc == 0) {
+          Store<float, S>::st(Y, make_float2(Xk.x, Xm.x));   // the real bins 0 and N
+        } else {
+          Store<float, S>::st(Y + ra * C + kc, Xk);
+          if (!(single && i2 == i1)) Store<float, S>::st(Y + rb * C + j2, Xm);
+        }
+      } else {
+        // y = w (X - V s) at bins k and N - k, merged back into the packed spectrum
+        const int sa = ra * C + kc, sb = rb * C + j2;
+        const float2 X1 = r0[i1], X2 = r1[i2];
+        const float2 S1 = corr_mode_sum(a, vd, sa);
+        float2 Yk, Ym;
+        if (ra == 0 && kc == 0) {
+          Yk = make_float2(filter_weight_fast(cf, 0) * (X1.x - S1.x), 0.f);
+          Ym = make_float2(filter_weight_fast(cf, (int)a.N) * (X1.y - S1.y), 0.f);
+        } else {
+          const float2 S2 = (single && i2 == i1) ? S1 : corr_mode_sum(a, vd, sb);
+          const float wk = filter_weight_fast(cf, k);
+          const float wm = filter_weight_fast(cf, (int)a.N - k);
+          Yk = pmul(make_float2(wk, wk), psub(X1, S1));
+          Ym = cconj(pmul(make_float2(wm, wm), psub(X2, S2)));
+        }
+        const float2 Ev = pmul(padd(Yk, Ym), half2);
+        const float2 Op = cmulc(pmul(psub(Yk, Ym), half2), W);
+        r0[i1] = make_float2(Ev.x - Op.y, Ev.y + Op.x);
+        if (!(single && i2 == i1)) r1[i2] = make_float2(Ev.x + Op.y, Op.x - Ev.y);
+      }
     }
   }
+  if constexpr (MODE == kFilterSplit) return;
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) x[e] = ad.ld_at(bi, e * TPR);
@@ -333,6 +402,98 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
       w = cmul(w, step);
     }
   }
+}
+
+// Cross-detector step of correlated noise, one thread per bin slot: t_j = sum_d
+// V_dj w_d(k) X_d(k) over all detectors, s = M(k)^-1 t with the per-bin
+// M = E^-1 + V^T D^-1 V of corr_minv, stored for kFilterMerge.  Slot 0 carries the
+// real bins 0 and N in its two parts (M^-1 of bin N at index N).
+template <typename S>
+__global__ void k_fast_corr(const TodArgs a, int n_det) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= a.N) return;
+  if (a.done && *a.done) return;
+  const int r = a.corr_r;
+  const int k = (slot & (a.C - 1)) * a.R + (slot >> a.logC);
+  const S* X = reinterpret_cast<const S*>(a.spec) + slot;
+  const float4* coef = reinterpret_cast<const float4*>(a.coef);
+  float2 t[kMaxCorrModes];
+  for (int j = 0; j < r; ++j) t[j] = make_float2(0.f, 0.f);
+  for (int d = 0; d < n_det; ++d) {
+    const float2 x = Store<float, S>::ld(X + (size_t)d * a.N);
+    const float4 cf = coef[a.d0 + d];
+    const float* vd = a.corrV + (a.d0 + d) * r;
+    float wx, wy;
+    if (slot == 0) {
+      wx = filter_weight_fast(cf, 0) * x.x;
+      wy = filter_weight_fast(cf, (int)a.N) * x.y;
+    } else {
+      const float w = filter_weight_fast(cf, k);
+      wx = w * x.x;
+      wy = w * x.y;
+    }
+    for (int j = 0; j < r; ++j) {
+      t[j].x = fmaf(vd[j], wx, t[j].x);
+      t[j].y = fmaf(vd[j], wy, t[j].y);
+    }
+  }
+  const float* m0 = a.corr_minv + (size_t)slot * r * r;
+  const float* m1 = slot == 0 ? a.corr_minv + (size_t)a.N * r * r : m0;   // bin N for the imaginary part
+  for (int j = 0; j < r; ++j) {
+    float sx = 0.f, sy = 0.f;
+    for (int l = 0; l < r; ++l) {
+      sx = fmaf(m0[j * r + l], t[l].x, sx);
+      sy = fmaf(m1[j * r + l], t[l].y, sy);
+    }
+    a.corr_s[(size_t)slot * r + j] = make_float2(sx, sy);
+  }
+}
+
+// M(k)^-1 per bin slot (slot order of the op's split; index N: bin N):
+// M = diag(1 / e_j(k)) + sum_d w_d(k) V_d V_d^T, accumulated and inverted in FP64
+// (Gauss-Jordan with partial pivoting, r <= 4), stored in FP32.
+__global__ void k_corr_minv(const TodArgs a, int n_det, const double* __restrict__ mode_par, double f_samp,
+                            float* __restrict__ minv) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot > a.N) return;
+  const int r = a.corr_r;
+  const int k = slot == (int)a.N ? (int)a.N : (slot & (a.C - 1)) * a.R + (slot >> a.logC);
+  double m[kMaxCorrModes][2 * kMaxCorrModes];
+  const double f = (double)(k == 0 ? 1 : k) * f_samp / (double)a.n_t;
+  for (int j = 0; j < r; ++j) {
+    for (int l = 0; l < 2 * r; ++l) m[j][l] = 0.0;
+    const double amp = mode_par[3 * j], fk = mode_par[3 * j + 1], al = mode_par[3 * j + 2];
+    const double e = amp * amp * (1.0 + pow(f / fk, -al));
+    m[j][j] = 1.0 / e;
+    m[j][r + j] = 1.0;
+  }
+  const float4* coef = reinterpret_cast<const float4*>(a.coef);
+  for (int d = 0; d < n_det; ++d) {
+    const double w = (double)filter_weight_fast(coef[d], k);
+    const float* vd = a.corrV + d * r;
+    for (int j = 0; j < r; ++j)
+      for (int l = 0; l < r; ++l) m[j][l] += w * (double)vd[j] * (double)vd[l];
+  }
+  for (int c = 0; c < r; ++c) {
+    int piv = c;
+    for (int q = c + 1; q < r; ++q)
+      if (fabs(m[q][c]) > fabs(m[piv][c])) piv = q;
+    if (piv != c)
+      for (int l = 0; l < 2 * r; ++l) {
+        const double tmp = m[c][l];
+        m[c][l] = m[piv][l];
+        m[piv][l] = tmp;
+      }
+    const double inv = 1.0 / m[c][c];
+    for (int l = 0; l < 2 * r; ++l) m[c][l] *= inv;
+    for (int q = 0; q < r; ++q)
+      if (q != c) {
+        const double fq = m[q][c];
+        for (int l = 0; l < 2 * r; ++l) m[q][l] -= fq * m[c][l];
+      }
+  }
+  for (int j = 0; j < r; ++j)
+    for (int l = 0; l < r; ++l) minv[(size_t)slot * r * r + j * r + l] = (float)m[j][r + l];
 }
 
 // ------------------------------------------------------------------ pass T' (inverse + P^T)
@@ -584,7 +745,7 @@ static int dispatch_T(const TodArgs& a, int nd, int pass, cudaStream_t st, bool 
                     : dispatch_T_p<NC, S, false>(a, nd, pass, st, attr_only);
 }
 
-template <typename S, int E, int... RC>
+template <typename S, int MODE, int E, int... RC>
 static int run_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
   constexpr int C = RadProd<RC...>::value;
   constexpr int ROWS = FilterShape<C, E>::ROWS;
@@ -592,26 +753,27 @@ static int run_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
   constexpr int PS = clog2(E);
   const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS));
   if (attr_only) {
-    CMM_CUDA(cudaFuncSetAttribute(k_fast_filter<S, E, RC...>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CMM_CUDA(cudaFuncSetAttribute(k_fast_filter<S, MODE, E, RC...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     return CMM_OK;
   }
   const int npairs = a.R / 2 + 1;
   const dim3 g((npairs + PAIRS - 1) / PAIRS, nd);
-  k_fast_filter<S, E, RC...><<<g, FilterShape<C, E>::THREADS, smem, st>>>(a);
+  k_fast_filter<S, MODE, E, RC...><<<g, FilterShape<C, E>::THREADS, smem, st>>>(a);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
 
-template <typename S>
+template <typename S, int MODE>
 static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only) {
   switch (a.logC) {
-    case 6: return run_F<S, 16, 16, 4>(a, nd, st, attr_only);
-    case 7: return run_F<S, 16, 16, 8>(a, nd, st, attr_only);
-    case 8: return run_F<S, 16, 16, 16>(a, nd, st, attr_only);
-    case 9: return run_F<S, 16, 16, 16, 2>(a, nd, st, attr_only);
-    case 10: return run_F<S, 16, 16, 16, 4>(a, nd, st, attr_only);
-    case 11: return run_F<S, 16, 16, 16, 8>(a, nd, st, attr_only);
-    default: return run_F<S, 16, 16, 16, 16>(a, nd, st, attr_only);
+    case 6: return run_F<S, MODE, 16, 16, 4>(a, nd, st, attr_only);
+    case 7: return run_F<S, MODE, 16, 16, 8>(a, nd, st, attr_only);
+    case 8: return run_F<S, MODE, 16, 16, 16>(a, nd, st, attr_only);
+    case 9: return run_F<S, MODE, 16, 16, 16, 2>(a, nd, st, attr_only);
+    case 10: return run_F<S, MODE, 16, 16, 16, 4>(a, nd, st, attr_only);
+    case 11: return run_F<S, MODE, 16, 16, 16, 8>(a, nd, st, attr_only);
+    default: return run_F<S, MODE, 16, 16, 16, 16>(a, nd, st, attr_only);
   }
 }
 
@@ -638,7 +800,17 @@ static int apply_fast_s(cmm_op* op, int d0, int nd, const void* tod, int tod_is_
     else if (nc == 1) CMM_TRY((dispatch_T<1, S>(a, nd, 0, st, false)));
     else CMM_TRY((dispatch_T<3, S>(a, nd, 0, st, false)));
   }
-  if (pass < 0 || pass == 1) CMM_TRY(dispatch_F<S>(a, nd, st, false));
+  if (pass < 0 || pass == 1) {
+    if (a.corr_r > 0) {
+      // correlated noise: split, cross-detector solve over the whole chunk, merge
+      CMM_TRY((dispatch_F<S, kFilterSplit>(a, nd, st, false)));
+      k_fast_corr<S><<<(int)((a.N + 255) / 256), 256, 0, st>>>(a, nd);
+      CMM_LAUNCH_CHECK();
+      CMM_TRY((dispatch_F<S, kFilterMerge>(a, nd, st, false)));
+    } else {
+      CMM_TRY((dispatch_F<S, kFilterFull>(a, nd, st, false)));
+    }
+  }
   if (pass < 0 || pass == 2) {
     for (int g0 = 0; g0 < nd; g0 += kFlushDets) {
       TodArgs b = a;
@@ -663,7 +835,19 @@ static int prepare_fast_s(cmm_op* op) {
   TodArgs a = make_args(op, 0);
   if (op->pt->ncomp == 1) CMM_TRY((dispatch_T<1, S>(a, 0, 0, nullptr, true)));
   else CMM_TRY((dispatch_T<3, S>(a, 0, 0, nullptr, true)));
-  return dispatch_F<S>(a, 0, nullptr, true);
+  CMM_TRY((dispatch_F<S, kFilterFull>(a, 0, nullptr, true)));
+  CMM_TRY((dispatch_F<S, kFilterSplit>(a, 0, nullptr, true)));
+  return dispatch_F<S, kFilterMerge>(a, 0, nullptr, true);
+}
+
+int launch_corr_minv(cmm_op* op, const double* mode_par_dev, float* minv) {
+  TodArgs a = make_args(op, 0);
+  a.corr_r = op->nz->corr_r;   // the tables are being built: make_args does not count them yet
+  const long long n = op->N + 1;
+  k_corr_minv<<<(int)((n + 127) / 128), 128, 0, op->ctx->stream>>>(a, op->pt->n_det, mode_par_dev, op->nz->f_samp,
+                                                                  minv);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
 }
 
 int prepare_fast(cmm_op* op) {
