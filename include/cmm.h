@@ -309,6 +309,20 @@ int cmm_unet_loss_grad(cmm_unet* net, int32_t batch, const float* in, const floa
 int cmm_unet_train_step(cmm_unet* net, int32_t batch, const float* in, const float* target, float lr,
                         double* loss_host);
 
+/* ---------------------------------------------------------------- diagnostics
+ * Flat-sky binned power spectra of TQU maps (the convergence diagnostic of the
+ * Results section: spectra of PCG iterates against the input map's, in units of
+ * cosmic variance).  maps: device double [nmaps][3][ny][nx] (2, 3, 5-smooth sides),
+ * square pixels of pix_rad radians.  Modes l = 2 pi (ky / (ny pix), kx / (nx pix))
+ * (signed frequencies); E = Q cos 2phi + U sin 2phi, B = -Q sin 2phi + U cos 2phi,
+ * phi = atan2(ly, lx); C_b = pix^2 / (ny nx) times the mean of |X|^2 over the modes
+ * with lmax b / nbins <= |l| < lmax (b + 1) / nbins (l = 0 excluded).
+ * cls_host: host double [nmaps][3][nbins] (TT, EE, BB); nmodes_host (may be NULL):
+ * host int64 [nbins] modes per bin.  nbins <= 1024.  Allocates work buffers;
+ * waits for the result. */
+int cmm_spectra(cmm_ctx* ctx, int32_t ny, int32_t nx, double pix_rad, int32_t nmaps, const double* maps,
+                int32_t nbins, double lmax, double* cls_host, int64_t* nmodes_host);
+
 /* ---------------------------------------------------------------- batches and tuning
  * Batched solves (many Monte-Carlo realisations or patches of uneven size): n
  * independent PCG solves, one per (ops[i], pcs[i], b[i], x[i]), are advanced

@@ -67,6 +67,7 @@ _SIGS = {
     "cmm_noise_create": [_vp, _i32, _i64, _d, _vp, _vp, _vp, _PP],
     "cmm_noise_destroy": [_vp],
     "cmm_noise_set_correlated": [_vp, _i32, _vp, _vp, _vp, _vp],
+    "cmm_spectra": [_vp, _i32, _i32, C.c_double, _i32, _vp, _i32, C.c_double, _vp, _vp],
     "cmm_noise_diag": [_vp, _vp],
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
     "cmm_op_destroy": [_vp],
@@ -196,6 +197,19 @@ def cmm_noise_set_correlated(h, corr=None):
     amp, fk, al = (np.ascontiguousarray(a, dtype=np.float64) for a in (corr.amp, corr.fknee, corr.alpha))
     p = lambda a: a.ctypes.data_as(C.c_void_p)
     _check(_lib.cmm_noise_set_correlated(h, int(v.shape[1]), p(v), p(amp), p(fk), p(al)))
+
+
+def cmm_spectra(ctx, maps, pix_rad, nbins, lmax):
+    """Binned flat-sky TT, EE, BB of device maps [nmaps, 3, ny, nx] (float64);
+    returns (cls [nmaps, 3, nbins], modes per bin [nbins])."""
+    if maps.dim() == 3:
+        maps = maps.unsqueeze(0)
+    nm, _, ny, nx = maps.shape
+    cls = np.zeros((nm, 3, nbins))
+    nmodes = np.zeros(nbins, dtype=np.int64)
+    _check(_lib.cmm_spectra(ctx, ny, nx, float(pix_rad), nm, _dev(maps, name="maps"), int(nbins), float(lmax),
+                            cls.ctypes.data_as(C.c_void_p), nmodes.ctypes.data_as(C.c_void_p)))
+    return cls, nmodes
 
 
 def cmm_noise_destroy(h):
