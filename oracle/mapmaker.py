@@ -37,6 +37,10 @@ R13 noise correlated between detectors (the Test setup section's noise model had
     N(f) = D(f) + V E(f) V^T, D from R1, V fixed mode templates, E diagonal red mode
     spectra (DC at the first bin); N^-1 acts on the detectors' Fourier coefficients
     bin by bin.
+R15 tiled circulant (the Summary's locally varying variant, not specified): tiles
+    on a regular ty x tx grid, each with the circulant preconditioner measured at
+    the unmasked pixel nearest its centre, merged as sum_t D_t M_t D_t with D_t the
+    square roots of a raised-cosine partition of unity.
 """
 from __future__ import annotations
 
@@ -390,6 +394,64 @@ def taper(ny, nx, sigma):
     ky = wrapped_offsets(ny)[:, None].astype(np.float64)
     kx = wrapped_offsets(nx)[None, :].astype(np.float64)
     return np.exp(-(ky ** 2 + kx ** 2) / (2.0 * sigma ** 2))
+
+
+def tile_windows_1d(n, t):
+    """R15: t raised-cosine windows on n pixels, centres c_i = (i + 1/2) n / t, spacing
+    h = n / t: w_i(y) = cos^2(pi (y - c_i) / (2 h)) within h of c_i, the outermost
+    windows held at 1 beyond their centres; sum_i w_i = 1 everywhere."""
+    y = np.arange(n, dtype=np.float64)
+    h = n / t
+    out = np.zeros((t, n))
+    for i in range(t):
+        c = (i + 0.5) * h
+        u = (y - c) / h
+        w = np.where(np.abs(u) <= 1.0, np.cos(0.5 * np.pi * u) ** 2, 0.0)
+        if i == 0:
+            w = np.where(y <= c, 1.0, w)
+        if i == t - 1:
+            w = np.where(y >= c, 1.0, w)
+        out[i] = w
+    return out
+
+
+def tile_windows(ny, nx, ty, tx):
+    """phi_t(y, x) = w_i(y) w_j(x), t = i tx + j: a partition of unity over the map."""
+    wy, wx = tile_windows_1d(ny, ty), tile_windows_1d(nx, tx)
+    return np.einsum("iy,jx->ijyx", wy, wx).reshape(ty * tx, ny, nx)
+
+
+def tile_reference(mask, ny, nx, cy, cx):
+    """The unmasked pixel nearest (cy, cx), ties to the lowest index (R9 at a tile centre)."""
+    cand = np.flatnonzero(mask)
+    iy, ix = np.divmod(cand, nx)
+    d2 = (iy - cy) ** 2 + (ix - cx) ** 2
+    return int(cand[d2 == d2.min()].min())
+
+
+class TiledCirculantPrecon:
+    """Locally varying circulant preconditioner (Summary section: tiles with their
+    own constant-correlation model), reading R15: a circulant M_t measured at each
+    tile's centre, merged with the partition of unity phi_t,
+    M = sum_t D_t M_t D_t, D_t = diag(sqrt(phi_t)) on every Stokes component
+    (symmetric positive definite whenever every M_t is)."""
+
+    def __init__(self, op, tiles=(2, 2), taper_sigma=math.inf, pd_eps=PD_EPS):
+        nc, ny, nx = op.shape
+        ty, tx = tiles
+        self.shape = op.shape
+        self.sqrt_phi = np.sqrt(tile_windows(ny, nx, ty, tx))
+        self.parts = []
+        for i in range(ty):
+            for j in range(tx):
+                ref = tile_reference(op.mask, ny, nx, int((i + 0.5) * ny / ty), int((j + 0.5) * nx / tx))
+                self.parts.append(CirculantPrecon(op, taper_sigma=taper_sigma, ref=ref, pd_eps=pd_eps))
+
+    def __call__(self, r):
+        z = np.zeros(self.shape)
+        for d, m in zip(self.sqrt_phi, self.parts):
+            z += d[None] * m(d[None] * r)
+        return z
 
 
 def circulant_forward(q, x):
