@@ -263,7 +263,9 @@ def run_ours(args, rank, world):
             for name, kind, kw in (("binned", cmm.PRECON_BINNED, {}),
                                    ("jacobi", cmm.PRECON_JACOBI, {}),
                                    ("circulant", cmm.PRECON_CIRCULANT, {"taper_sigma_px": args.taper}),
-                                   ("circulant_taper20", cmm.PRECON_CIRCULANT, {"taper_sigma_px": 20.0})):
+                                   ("circulant_taper20", cmm.PRECON_CIRCULANT, {"taper_sigma_px": 20.0}),
+                                   ("circulant_tiled_2x2", cmm.PRECON_CIRC_TILED,
+                                    {"taper_sigma_px": args.taper, "tiles": (2, 2)})):
                 if name == "circulant_taper20" and args.taper == 20.0:
                     continue
                 t1 = time.perf_counter()

@@ -59,7 +59,8 @@ enum cmm_precon_kind {
   CMM_PRECON_JACOBI = 1,    /* M_J, Eq. 5: per-pixel inverse of P^T P */
   CMM_PRECON_CIRCULANT = 2, /* M_C, Eq. 7-13 with the Gaussian regularisation */
   CMM_PRECON_IDENTITY = 3,  /* M = I (plain CG) */
-  CMM_PRECON_CIRC_LEARNED = 4 /* M_C followed by a learned correction (flexible CG) */
+  CMM_PRECON_CIRC_LEARNED = 4, /* M_C followed by a learned correction (flexible CG) */
+  CMM_PRECON_CIRC_TILED = 5    /* locally varying M_C: per-tile circulants merged by a partition of unity */
 };
 
 typedef struct cmm_ctx cmm_ctx;
@@ -80,6 +81,12 @@ typedef struct {
   double taper_sigma_px; /* Gaussian regularisation width in pixels (Sec. Regularization); <= 0 or inf: off */
   int64_t ref_pixel;     /* linear index of the reference pixel (Sec. Implementation); -1: nearest the centre */
   double pd_eps;         /* eigenvalue floor relative to the largest mode eigenvalue; <= 0: 1e-6 */
+  int32_t tiles_y, tiles_x; /* CMM_PRECON_CIRC_TILED: tile grid (<= 0: 2 x 2).  Each tile has the
+                               circulant measured at the unmasked pixel nearest its centre;
+                               M = sum_t D_t M_t D_t, D_t = diag(sqrt(phi_t)), phi_t(y, x) =
+                               w_i(y) w_j(x) with raised-cosine windows w_i (centres
+                               (i + 1/2) n / t, half-width n / t, the outer ones held at 1
+                               towards the edges) summing to 1 (Summary section's variant) */
 } cmm_precon_opts;
 
 typedef struct {

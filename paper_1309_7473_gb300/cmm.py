@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libcmm.so")
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 PRECON_BINNED, PRECON_JACOBI, PRECON_CIRCULANT, PRECON_IDENTITY, PRECON_CIRC_LEARNED = 0, 1, 2, 3, 4
+PRECON_CIRC_TILED = 5
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 
@@ -36,7 +37,8 @@ class MapGeom(C.Structure):
 
 
 class PreconOpts(C.Structure):
-    _fields_ = [("taper_sigma_px", C.c_double), ("ref_pixel", C.c_int64), ("pd_eps", C.c_double)]
+    _fields_ = [("taper_sigma_px", C.c_double), ("ref_pixel", C.c_int64), ("pd_eps", C.c_double),
+                ("tiles_y", C.c_int32), ("tiles_x", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -280,8 +282,8 @@ def cmm_dot(op, x, y):
     return out.value
 
 
-def cmm_precon_create(op, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0):
-    opts = PreconOpts(float(taper_sigma_px), int(ref_pixel), float(pd_eps))
+def cmm_precon_create(op, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0)):
+    opts = PreconOpts(float(taper_sigma_px), int(ref_pixel), float(pd_eps), int(tiles[0]), int(tiles[1]))
     h = C.c_void_p()
     _check(_lib.cmm_precon_create(op, kind, C.byref(opts), C.byref(h)))
     return h
@@ -495,10 +497,10 @@ class Operator:
 
 
 class Precon:
-    def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0):
+    def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0)):
         self.op = op
         self.kind = kind
-        self.h = cmm_precon_create(op.h, kind, taper_sigma_px, ref_pixel, pd_eps)
+        self.h = cmm_precon_create(op.h, kind, taper_sigma_px, ref_pixel, pd_eps, tiles)
 
     def apply(self, r, out=None):
         out = self.op.new_map() if out is None else out

@@ -131,6 +131,9 @@ struct cmm_precon {
   int64_t ref = -1;
   double taper = 0.0;
   cmm_unet* unet = nullptr;    // learned correction (CIRC_LEARNED)
+  std::vector<cmm_precon*> parts;   // CIRC_TILED: one circulant per tile
+  double* sqrt_phi = nullptr;  // CIRC_TILED: [tiles][npix] square roots of the partition of unity
+  double* ttmp = nullptr;      // CIRC_TILED: [2][ncomp * npix]
 };
 
 extern "C" {
@@ -692,6 +695,9 @@ int cmm_precon_destroy(cmm_precon* pc) {
   dfree(pc->planes);
   dfree(pc->tmp);
   dfree(pc->plan.tw);
+  dfree(pc->sqrt_phi);
+  dfree(pc->ttmp);
+  for (cmm_precon* q : pc->parts) cmm_precon_destroy(q);
   cmm_op* op = pc->op;
   cmm_unet* net = pc->unet;
   delete pc;
@@ -699,6 +705,76 @@ int cmm_precon_destroy(cmm_precon* pc) {
   op_release(op);
   return CMM_OK;
 }
+
+}  // extern "C"
+
+// Raised-cosine windows on n pixels, t of them, summing to 1 (centres (i + 1/2) n/t,
+// half-width n/t, the outer ones held at 1 towards the edges).
+static std::vector<double> tile_windows_1d(int n, int t) {
+  std::vector<double> w((size_t)t * n, 0.0);
+  const double h = (double)n / t;
+  for (int i = 0; i < t; ++i) {
+    const double c = (i + 0.5) * h;
+    for (int y = 0; y < n; ++y) {
+      const double u = (y - c) / h;
+      double v = std::fabs(u) <= 1.0 ? std::pow(std::cos(0.5 * M_PI * u), 2) : 0.0;
+      if (i == 0 && y <= c) v = 1.0;
+      if (i == t - 1 && y >= c) v = 1.0;
+      w[(size_t)i * n + y] = v;
+    }
+  }
+  return w;
+}
+
+// the unmasked pixel nearest (cy, cx), ties to the lowest index
+static int64_t nearest_unmasked(const std::vector<uint8_t>& mask, int nx, long long cy, long long cx) {
+  int64_t best = -1;
+  long long bd = -1;
+  for (int64_t p = 0; p < (int64_t)mask.size(); ++p) {
+    if (!mask[p]) continue;
+    const long long dy = p / nx - cy, dx = p % nx - cx;
+    const long long d2 = dy * dy + dx * dx;
+    if (best < 0 || d2 < bd) {
+      best = p;
+      bd = d2;
+    }
+  }
+  return best;
+}
+
+static int tiled_build(cmm_precon* pc, const cmm_precon_opts* o) {
+  cmm_op* op = pc->op;
+  cmm_pointing* pt = op->pt;
+  const int ny = pt->ny, nx = pt->nx, nc = pt->ncomp;
+  const int64_t npix = pt->npix;
+  const int ty = (o && o->tiles_y > 0) ? o->tiles_y : 2, tx = (o && o->tiles_x > 0) ? o->tiles_x : 2;
+  if (ty > ny || tx > nx || ty * tx > 64) return fail(CMM_ERR_ARG, "bad tile grid (at most 64 tiles)");
+  std::vector<uint8_t> mask(npix);
+  CMM_CUDA(cudaMemcpy(mask.data(), pt->mask, npix, cudaMemcpyDeviceToHost));
+  const std::vector<double> wy = tile_windows_1d(ny, ty), wx = tile_windows_1d(nx, tx);
+  std::vector<double> sp((size_t)ty * tx * npix);
+  for (int i = 0; i < ty; ++i)
+    for (int j = 0; j < tx; ++j)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+          sp[((size_t)(i * tx + j) * ny + y) * nx + x] = std::sqrt(wy[(size_t)i * ny + y] * wx[(size_t)j * nx + x]);
+  CMM_TRY(dalloc(&pc->sqrt_phi, sizeof(double) * sp.size()));
+  CMM_TRY(dalloc(&pc->ttmp, sizeof(double) * 2 * nc * npix));
+  CMM_CUDA(cudaMemcpy(pc->sqrt_phi, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice));
+  for (int i = 0; i < ty; ++i)
+    for (int j = 0; j < tx; ++j) {
+      cmm_precon_opts co{};
+      if (o) co = *o;
+      co.ref_pixel = nearest_unmasked(mask, nx, (long long)((i + 0.5) * ny / ty), (long long)((j + 0.5) * nx / tx));
+      if (co.ref_pixel < 0) return fail(CMM_ERR_ARG, "no unmasked pixel");
+      cmm_precon* part = nullptr;
+      CMM_TRY(cmm_precon_create(op, CMM_PRECON_CIRCULANT, &co, &part));
+      pc->parts.push_back(part);
+    }
+  return CMM_OK;
+}
+
+extern "C" {
 
 static int64_t pick_reference(const std::vector<uint8_t>& mask, int ny, int nx) {
   const int64_t p0 = (int64_t)(ny / 2) * nx + nx / 2;
@@ -792,7 +868,8 @@ int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm
   *out = nullptr;
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   CMM_TRY(op_sync_corr(op));
-  if (kind < CMM_PRECON_BINNED || kind > CMM_PRECON_IDENTITY) return fail(CMM_ERR_ARG, "bad preconditioner kind");
+  if (kind < CMM_PRECON_BINNED || kind > CMM_PRECON_CIRC_TILED || kind == CMM_PRECON_CIRC_LEARNED)
+    return fail(CMM_ERR_ARG, "bad preconditioner kind");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   cmm_precon* pc = new cmm_precon();
   pc->op = op;
@@ -819,6 +896,8 @@ int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm
     dfree(blocks);
   } else if (kind == CMM_PRECON_CIRCULANT) {
     s = op->prec == CMM_PREC_F64 ? circulant_build<double>(pc, opts) : circulant_build<float>(pc, opts);
+  } else if (kind == CMM_PRECON_CIRC_TILED) {
+    s = tiled_build(pc, opts);
   }
   if (s != CMM_OK) {
     cmm_precon_destroy(pc);
@@ -860,6 +939,19 @@ static int precon_apply_dev(cmm_precon* pc, const double* r, double* z, double* 
     case CMM_PRECON_CIRCULANT:
       return op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, partial, done)
                                       : circulant_apply<float>(pc, r, z, partial, done);
+    case CMM_PRECON_CIRC_TILED: {
+      // z = sum_t D_t M_t D_t r
+      double* a = pc->ttmp;
+      double* b = pc->ttmp + nc * npix;
+      for (size_t t = 0; t < pc->parts.size(); ++t) {
+        const double* d = pc->sqrt_phi + t * npix;
+        CMM_TRY(launch_window_mul(d, r, a, npix, nc, done, st));
+        CMM_TRY(precon_apply_dev(pc->parts[t], a, b, nullptr, done));
+        CMM_TRY(launch_window_acc(d, b, z, npix, nc, t == 0, done, st));
+      }
+      if (partial) CMM_TRY(launch_dot_partial(r, z, nc * npix, partial, done, st));
+      return CMM_OK;
+    }
     case CMM_PRECON_CIRC_LEARNED:
       CMM_TRY(op->prec == CMM_PREC_F64 ? circulant_apply<double>(pc, r, z, nullptr, done)
                                        : circulant_apply<float>(pc, r, z, nullptr, done));

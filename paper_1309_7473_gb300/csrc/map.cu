@@ -936,4 +936,28 @@ int launch_mode_apply(int ncomp, V2<T>* planes, const double* hinv, long long np
 template int launch_mode_apply<float>(int, float2*, const double*, long long, const int*, cudaStream_t);
 template int launch_mode_apply<double>(int, double2*, const double*, long long, const int*, cudaStream_t);
 
+__global__ void k_window(const double* __restrict__ d, const double* __restrict__ x, double* __restrict__ y,
+                         long long npix, int ncomp, int mode, const int* done) {
+  if (done && *done) return;
+  const long long n = npix * ncomp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = d[i % npix] * x[i];
+    y[i] = mode == 2 ? y[i] + v : v;   // 0: y = d x, 1: first accumulation, 2: y += d x
+  }
+}
+
+int launch_window_mul(const double* d, const double* x, double* y, int64_t npix, int ncomp, const int* done,
+                      cudaStream_t s) {
+  k_window<<<grid_for(npix * ncomp), 256, 0, s>>>(d, x, y, npix, ncomp, 0, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_window_acc(const double* d, const double* x, double* z, int64_t npix, int ncomp, bool first,
+                      const int* done, cudaStream_t s) {
+  k_window<<<grid_for(npix * ncomp), 256, 0, s>>>(d, x, z, npix, ncomp, first ? 1 : 2, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
 }  // namespace cmm

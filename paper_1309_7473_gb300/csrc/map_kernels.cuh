@@ -52,6 +52,11 @@ __device__ __forceinline__ double block_sum_all(const double* partial, int n) {
 
 int launch_block_apply_dot(int ncomp, int64_t npix, const double* blk, const double* x, double* y,
                            const double* w, double* partial, const int* done, cudaStream_t s);
+// y = d .* x and z = (first ? 0 : z) + d .* x on every Stokes component (d [npix])
+int launch_window_mul(const double* d, const double* x, double* y, int64_t npix, int ncomp, const int* done,
+                      cudaStream_t s);
+int launch_window_acc(const double* d, const double* x, double* z, int64_t npix, int ncomp, bool first,
+                      const int* done, cudaStream_t s);
 int launch_dot_partial(const double* x, const double* y, int64_t n, double* partial, const int* done,
                        cudaStream_t s);
 int launch_copy_sub(double* dst, const double* a, const double* b, int64_t n, cudaStream_t s);

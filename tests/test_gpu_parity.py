@@ -460,3 +460,35 @@ def test_autotune_keeps_parity(cmm, ctx, tmp_path):
     assert lr2 == lr and ms2 == -1.0
     assert rel(host(op2.apply(dev(m))), ref) < TOL[1]
     assert open(cache).read().split()[-1] == str(lr)
+
+
+# ---------------------------------------------------------------- tiled circulant (next row 3)
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tiled_circulant_matches_oracle(cmm, ctx, prec):
+    scan, noise = small(3)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    r = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=331)[0]
+    r[:, ~oop.mask.reshape(scan.ny, scan.nx)] = 0
+    ref = om.TiledCirculantPrecon(oop, tiles=(2, 3), taper_sigma=4.0)(r)
+    pc = cmm.Precon(op, cmm.PRECON_CIRC_TILED, taper_sigma_px=4.0, tiles=(2, 3))
+    assert rel(host(pc.apply(dev(r))), ref) < (1e-9 if prec == 0 else 2e-5)
+    one = cmm.Precon(op, cmm.PRECON_CIRC_TILED, taper_sigma_px=4.0, tiles=(1, 1))
+    circ = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=4.0)
+    assert rel(host(one.apply(dev(r))), host(circ.apply(dev(r)))) < 1e-12
+
+
+def test_tiled_circulant_pcg_config1(cmm, ctx):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    m = gen.sky_map(scan.ny, scan.nx, cfg=332)
+    b_ref = om.apply_A(oop, m)
+    pc = cmm.Precon(op, cmm.PRECON_CIRC_TILED, taper_sigma_px=8.0, tiles=(2, 2))
+    x, info, _, _ = cmm.solve(op, pc, dev(b_ref), tol=1e-10, maxit=500)
+    assert info.status == 0
+    xo, io = om.pcg(lambda v: om.apply_A(oop, v), om.TiledCirculantPrecon(oop, tiles=(2, 2), taper_sigma=8.0),
+                    b_ref, tol=1e-10, maxit=500)
+    assert abs(info.iterations - io.iterations) <= 2
+    assert rel(host(x), xo) < 1e-8
