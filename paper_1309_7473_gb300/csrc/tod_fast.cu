@@ -44,6 +44,9 @@ namespace cmm {
 #ifndef CMM_GEN_UNROLL
 #define CMM_GEN_UNROLL 2
 #endif
+#ifndef CMM_BIN_HALVES
+#define CMM_BIN_HALVES 1   // consecutive samples per lane in the binning: 8 x this
+#endif
 #ifndef CMM_BIN_UNROLL
 #define CMM_BIN_UNROLL 1
 #endif
@@ -51,6 +54,7 @@ namespace cmm {
 constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
 constexpr int kGenUnroll = CMM_GEN_UNROLL;
 constexpr int kBinUnroll = CMM_BIN_UNROLL;
+constexpr int kBinHalves = CMM_BIN_HALVES;
 constexpr int kFlushDets = 128;
 constexpr int kE = 16;     // elements per thread in the column FFT
 
@@ -506,40 +510,40 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
                : "memory");
 }
 
-// Bins 8 consecutive samples of one lane: runs of equal pixels are summed in
-// registers and each run issues one reduction into the FP32 partial map.  Runs in
-// the extra pixel `skip` (samples outside the map) issue none: every warp would
-// otherwise hit that one address.
+// Run accumulator of one lane's consecutive samples: samples in the same pixel as
+// the open run are summed in registers; a new pixel closes the run with one
+// reduction into the FP32 partial map.  Runs in the extra pixel `skip` (samples
+// outside the map) issue none: every warp would otherwise hit that one address.
+struct BinRun {
+  int cur = -1;   // pixel of the open run (-1: none)
+  float ax = 0.f, ay = 0.f, az = 0.f;
+};
+
 template <int NC>
-__device__ __forceinline__ void bin_run8(float* acc32, const int (&p)[8], const float (&u)[8], const float (&c)[8],
-                                         const float (&s)[8], int skip) {
-  int cur = p[0];
-  float ax = u[0], ay = 0.f, az = 0.f;
-  if (NC == 3) {
-    ay = c[0] * u[0];
-    az = s[0] * u[0];
+__device__ __forceinline__ void bin_close(float* acc32, const BinRun& r, int skip) {
+  if (r.cur >= 0 && r.cur != skip) {
+    if (NC == 1) red_add(acc32 + r.cur, r.ax);
+    else red_add4(acc32 + 4 * r.cur, r.ax, r.ay, r.az);
   }
+}
+
+template <int NC>
+__device__ __forceinline__ void bin_push8(float* acc32, BinRun& r, const int (&p)[8], const float (&u)[8],
+                                          const float (&c)[8], const float (&s)[8], int skip) {
 #pragma unroll
-  for (int k = 1; k < 8; ++k) {
-    if (p[k] != cur) {
-      if (cur != skip) {
-        if (NC == 1) red_add(acc32 + cur, ax);
-        else red_add4(acc32 + 4 * cur, ax, ay, az);
-      }
-      cur = p[k];
-      ax = 0.f;
-      ay = 0.f;
-      az = 0.f;
+  for (int k = 0; k < 8; ++k) {
+    if (p[k] != r.cur) {
+      bin_close<NC>(acc32, r, skip);
+      r.cur = p[k];
+      r.ax = 0.f;
+      r.ay = 0.f;
+      r.az = 0.f;
     }
-    ax += u[k];
+    r.ax += u[k];
     if (NC == 3) {
-      ay = fmaf(c[k], u[k], ay);
-      az = fmaf(s[k], u[k], az);
+      r.ay = fmaf(c[k], u[k], r.ay);
+      r.az = fmaf(s[k], u[k], r.az);
     }
-  }
-  if (cur != skip) {
-    if (NC == 1) red_add(acc32 + cur, ax);
-    else red_add4(acc32 + 4 * cur, ax, ay, az);
   }
 }
 
@@ -559,7 +563,9 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   // binning layout: BS = row stride of the tile (the 2-complex pad spreads the
   // rows' 16-byte reads over all banks), LPR lanes per row, RPP rows per pass
   constexpr int BS = J + 2;
-  constexpr int LPR = J / 4;
+  constexpr int H = kBinHalves;           // groups of 8 consecutive samples per lane
+  constexpr int LPR = J / (4 * H);        // lanes per row
+  static_assert(LPR >= 1, "a row must hold the lane's samples");
   constexpr int RPP = ColShape<R>::THREADS / LPR;
   constexpr int PSTR = 2 * J + 4;   // ints per staged pixel row (the pad spreads 16-byte reads over the banks)
   const int bq = threadIdx.x % LPR;
@@ -585,50 +591,57 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
     const float2 pol = reinterpret_cast<const float2*>(a.pol)[d];
     const int* pixd = CACHED ? a.pix + (size_t)d * a.n_t : nullptr;
     int* pst = reinterpret_cast<int*>(smf + R * BS);   // pixel staging of one pass (on-the-fly pointing)
-    // each lane bins 8 consecutive samples: 4 complex of row kr from column 4 q
+    // each lane bins 8 H consecutive samples: 4 H complex of row kr from column 4 H q
 #pragma unroll kBinUnroll
     for (int kr0 = 0; kr0 < R; kr0 += RPP) {
       const int kr = kr0 + br;
-      const int t = 2 * (c0 + 4 * bq + kr * a.C);
-      int p[8];
+      const int tq = 2 * (c0 + 4 * H * bq + kr * a.C);
       if constexpr (!CACHED) {
         // pixels of the pass's RPP rows x 2J samples, lanes on consecutive samples
         // (coalesced boresight reads), staged in shared memory
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 8 * H; ++k) {
           const int sidx = threadIdx.x + k * ColShape<R>::THREADS;
           const int rr = sidx / (2 * J), col = sidx % (2 * J);
           const int ts = 2 * (c0 + (kr0 + rr) * a.C) + col;
           pst[rr * PSTR + col] = pixel_fast<PERIODIC>(__ldg(a.bore + ts), off, a.ny, a.nx, npix);
         }
         __syncthreads();
-        const int4 P0 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * bq);
-        const int4 P1 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * bq + 4);
-        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
-        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
-      } else {
-        const int4 P0 = __ldcs(reinterpret_cast<const int4*>(pixd + t));
-        const int4 P1 = __ldcs(reinterpret_cast<const int4*>(pixd + t + 4));
-        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
-        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
       }
-      const float4 A = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * bq);
-      const float4 B = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * bq + 2);
-      float u[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
-      float cc[8], ss[8];
+      BinRun run;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) u[k] *= scale;
-      if (NC == 3) {
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          const float4 r2 = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k));
-          cc[k] = pol.x * r2.x - pol.y * r2.y;
-          ss[k] = pol.y * r2.x + pol.x * r2.y;
-          cc[k + 1] = pol.x * r2.z - pol.y * r2.w;
-          ss[k + 1] = pol.y * r2.z + pol.x * r2.w;
+      for (int h = 0; h < H; ++h) {
+        const int t = tq + 8 * h;
+        int p[8];
+        int4 P0, P1;
+        if constexpr (!CACHED) {
+          P0 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * H * bq + 8 * h);
+          P1 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * H * bq + 8 * h + 4);
+        } else {
+          P0 = __ldcs(reinterpret_cast<const int4*>(pixd + t));
+          P1 = __ldcs(reinterpret_cast<const int4*>(pixd + t + 4));
         }
+        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
+        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
+        const float4 A = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * H * bq + 4 * h);
+        const float4 B = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * H * bq + 4 * h + 2);
+        float u[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+        float cc[8], ss[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] *= scale;
+        if (NC == 3) {
+#pragma unroll
+          for (int k = 0; k < 8; k += 2) {
+            const float4 r2 = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k));
+            cc[k] = pol.x * r2.x - pol.y * r2.y;
+            ss[k] = pol.y * r2.x + pol.x * r2.y;
+            cc[k + 1] = pol.x * r2.z - pol.y * r2.w;
+            ss[k + 1] = pol.y * r2.z + pol.x * r2.w;
+          }
+        }
+        bin_push8<NC>(a.acc32, run, p, u, cc, ss, npix);
       }
-      bin_run8<NC>(a.acc32, p, u, cc, ss, npix);
+      bin_close<NC>(a.acc32, run, npix);
       if constexpr (!CACHED) __syncthreads();   // the staging is rewritten by the next pass
     }
   }
@@ -706,7 +719,7 @@ static int run_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, bool att
   // forward: FFT tile R x J complex.  inverse: binning tile R x (J + 2) complex,
   // then the pixel staging of one binning pass, (threads / (J / 4)) rows x (2 J + 4) ints
   const int smem_f = (int)(sizeof(float2) * R * J);
-  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * (NT / (J / 4)) * (2 * J + 4));
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * (NT / (J / (4 * kBinHalves))) * (2 * J + 4));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_fast_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_f));
