@@ -152,6 +152,22 @@ def oracle_rate(args, seconds, rank=0):
     return rate, sample
 
 
+def job_ms(ms, world, device):
+    """The job's time: the slowest rank's (max over ranks; the ranks ran after a barrier)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_s_per_rank, steps, ms, world):
+    """Whole-job throughput: the samples every rank processed over the job's time
+    (replicas: each rank solves its own realisation of the same size)."""
+    return world * n_s_per_rank * steps / (ms / 1e3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -211,12 +227,9 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_ms(ms, world, f"cuda:{dev}")
     ms_step = ms / args.steps
-    value = world * n_s * args.steps / (ms / 1e3)
+    value = job_value(n_s, args.steps, ms, world)
 
     # per-pass durations of the A-application (CUDA events between its kernels)
     with torch.cuda.stream(stream):
