@@ -96,23 +96,6 @@ __device__ __forceinline__ void rfft(float2 (&x)[E], const int i, const float2* 
   rfft_stages<SIGN, E, RadProd<RS...>::value, 1, Addr, RS...>(x, i, tw, ad);
 }
 
-// Shared-memory tile of J = 8 interleaved columns (pass T): position pos of column
-// cl at 8 (pos + pos / 8) + (cl ^ (pos mod 8)): the eight columns of a row share
-// one 64-byte segment (permuted within it), consecutive groups of eight rows shift
-// by half the banks, and a thread reading the eight columns of one row in order
-// meets no bank conflict with its neighbours.
-struct ColAddr {
-  float2* buf;
-  int cl;
-  __device__ __forceinline__ int idx(int pos) const { return ((pos + (pos >> 3)) << 3) + (cl ^ (pos & 7)); }
-  __device__ __forceinline__ void st(int pos, float2 v) const { buf[idx(pos)] = v; }
-  __device__ __forceinline__ float2 ld(int pos) const { return buf[idx(pos)]; }
-  __device__ __forceinline__ int base(int pos) const { return pos; }
-  __device__ __forceinline__ void st_at(int b, int o, float2 v) const { st(b + o, v); }
-  __device__ __forceinline__ float2 ld_at(int b, int o) const { return ld(b + o); }
-};
-__host__ __device__ constexpr int col_tile_elems(int L) { return 8 * (L + L / 8); }
-
 // One contiguous row (pass F), padded by one element every 2^PS positions.
 // st_at / ld_at address position pos + o from base(pos) with a constant offset o;
 // exact whenever the low PS bits of pos and o do not carry into each other, which

@@ -44,6 +44,9 @@ namespace cmm {
 #ifndef CMM_GEN_UNROLL
 #define CMM_GEN_UNROLL 2
 #endif
+#ifndef CMM_COLJ_256
+#define CMM_COLJ_256 16   // columns per CTA of the column passes at R = 256
+#endif
 #ifndef CMM_BIN_HALVES
 #define CMM_BIN_HALVES 1   // consecutive samples per lane in the binning: 8 x this
 #endif
@@ -62,7 +65,7 @@ constexpr int kE = 16;     // elements per thread in the column FFT
 // for R = 256; either way a half-warp reads 16 complex = 32 consecutive samples
 // and touches 32 different shared-memory banks.
 template <int R> struct ColShape {
-  static constexpr int J = R >= 256 ? 16 : 32;
+  static constexpr int J = R >= 256 ? CMM_COLJ_256 : 32;
   static constexpr int THREADS = J * R / kE;
   static constexpr int MINB = CMM_COL_THREADS_PER_SM / THREADS > 0 ? CMM_COL_THREADS_PER_SM / THREADS : 1;
   static constexpr int MINB_INV = CMM_INV_THREADS_PER_SM / THREADS > 0 ? CMM_INV_THREADS_PER_SM / THREADS : 1;
