@@ -158,6 +158,13 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
                      const double* sigma, const double* fknee, const double* alpha,
                      cmm_noise** out);
 int cmm_noise_destroy(cmm_noise* nz);
+/* Tabulated noise weights instead of the law: w_host (host double
+ * [n_det][n_samp/2 + 1]) holds w_d(f_k) = 1 / PSD_d(f_k) for k = 0 .. n_samp/2, e.g.
+ * measured noise spectra (finite, >= 0).  diag(N^-1) (Eq. 3, 7) is recomputed from
+ * the table; operators made from this noise use it at their next application
+ * (4 more bytes per bin per detector read by the filter pass).  NULL restores the
+ * law.  Waits for the context's stream. */
+int cmm_noise_set_table(cmm_noise* nz, const double* w_host);
 /* Noise correlated between detectors (an extension: the paper's test noise model
  * had inter-detector correlations without stating them).  Per frequency bin the
  * detectors' covariance becomes N(f) = D(f) + V E(f) V^T: D the per-detector law

@@ -240,11 +240,14 @@ class Operator:
         return (self.scan.ncomp, self.scan.ny, self.scan.nx)
 
 
-def make_operator(scan, noise, mask=None, corr=None):
+def make_operator(scan, noise, mask=None, corr=None, w=None):
+    """w: tabulated weights w_d(f_k) [n_det, n_t/2 + 1] replacing the law of R1."""
     if mask is None:
         mask = pixel_mask(scan)
     e = None if corr is None else mode_psd(corr, scan.n_t, scan.f_samp)
-    return Operator(scan, noise, np.asarray(mask, bool), filter_weights(noise, scan.n_t, scan.f_samp), corr, e)
+    if w is None:
+        w = filter_weights(noise, scan.n_t, scan.f_samp)
+    return Operator(scan, noise, np.asarray(mask, bool), np.asarray(w, np.float64), corr, e)
 
 
 def _ninv(op, tod, dets):

@@ -69,6 +69,7 @@ _SIGS = {
     "cmm_noise_create": [_vp, _i32, _i64, _d, _vp, _vp, _vp, _PP],
     "cmm_noise_destroy": [_vp],
     "cmm_noise_set_correlated": [_vp, _i32, _vp, _vp, _vp, _vp],
+    "cmm_noise_set_table": [_vp, _vp],
     "cmm_spectra": [_vp, _i32, _i32, C.c_double, _i32, _vp, _i32, C.c_double, _vp, _vp],
     "cmm_noise_diag": [_vp, _vp],
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
@@ -212,6 +213,15 @@ def cmm_spectra(ctx, maps, pix_rad, nbins, lmax):
     _check(_lib.cmm_spectra(ctx, ny, nx, float(pix_rad), nm, _dev(maps, name="maps"), int(nbins), float(lmax),
                             cls.ctypes.data_as(C.c_void_p), nmodes.ctypes.data_as(C.c_void_p)))
     return cls, nmodes
+
+
+def cmm_noise_set_table(h, w=None):
+    """w: float64 [n_det, n_samp/2 + 1] of w_d(f_k) = 1 / PSD_d(f_k), or None for the law."""
+    if w is None:
+        _check(_lib.cmm_noise_set_table(h, None))
+        return
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(_lib.cmm_noise_set_table(h, w.ctypes.data_as(C.c_void_p)))
 
 
 def cmm_noise_destroy(h):
@@ -447,6 +457,9 @@ class Noise:
 
     def set_correlated(self, corr):
         cmm_noise_set_correlated(self.h, corr)
+
+    def set_table(self, w):
+        cmm_noise_set_table(self.h, w)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -300,6 +300,8 @@ static void free_noise(cmm_noise* nz) {
   dfree(nz->diag);
   dfree(nz->corr_V);
   dfree(nz->corr_par);
+  dfree(nz->wtab64);
+  dfree(nz->wtab32);
   cmm_ctx* c = nz->ctx;
   delete nz;
   ctx_release(c);
@@ -478,6 +480,46 @@ static int op_set_split(cmm_op* op, int logR) {
   op->corr_version = -1;   // the correlated-noise tables are in the old split's slot order
   CMM_TRY(op_init_twiddles(op));
   return op_prepare_kernels(op);
+}
+
+int cmm_noise_set_table(cmm_noise* nz, const double* w_host) {
+  if (!nz) return fail(CMM_ERR_ARG, "null argument");
+  const int64_t K = nz->n_t / 2 + 1;
+  const int n_det = nz->n_det;
+  if (w_host)
+    for (int64_t q = 0; q < (int64_t)n_det * K; ++q)
+      if (!(w_host[q] >= 0) || !std::isfinite(w_host[q])) return fail(CMM_ERR_ARG, "weights must be finite and >= 0");
+  CMM_CUDA(cudaSetDevice(nz->ctx->device));
+  cudaStream_t st = nz->ctx->stream;
+  CMM_CUDA(cudaStreamSynchronize(st));
+  dfree(nz->wtab64);
+  dfree(nz->wtab32);
+  nz->wtab64 = nullptr;
+  nz->wtab32 = nullptr;
+  nz->corr_version++;   // correlated-noise tables depend on the weights
+  std::vector<double> diag(n_det);
+  if (!w_host) {
+    k_noise_diag<<<n_det, 256, 0, st>>>(nz->coef64, nz->n_t, nz->diag);
+    CMM_LAUNCH_CHECK();
+    CMM_CUDA(cudaMemcpyAsync(nz->diag_host.data(), nz->diag, sizeof(double) * n_det, cudaMemcpyDeviceToHost, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    return CMM_OK;
+  }
+  std::vector<float> w32((size_t)n_det * K);
+  for (int d = 0; d < n_det; ++d) {
+    const double* w = w_host + (size_t)d * K;
+    double inner = 0.0;   // R3: mean of w over the full two-sided grid
+    for (int64_t k = 1; k < K - 1; ++k) inner += w[k];
+    diag[d] = (w[0] + 2.0 * inner + w[K - 1]) / (double)nz->n_t;
+    for (int64_t k = 0; k < K; ++k) w32[(size_t)d * K + k] = (float)w[k];
+  }
+  CMM_TRY(dalloc(&nz->wtab64, sizeof(double) * (size_t)n_det * K));
+  CMM_TRY(dalloc(&nz->wtab32, sizeof(float) * (size_t)n_det * K));
+  CMM_CUDA(cudaMemcpy(nz->wtab64, w_host, sizeof(double) * (size_t)n_det * K, cudaMemcpyHostToDevice));
+  CMM_CUDA(cudaMemcpy(nz->wtab32, w32.data(), sizeof(float) * (size_t)n_det * K, cudaMemcpyHostToDevice));
+  CMM_CUDA(cudaMemcpy(nz->diag, diag.data(), sizeof(double) * n_det, cudaMemcpyHostToDevice));
+  nz->diag_host = diag;
+  return CMM_OK;
 }
 
 int cmm_noise_set_correlated(cmm_noise* nz, int32_t r, const double* modes, const double* amp, const double* fknee,

@@ -114,6 +114,8 @@ struct cmm_noise {
   // per detector (1/sigma^2, alpha, -alpha*log2(f_samp/(n_t*fknee)), white ? 1 : 0)
   double4_32a* coef64 = nullptr;
   float4* coef32 = nullptr;
+  double* wtab64 = nullptr;    // optional [n_det][n_t/2 + 1] tabulated w_d(f_k) (replaces the law)
+  float* wtab32 = nullptr;
   double* diag = nullptr;      // [n_det] diag(N^-1)
   std::vector<double> diag_host;
   // noise correlated between detectors: N(f) = D(f) + V E(f) V^T (r modes, 0 = none)

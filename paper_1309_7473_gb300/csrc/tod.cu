@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256) k_tod_filter(const TodArgs a) {
     const C2 D{(A.x - B.x) * (T)0.5, (A.y - B.y) * (T)0.5};
     const C2 O{D.y, -D.x};                   // (A - B) / (2i)
     const C2 W = cmul(wrow, tw[a.twl.C2_off + kc]);   // w_{2N}^k
-    const T wk = filter_weight<T>(cf, k);
-    const T wm = filter_weight<T>(cf, a.N - k);
+    const T wk = noise_weight<T>(a.wtab, a.N, d, cf, k);
+    const T wm = noise_weight<T>(a.wtab, a.N, d, cf, a.N - k);
     const T ws = (T)0.5 * (wk + wm), wd = (T)0.5 * (wk - wm);
     const C2 WO = cmul(W, O);
     const C2 Ep{ws * E.x + wd * WO.x, ws * E.y + wd * WO.y};

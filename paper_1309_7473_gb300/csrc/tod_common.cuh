@@ -54,6 +54,13 @@ __device__ __forceinline__ T filter_weight(const V4<T> cf, long long k) {
   return cf.x / ((T)1 + e);
 }
 
+// w_d(f_k) from the detector's table when the noise has one, else the law
+template <typename T>
+__device__ __forceinline__ T noise_weight(const void* wtab, long long N, int d, const V4<T> cf, long long k) {
+  if (wtab) return reinterpret_cast<const T*>(wtab)[(long long)d * (N + 1) + k];
+  return filter_weight<T>(cf, k);
+}
+
 // ------------------------------------------------------------------ spectrum storage
 template <typename T, typename S> struct Store;
 template <typename T> struct Store<T, V2<T>> {
@@ -71,6 +78,7 @@ struct TodArgs {
   const float2* rot2;   // [n_t] (cos 2phi, sin 2phi) in FP32
   const void* pol;      // V2<T> [n_det]
   const void* coef;     // V4<T> [n_det]
+  const void* wtab;     // T [n_det][N + 1] tabulated w_d(f_k), or nullptr (the parametric law)
   int ny, nx, periodic;
   long long n_t, N;
   int R, C, logR, logC, J, logJ;
@@ -154,6 +162,7 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   const bool f64 = op->prec == CMM_PREC_F64;
   a.pol = f64 ? (const void*)pt->det_pol64 : (const void*)pt->det_pol32;
   a.coef = f64 ? (const void*)op->nz->coef64 : (const void*)op->nz->coef32;
+  a.wtab = f64 ? (const void*)op->nz->wtab64 : (const void*)op->nz->wtab32;
   a.ny = pt->ny;
   a.nx = pt->nx;
   a.periodic = pt->periodic;

@@ -81,11 +81,17 @@ __device__ __forceinline__ float small_int_to_float(int k) {
 }
 
 // exp2 / log2 on the special function unit; relative error of w below 1e-6.
-__device__ __forceinline__ float filter_weight_fast(const float4 cf, int k) {
+__device__ __forceinline__ float filter_weight_law(const float4 cf, int k) {
   if (cf.w != 0.0f) return cf.x;
   const float kk = small_int_to_float(k == 0 ? 1 : k);
   const float e = exp2f(fmaf(-cf.y, __log2f(kk), cf.z));
   return __fdividef(cf.x, 1.0f + e);
+}
+
+// w_d(f_k): the detector's tabulated weight when the noise has a table, else the law
+__device__ __forceinline__ float filter_weight_fast(const TodArgs& a, int d, const float4 cf, int k) {
+  if (a.wtab) return __ldg(reinterpret_cast<const float*>(a.wtab) + (size_t)d * (a.N + 1) + k);
+  return filter_weight_law(cf, k);
 }
 
 // (cos 2a, sin 2a) of sample t, a = psi_d + phi_t, from the FP32 (cos 2phi, sin 2phi)
@@ -345,8 +351,8 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
         const float2 Ev = pmul(padd(A, B), half2);
         const float2 Dv = pmul(psub(A, B), half2);
         const float2 O{Dv.y, -Dv.x};
-        const float wk = filter_weight_fast(cf, k);
-        const float wm = filter_weight_fast(cf, (int)a.N - k);
+        const float wk = filter_weight_fast(a, d, cf, k);
+        const float wm = filter_weight_fast(a, d, cf, (int)a.N - k);
         const float ws = 0.5f * (wk + wm), wd = 0.5f * (wk - wm);
         const float2 WO = cmul(W, O);
         const float2 Ep = __ffma2_rn(make_float2(ws, ws), Ev, pmul(make_float2(wd, wd), WO));
@@ -377,12 +383,12 @@ __global__ void __launch_bounds__(FilterShape<RadProd<RC...>::value, E>::THREADS
         const float2 S1 = corr_mode_sum(a, vd, sa);
         float2 Yk, Ym;
         if (ra == 0 && kc == 0) {
-          Yk = make_float2(filter_weight_fast(cf, 0) * (X1.x - S1.x), 0.f);
-          Ym = make_float2(filter_weight_fast(cf, (int)a.N) * (X1.y - S1.y), 0.f);
+          Yk = make_float2(filter_weight_fast(a, d, cf, 0) * (X1.x - S1.x), 0.f);
+          Ym = make_float2(filter_weight_fast(a, d, cf, (int)a.N) * (X1.y - S1.y), 0.f);
         } else {
           const float2 S2 = (single && i2 == i1) ? S1 : corr_mode_sum(a, vd, sb);
-          const float wk = filter_weight_fast(cf, k);
-          const float wm = filter_weight_fast(cf, (int)a.N - k);
+          const float wk = filter_weight_fast(a, d, cf, k);
+          const float wm = filter_weight_fast(a, d, cf, (int)a.N - k);
           Yk = pmul(make_float2(wk, wk), psub(X1, S1));
           Ym = cconj(pmul(make_float2(wm, wm), psub(X2, S2)));
         }
@@ -432,10 +438,10 @@ __global__ void k_fast_corr(const TodArgs a, int n_det) {
     const float* vd = a.corrV + (a.d0 + d) * r;
     float wx, wy;
     if (slot == 0) {
-      wx = filter_weight_fast(cf, 0) * x.x;
-      wy = filter_weight_fast(cf, (int)a.N) * x.y;
+      wx = filter_weight_fast(a, a.d0 + d, cf, 0) * x.x;
+      wy = filter_weight_fast(a, a.d0 + d, cf, (int)a.N) * x.y;
     } else {
-      const float w = filter_weight_fast(cf, k);
+      const float w = filter_weight_fast(a, a.d0 + d, cf, k);
       wx = w * x.x;
       wy = w * x.y;
     }
@@ -476,7 +482,7 @@ __global__ void k_corr_minv(const TodArgs a, int n_det, const double* __restrict
   }
   const float4* coef = reinterpret_cast<const float4*>(a.coef);
   for (int d = 0; d < n_det; ++d) {
-    const double w = (double)filter_weight_fast(coef[d], k);
+    const double w = (double)filter_weight_fast(a, d, coef[d], k);
     const float* vd = a.corrV + d * r;
     for (int j = 0; j < r; ++j)
       for (int l = 0; l < r; ++l) m[j][l] += w * (double)vd[j] * (double)vd[l];
