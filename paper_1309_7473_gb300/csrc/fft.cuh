@@ -160,15 +160,43 @@ struct MixedPlan {
   int rad[kMaxFactors];
 };
 
-// One mixed-radix Stockham pass (radix R in {2,3,4,5}); tw holds w_L^e, e < L.
-template <typename T>
-__device__ __forceinline__ void mixed_pass(const V2<T>* __restrict__ in, V2<T>* __restrict__ out,
-                                           int L, int R, int p, int nseq, int sstride, int estride,
-                                           const V2<T>* __restrict__ tw, int sign) {
+// cos and sin of 2 pi j / R for the radices of the map FFT (R in {2, 3, 4, 5})
+template <int R> struct RootsR;
+template <> struct RootsR<2> {
+  static __device__ __forceinline__ double c(int j) { return j ? -1.0 : 1.0; }
+  static __device__ __forceinline__ double s(int) { return 0.0; }
+};
+template <> struct RootsR<3> {
+  static __device__ __forceinline__ double c(int j) { return j ? -0.5 : 1.0; }
+  static __device__ __forceinline__ double s(int j) {
+    return j == 0 ? 0.0 : (j == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
+  }
+};
+template <> struct RootsR<4> {
+  static __device__ __forceinline__ double c(int j) { return j == 0 ? 1.0 : (j == 2 ? -1.0 : 0.0); }
+  static __device__ __forceinline__ double s(int j) { return j == 1 ? 1.0 : (j == 3 ? -1.0 : 0.0); }
+};
+template <> struct RootsR<5> {
+  static __device__ __forceinline__ double c(int j) {
+    return j == 0 ? 1.0 : ((j == 1 || j == 4) ? 0.30901699437494742410 : -0.80901699437494742410);
+  }
+  static __device__ __forceinline__ double s(int j) {
+    return j == 0 ? 0.0
+                  : (j == 1 ? 0.95105651629515357212
+                            : (j == 2 ? 0.58778525229247312917 : (j == 3 ? -0.58778525229247312917 : -0.95105651629515357212)));
+  }
+};
+
+// One mixed-radix Stockham pass of compile-time radix R; tw holds w_L^e, e < L.
+// The R-point DFT uses constant roots (unrolled), only the inter-stage twiddles
+// come from the table.
+template <typename T, int R>
+__device__ __forceinline__ void mixed_pass_r(const V2<T>* __restrict__ in, V2<T>* __restrict__ out, int L, int p,
+                                             int nseq, int sstride, int estride, const V2<T>* __restrict__ tw,
+                                             int sign) {
   const int nbf = L / R;
   const int total = nbf * nseq;
   const int step = L / (p * R);
-  const int rstep = L / R;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int s, i;
     if (sstride == 1) {
@@ -180,24 +208,46 @@ __device__ __forceinline__ void mixed_pass(const V2<T>* __restrict__ in, V2<T>* 
     }
     const int k = i % p;
     const V2<T>* src = in + s * sstride;
-    V2<T> x[5];
+    V2<T> x[R];
+#pragma unroll
     for (int m = 0; m < R; ++m) {
-      V2<T> v = src[(i + m * nbf) * estride];
-      V2<T> w = tw[m * k * step];
-      if (sign > 0) w.y = -w.y;
-      x[m] = cmul(v, w);
+      const V2<T> v = src[(i + m * nbf) * estride];
+      if (m == 0 || k == 0) {
+        x[m] = v;
+      } else {
+        V2<T> w = tw[m * k * step];
+        if (sign > 0) w.y = -w.y;
+        x[m] = cmul(v, w);
+      }
     }
     const int base = (i - k) * R + k;
     V2<T>* dst = out + s * sstride;
+#pragma unroll
     for (int q = 0; q < R; ++q) {
       V2<T> acc = x[0];
+#pragma unroll
       for (int m = 1; m < R; ++m) {
-        V2<T> w = tw[((m * q) % R) * rstep];
-        if (sign > 0) w.y = -w.y;
-        acc = cadd(acc, cmul(x[m], w));
+        const int j = (m * q) % R;
+        const T c = (T)RootsR<R>::c(j);
+        const T sn = (T)(sign > 0 ? RootsR<R>::s(j) : -RootsR<R>::s(j));
+        acc.x += x[m].x * c - x[m].y * sn;
+        acc.y += x[m].x * sn + x[m].y * c;
       }
       dst[(base + q * p) * estride] = acc;
     }
+  }
+}
+
+// One mixed-radix Stockham pass (radix R in {2,3,4,5}).
+template <typename T>
+__device__ __forceinline__ void mixed_pass(const V2<T>* __restrict__ in, V2<T>* __restrict__ out,
+                                           int L, int R, int p, int nseq, int sstride, int estride,
+                                           const V2<T>* __restrict__ tw, int sign) {
+  switch (R) {
+    case 2: mixed_pass_r<T, 2>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
+    case 3: mixed_pass_r<T, 3>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
+    case 4: mixed_pass_r<T, 4>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
+    default: mixed_pass_r<T, 5>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
   }
 }
 
