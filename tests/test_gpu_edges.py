@@ -97,3 +97,26 @@ def test_rejected_inputs(cmm, ctx):
     m = dev(np.zeros((3, scan.ny, scan.nx)))
     with pytest.raises(cmm.CmmError):
         cmm.cmm_apply_A(op.h, m, m)   # aliasing input and output
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_smallest_sample_count(cmm, ctx, prec):
+    """n_samp = 64: the generic kernels at the bottom of the supported range."""
+    scan = gen.small_scan(cfg=343, ny=6, nx=6, n_t=64, ncols=2, nrows=2, spacing_px=1.0, throw_px=5.0,
+                          speed_px_s=120.0)
+    noise = gen.noise_params(scan.n_det, fknee=20.0, alpha=2.0, scatter=0.2, cfg=343)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=344)[0]
+    ref = om.apply_A(oop, m)
+    if np.linalg.norm(ref) > 0:
+        assert rel(op.apply(dev(m)).cpu().numpy(), ref) < (1e-10 if prec == 0 else 1e-5)
+
+
+def test_zero_rhs_solves_to_zero(cmm, ctx):
+    scan, noise = gen.config1()
+    op = cmm.Operator(ctx, scan, noise, precision=1)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
+    b = dev(np.zeros((3, scan.ny, scan.nx)))
+    x, info, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=50)
+    assert info.status == 0 and not x.any()
