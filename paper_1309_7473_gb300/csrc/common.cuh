@@ -103,7 +103,15 @@ struct cmm_pointing {
   float2* det_pol32 = nullptr;
   float2* rot2 = nullptr;      // [n_t] (cos 2phi, sin 2phi) rounded to FP32 (FP32 response)
   uint8_t* mask = nullptr;     // [npix]
+  int64_t max_hits = 0;        // largest number of samples (all detectors) on one pixel
 };
+
+// Above this many samples (all detectors) on one pixel the fast path's FP32
+// partial map would sum too many terms between flushes: its error grows with the
+// number of adds, and where the added values are exact ties the rounding is
+// biased.  The binning pass of such operators runs the generic kernel, which
+// reduces every sample straight into the FP64 map.
+constexpr int64_t kF32HitLimit = 8192;
 
 struct cmm_noise {
   int refs = 1;                // owner reference + one per dependent handle

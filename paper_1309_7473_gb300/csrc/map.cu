@@ -87,7 +87,8 @@ __device__ __forceinline__ void sym3_store(double* b, const double (&a)[3][3]) {
 // number >= 1e-3 (eigenvalues of the symmetric 3x3 block).
 template <int NC>
 __global__ void k_mask_from_hits(const double* __restrict__ blocks, uint8_t* __restrict__ mask,
-                                 long long npix, unsigned long long* __restrict__ n_good) {
+                                 long long npix, unsigned long long* __restrict__ n_good,
+                                 unsigned long long* __restrict__ max_hits) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
     bool ok;
@@ -104,6 +105,9 @@ __global__ void k_mask_from_hits(const double* __restrict__ blocks, uint8_t* __r
     }
     mask[p] = ok ? 1 : 0;
     if (ok) atomicAdd(n_good, 1ULL);
+    // unit-weight blocks: the (T, T) entry is the pixel's sample count
+    const double hits = NC == 1 ? blocks[p] : blocks[6 * p];
+    if (hits > 0.0) atomicMax(max_hits, (unsigned long long)hits);
   }
 }
 
@@ -674,19 +678,22 @@ __global__ void k_fft_lines(V2<T>* __restrict__ data, MixedPlan plan, int nlines
 static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096)); }
 
 int launch_mask_from_hits(cmm_pointing* pt, const double* blocks) {
-  unsigned long long* d_cnt = nullptr;
-  CMM_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
-  CMM_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), pt->ctx->stream));
+  unsigned long long* d_cnt = nullptr;   // [0] unmasked pixels, [1] largest hit count
+  CMM_CUDA(cudaMalloc(&d_cnt, 2 * sizeof(unsigned long long)));
+  CMM_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), pt->ctx->stream));
   if (pt->ncomp == 1)
-    k_mask_from_hits<1><<<grid_for(pt->npix), 256, 0, pt->ctx->stream>>>(blocks, pt->mask, pt->npix, d_cnt);
+    k_mask_from_hits<1><<<grid_for(pt->npix), 256, 0, pt->ctx->stream>>>(blocks, pt->mask, pt->npix, d_cnt,
+                                                                         d_cnt + 1);
   else
-    k_mask_from_hits<3><<<grid_for(pt->npix), 256, 0, pt->ctx->stream>>>(blocks, pt->mask, pt->npix, d_cnt);
+    k_mask_from_hits<3><<<grid_for(pt->npix), 256, 0, pt->ctx->stream>>>(blocks, pt->mask, pt->npix, d_cnt,
+                                                                         d_cnt + 1);
   CMM_LAUNCH_CHECK();
-  unsigned long long h = 0;
-  CMM_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, pt->ctx->stream));
+  unsigned long long h[2] = {0, 0};
+  CMM_CUDA(cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, pt->ctx->stream));
   CMM_CUDA(cudaStreamSynchronize(pt->ctx->stream));
   CMM_CUDA(cudaFree(d_cnt));
-  pt->n_good = (int64_t)h;
+  pt->n_good = (int64_t)h[0];
+  pt->max_hits = (int64_t)h[1];
   return CMM_OK;
 }
 

@@ -377,8 +377,18 @@ static int apply_chunk_nc(cmm_op* op, int d0, int nd, const void* tod, int pass)
 }
 
 int launch_apply_chunk(cmm_op* op, int d0, int nd, const void* tod, int tod_is_f64, int pass) {
-  if (fast_path_ok(op)) return launch_apply_chunk_fast(op, d0, nd, tod, tod_is_f64, pass);
   const int nc = op->pt->ncomp;
+  if (fast_path_ok(op)) {
+    if (op->pt->max_hits <= kF32HitLimit || pass == 0 || pass == 1)
+      return launch_apply_chunk_fast(op, d0, nd, tod, tod_is_f64, pass);
+    // more samples on one pixel than the FP32 partial map takes: fast forward and
+    // filter passes, then the generic binning into the FP64 map (same spectrum layout)
+    if (pass < 0) {
+      CMM_TRY(launch_apply_chunk_fast(op, d0, nd, tod, tod_is_f64, 0));
+      CMM_TRY(launch_apply_chunk_fast(op, d0, nd, tod, tod_is_f64, 1));
+    }
+    return nc == 1 ? apply_chunk_nc<1, 0>(op, d0, nd, nullptr, 2) : apply_chunk_nc<3, 0>(op, d0, nd, nullptr, 2);
+  }
   if (!tod) return nc == 1 ? apply_chunk_nc<1, 0>(op, d0, nd, nullptr, pass) : apply_chunk_nc<3, 0>(op, d0, nd, nullptr, pass);
   if (tod_is_f64) return nc == 1 ? apply_chunk_nc<1, 2>(op, d0, nd, tod, pass) : apply_chunk_nc<3, 2>(op, d0, nd, tod, pass);
   return nc == 1 ? apply_chunk_nc<1, 1>(op, d0, nd, tod, pass) : apply_chunk_nc<3, 1>(op, d0, nd, tod, pass);
