@@ -299,7 +299,7 @@ def run_ours(args, rank, world):
                 x, info, _, _ = cmm.solve(op, p2, b, tol=1e-6, maxit=2000, check_every=10)
                 solves[name] = {"iterations": info.iterations, "status": cmm.STATUS[info.status],
                                 "seconds": round(info.seconds, 4), "build_seconds": round(build_s, 4),
-                                "rel_resid": info.rel_resid}
+                                "rel_resid": info.rel_resid, "true_rel_resid": info.true_rel_resid}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -108,6 +108,8 @@ typedef struct {
   int32_t status;       /* CMM_OK, CMM_ERR_NOT_CONVERGED or CMM_ERR_BREAKDOWN */
   double rel_resid;     /* last recursive ||r|| / ||b|| */
   double seconds;       /* wall time of the call */
+  double true_rel_resid; /* ||b - A x|| / ||b|| recomputed from the returned x at exit
+                            (one more A-application, inside `seconds`) */
 } cmm_solve_info;
 
 /* ---------------------------------------------------------------- context */

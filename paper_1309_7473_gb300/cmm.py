@@ -50,7 +50,7 @@ class SolveOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_resid", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("true_rel_resid", C.c_double)]
 
 
 if not os.path.exists(LIB_PATH):

@@ -1065,6 +1065,20 @@ struct SolveBufs {
   double *r, *z, *p, *q, *r_old, *p1, *p2, *p3;
 };
 
+// ||b - A x|| / ||b|| recomputed from x (one A-application), in the op's CG
+// scratch (q and r_old slots); the check the recursive residual is compared with.
+static int true_residual(cmm_op* op, const double* b, const double* x, double bnorm2, double* out) {
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  double* q = op->sol + 3 * n;
+  double* r = op->sol + 4 * n;
+  CMM_TRY(apply_A_dev(op, x, q));
+  CMM_TRY(launch_sub(r, b, q, n, op->ctx->stream));
+  double rr = 0.0;
+  CMM_TRY(cmm_dot(op, r, r, n, &rr));
+  *out = std::sqrt(rr / bnorm2);
+  return CMM_OK;
+}
+
 // z = M r (and the learned correction when the preconditioner has one), then the
 // CG dot products of z.
 static int precon_step(cmm_op* op, cmm_precon* pc, const SolveBufs& v, SolverDev* dst, bool flexible) {
@@ -1141,6 +1155,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     info->iterations = 0;
     info->status = CMM_OK;
     info->rel_resid = 0.0;
+    info->true_rel_resid = 0.0;
     info->seconds = 0.0;
     return CMM_OK;
   }
@@ -1217,6 +1232,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   info->iterations = hs->iter;
   info->status = hs->status;
   info->rel_resid = hs->rel;
+  CMM_TRY(true_residual(op, b, x, h.bnorm2, &info->true_rel_resid));
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return CMM_OK;
 }
@@ -1442,14 +1458,16 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
   if (exec) cudaGraphExecDestroy(exec);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (status == CMM_OK)
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && status == CMM_OK; ++i) {
       infos[i].iterations = pinned[i].iter;
       infos[i].status = pinned[i].status;
       infos[i].rel_resid = pinned[i].rel;
-      infos[i].seconds = secs;
+      status = true_residual(ops[i], b[i], x[i], pinned[i].bnorm2, &infos[i].true_rel_resid);
     }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (status == CMM_OK)
+    for (int i = 0; i < n; ++i) infos[i].seconds = secs;
   if (pinned) cudaFreeHost(pinned);
   return status;
 }

@@ -216,5 +216,6 @@ int launch_block_apply(int ncomp, int64_t npix, const double* blocks, const doub
                        double* y, const int* done, cudaStream_t s);
 int launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out,
                const int* done, cudaStream_t s);
+int launch_sub(double* r, const double* b, const double* q, int64_t n, cudaStream_t s);
 
 }  // namespace cmm

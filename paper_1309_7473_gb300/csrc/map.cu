@@ -212,6 +212,13 @@ __global__ void k_block_apply(const double* __restrict__ blk, const double* __re
 }
 
 // ------------------------------------------------------------------ reductions
+// r = b - q (the true residual once A x is in q)
+__global__ void k_sub(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q,
+                      long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = b[i] - q[i];
+}
+
 __global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, long long n,
                               double* __restrict__ partial, const int* done) {
   if (done && *done) return;
@@ -730,6 +737,12 @@ int launch_block_apply(int ncomp, int64_t npix, const double* blk, const double*
 int launch_dot_partial(const double* x, const double* y, int64_t n, double* partial, const int* done,
                        cudaStream_t s) {
   k_dot_partial<<<kRedBlocks, 256, 0, s>>>(x, y, n, partial, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_sub(double* r, const double* b, const double* q, int64_t n, cudaStream_t s) {
+  k_sub<<<grid_for(n), 256, 0, s>>>(r, b, q, n);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }

@@ -270,6 +270,10 @@ def test_pcg_binned_config1_matches_oracle(cmm, ctx, graph):
     np.testing.assert_allclose(t[:10], io.anorm_terms[:10], rtol=1e-6)
     # noise-free data: the solution is the input map on unmasked pixels
     assert rel(host(x), m) < 1e-6
+    # the exit check ||b - A x|| / ||b|| against the oracle's A on the returned x
+    true_o = np.linalg.norm(b_ref - om.apply_A(oop, host(x))) / np.linalg.norm(b_ref)
+    assert info.true_rel_resid < 1e-9
+    assert info.true_rel_resid == pytest.approx(true_o, rel=0.2)
 
 
 def test_pcg_circulant_config1(cmm, ctx):
@@ -286,6 +290,7 @@ def test_pcg_circulant_config1(cmm, ctx):
     assert info.status == 0 and io.converged
     assert abs(info.iterations - io.iterations) <= max(2, 0.1 * io.iterations)
     assert rel(host(x), xo) < 1e-5
+    assert info.rel_resid <= 1e-6 and info.true_rel_resid < 2e-6
 
 
 # ---------------------------------------------------------------- fast-path sizes
@@ -443,6 +448,8 @@ def test_batch_solve_matches_individual_solves(cmm):
         xo, io = refs[k]
         assert abs(infos[k].iterations - io.iterations) <= max(2, 0.1 * io.iterations)
         assert rel(host(xs[k]), xo) < 1e-6
+        assert infos[k].true_rel_resid < 1e-8
+        assert infos[k].true_rel_resid == pytest.approx(ii.true_rel_resid, rel=0.05, abs=1e-11)
 
 
 def test_autotune_keeps_parity(cmm, ctx, tmp_path):
