@@ -101,6 +101,7 @@ typedef struct {
   int32_t snapshot_every; /* with a snapshot buffer: keep (x_k, r_k) every that many iterations */
   int32_t snapshot_max;   /* number of snapshot slots */
   int32_t batch_width;    /* cmm_batch_solve: concurrent lanes (<= 0: automatic) */
+  int32_t skip_true_resid; /* != 0: no exit check of ||b - A x|| (true_rel_resid = -1) */
 } cmm_solve_opts;
 
 typedef struct {
@@ -109,7 +110,8 @@ typedef struct {
   double rel_resid;     /* last recursive ||r|| / ||b|| */
   double seconds;       /* wall time of the call */
   double true_rel_resid; /* ||b - A x|| / ||b|| recomputed from the returned x at exit
-                            (one more A-application, inside `seconds`) */
+                            (one more A-application, inside `seconds`); -1 when
+                            opts->skip_true_resid */
 } cmm_solve_info;
 
 /* ---------------------------------------------------------------- context */

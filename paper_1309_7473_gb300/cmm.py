@@ -45,7 +45,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
                 ("resid_replace", C.c_int32), ("flexible", C.c_int32), ("snapshot_every", C.c_int32),
-                ("snapshot_max", C.c_int32), ("batch_width", C.c_int32)]
+                ("snapshot_max", C.c_int32), ("batch_width", C.c_int32), ("skip_true_resid", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -315,11 +315,11 @@ def cmm_precon_clamped(pc):
 
 def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
               resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False,
-              snapshots=None, snapshot_every=1):
+              snapshots=None, snapshot_every=1, true_resid=True):
     snap_max = 0 if snapshots is None else snapshots.shape[0]
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0,
                      1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0, int(snapshot_every),
-                     int(snap_max))
+                     int(snap_max), 0, 0 if true_resid else 1)
     info = SolveInfo()
     _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
                           _dev(resid_hist, numel=None, name="resid_hist"),
@@ -393,13 +393,13 @@ def cmm_unet_train_step(h, x, target, lr):
 
 
 def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f32=False, flexible=False,
-                    width=0):
+                    width=0, true_resid=True):
     """Batched PCG over parallel lists of operator / preconditioner handles and
     device maps; returns the list of SolveInfo."""
     n = len(ops)
     arr = lambda items: (C.c_void_p * n)(*[C.c_void_p(v if isinstance(v, int) else v.value) for v in items])
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0,
-                     0, 0, int(width))
+                     0, 0, int(width), 0 if true_resid else 1)
     infos = (SolveInfo * n)()
     _check(_lib.cmm_batch_solve(n, arr(ops), arr(pcs), arr([t.data_ptr() for t in bs]),
                                 arr([t.data_ptr() for t in xs]), C.byref(opts), infos))
@@ -564,7 +564,7 @@ class UNet:
 
 
 def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=10, use_graph=True,
-          history=False, cg_f32=False, resid_replace=0, flexible=False):
+          history=False, cg_f32=False, resid_replace=0, flexible=False, true_resid=True):
     """PCG on A x = b; returns (x, info, resid_hist, anorm_terms)."""
     import torch
     x0_given = x is not None
@@ -572,5 +572,5 @@ def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=
     hist = torch.zeros(maxit + 1, dtype=torch.float64, device=b.device) if history else None
     terms = torch.zeros(max(maxit, 1), dtype=torch.float64, device=b.device) if history else None
     info = cmm_solve(op.h, pc.h, b, x, tol, maxit, check_every, use_graph, x0_given, hist, terms,
-                     cg_f32, resid_replace, flexible)
+                     cg_f32, resid_replace, flexible, true_resid=true_resid)
     return x, info, hist, terms

@@ -56,9 +56,21 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
   return r;
 }
 
-// In-register DFT of size R = 2^LR (R <= 32): x_q <- sum_j x_j w_R^{j q}
+// 4-point DFT in place: (x0, x1, x2, x3) <- their transform (w_4 = exp(SIGN i pi / 2))
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft4_reg(V2<T>& x0, V2<T>& x1, V2<T>& x2, V2<T>& x3) {
+  const V2<T> a0 = padd(x0, x2), a1 = psub(x0, x2), a2 = padd(x1, x3);
+  const V2<T> d = psub(x1, x3);
+  const V2<T> a3 = SIGN < 0 ? V2<T>{d.y, -d.x} : V2<T>{-d.y, d.x};   // d w_4
+  x0 = padd(a0, a2);
+  x2 = psub(a0, a2);
+  x1 = padd(a1, a3);
+  x3 = psub(a1, a3);
+}
+
+// In-register DFT of size R = 2^LR by bit reversal and LR radix-2 stages
 template <typename T, int LR, int SIGN>
-__device__ __forceinline__ void dft_reg(V2<T>* x) {
+__device__ __forceinline__ void dft_reg_radix2(V2<T>* x) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -81,6 +93,34 @@ __device__ __forceinline__ void dft_reg(V2<T>* x) {
         x[start + j + half] = psub(u, t);
       }
     }
+  }
+}
+
+// In-register DFT of size R = 2^LR (R <= 32): x_q <- sum_j x_j w_R^{j q}
+template <typename T, int LR, int SIGN>
+__device__ __forceinline__ void dft_reg(V2<T>* x) {
+  if constexpr (LR == 4) {
+    // 16 = 4 x 4 (index n1 + 4 n2 -> k2 + 4 k1): 4-point DFTs over n2, twiddles
+    // w_16^(n1 k2), 4-point DFTs over n1.  Same transform as four radix-2 stages
+    // with fewer live registers (fewer spills in the 64-register kernels).
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) dft4_reg<T, SIGN>(x[n1], x[n1 + 4], x[n1 + 8], x[n1 + 12]);
+#pragma unroll
+    for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+      for (int k2 = 1; k2 < 4; ++k2) x[n1 + 4 * k2] = rot32<T, SIGN>(x[n1 + 4 * k2], 2 * n1 * k2);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) dft4_reg<T, SIGN>(x[4 * k2], x[4 * k2 + 1], x[4 * k2 + 2], x[4 * k2 + 3]);
+    // x[4 k2 + k1] holds X[k2 + 4 k1]: transpose the 4 x 4 index (register renaming)
+    V2<T> t[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) t[k2 + 4 * k1] = x[4 * k2 + k1];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x[e] = t[e];
+  } else {
+    dft_reg_radix2<T, LR, SIGN>(x);
   }
 }
 

@@ -175,14 +175,17 @@ template <> struct ColPlan<256> {
 };
 
 // ------------------------------------------------------------------ pass T (forward)
-// Gather with a known pixel (cached pointing).
+// The samples t (even) and t + 1 with known pixels (cached pointing): one 16-byte
+// load of their two (cos 2phi, sin 2phi).
 template <int NC>
-__device__ __forceinline__ float gather_fast(const TodArgs& a, int p, const float2 pol, int t) {
-  if (NC == 1) return __ldg((const float*)a.gather + p);
-  const float4 g = __ldg((const float4*)a.gather + p);
-  float c, s;
-  response_fast(a, t, pol, c, s);
-  return fmaf(s, g.z, fmaf(c, g.y, g.x));
+__device__ __forceinline__ float2 gather_pair(const TodArgs& a, const int2 p, const float2 pol, int t) {
+  if (NC == 1) return make_float2(__ldg((const float*)a.gather + p.x), __ldg((const float*)a.gather + p.y));
+  const float4 g0 = __ldg((const float4*)a.gather + p.x);
+  const float4 g1 = __ldg((const float4*)a.gather + p.y);
+  const float4 r = __ldg(reinterpret_cast<const float4*>(a.rot2 + t));
+  const float c0 = pol.x * r.x - pol.y * r.y, s0 = pol.y * r.x + pol.x * r.y;
+  const float c1 = pol.x * r.z - pol.y * r.w, s1 = pol.y * r.z + pol.x * r.w;
+  return make_float2(fmaf(s0, g0.z, fmaf(c0, g0.y, g0.x)), fmaf(s1, g1.z, fmaf(c1, g1.y, g1.x)));
 }
 
 template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
@@ -216,10 +219,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_fas
 #pragma unroll
       for (int e = 0; e < kE; ++e) pq[e] = __ldcs(pp + e * (dt / 2));
 #pragma unroll
-      for (int e = 0; e < kE; ++e) {
-        const int t = t0 + e * dt;
-        ad.st(i + e * TPC, make_float2(gather_fast<NC>(a, pq[e].x, pol, t), gather_fast<NC>(a, pq[e].y, pol, t + 1)));
-      }
+      for (int e = 0; e < kE; ++e) ad.st(i + e * TPC, gather_pair<NC>(a, pq[e], pol, t0 + e * dt));
     } else {
 #pragma unroll kGenUnroll
       for (int e = 0; e < kE; ++e) {

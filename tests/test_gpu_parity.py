@@ -291,6 +291,8 @@ def test_pcg_circulant_config1(cmm, ctx):
     assert abs(info.iterations - io.iterations) <= max(2, 0.1 * io.iterations)
     assert rel(host(x), xo) < 1e-5
     assert info.rel_resid <= 1e-6 and info.true_rel_resid < 2e-6
+    _, info2, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=400, true_resid=False)
+    assert info2.iterations == info.iterations and info2.true_rel_resid == -1.0
 
 
 # ---------------------------------------------------------------- fast-path sizes
