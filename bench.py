@@ -448,11 +448,17 @@ TRAFFIC_SOURCES = ("tod_fast.cu", "fft_reg.cuh", "fft.cuh", "tod_common.cuh", "c
 
 
 def kernel_sources_digest():
+    """SHA-256 over the kernels' sources with comments and blank space removed (the
+    counters depend on the code, not on its comments)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_1309_7473_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1309_7473_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -1,23 +1,25 @@
 // Fast path of A = P^T N^-1 P for FP32 compute (FP32 or BF16 spectrum storage).
 //
 // The complex length N = n_t / 2 is split as N = R C with short columns
-// (R = 64 or 128) and long rows (C = N / R up to 4096):
+// (R = 64, 128 or 256) and long rows (C = N / R, 64 to 2048 points):
 //
-//   k_fast_fwd:     pass T.  A CTA holds 32 adjacent columns; thread (lane cl, warp i)
-//                   owns the 16 rows i + e R/16 of column c0 + cl, so every warp
-//                   reads 64 consecutive samples at a time (coalesced boresight and
-//                   gather loads).  P m is produced on the fly, transformed by a
+//   k_fast_fwd:     pass T.  A CTA holds J = 32 (R <= 128) or 16 (R = 256) adjacent
+//                   columns; thread (cl, i) owns the 16 rows i + e R/16 of column
+//                   c0 + cl, so each group of J lanes reads 2J consecutive samples
+//                   at a time (coalesced pixel-cache, boresight and rotation loads).
+//                   P m is produced into a shared tile, transformed by a
 //                   register-resident R-point FFT and stored times w_N^{c k_r}.
 //   k_fast_filter:  pass F.  Row pairs (k_r, R - k_r) of C points: forward FFT, the
 //                   real-FFT split, the noise filter w_d(f), the merge, inverse FFT.
-//   k_fast_inv_bin: pass T'.  Inverse R-point FFTs; each warp then holds 64
-//                   consecutive filtered samples in lane order, and runs of samples
-//                   that fall in the same pixel are summed by a warp-level segmented
-//                   scan, so that one vector FP32 reduction per run goes to an
-//                   L2-resident partial map.
+//   k_fast_inv_bin: pass T'.  Inverse R-point FFTs into a padded shared tile; each
+//                   lane then takes 8 consecutive filtered samples, sums runs of
+//                   samples in the same pixel in registers and issues one vector FP32
+//                   reduction per run into an L2-resident partial map.
 //   k_fast_flush:   adds the FP32 partial map into the FP64 accumulator and clears
 //                   it, after every group of at most kFlushDets detectors, so each
-//                   FP32 partial sums a bounded number of samples.
+//                   FP32 partial sums a bounded number of samples (operators with
+//                   more samples on a pixel than that allows bin with the generic
+//                   kernel instead, see kF32HitLimit).
 #include <math.h>
 
 #include <algorithm>
