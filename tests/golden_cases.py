@@ -22,7 +22,7 @@ import gen
 from gen.inputs import QB, QD, QR
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-NAMES = ("runs_T_filters", "two_angle_blocks_TQU", "rotated_offset_pointing")
+NAMES = ("runs_T_filters", "two_angle_blocks_TQU", "rotated_offset_pointing", "common_mode_pair_T")
 
 # (cos phi, sin phi) in rotation units for the angles the fixtures use: exact
 _ROT = {0: (QR, 0), 90: (0, QR), 180: (-QR, 0), 270: (0, -QR)}
@@ -74,6 +74,16 @@ def table_of(case: dict, n_det: int, n_t: int):
         if key in spec:
             w[:, k] = float(spec[key])
     return w
+
+
+def corr_of(case: dict):
+    """The case's noise correlated between detectors (templates and mode spectra),
+    or None."""
+    c = case.get("corr")
+    if c is None:
+        return None
+    return gen.CorrNoise(np.array(c["modes"], np.float64), np.array(c["amp"], np.float64),
+                         np.array(c["fknee"], np.float64), np.array(c["alpha"], np.float64))
 
 
 def map_of(fx: dict) -> np.ndarray:

@@ -17,7 +17,7 @@ IDS = [f"{name}-{case['name']}" for name, _, case in CASES]
 def operator(fx, case, K):
     scan = gc.scan_of(fx, K)
     noise = gc.noise_of(case, scan.n_det)
-    return om.make_operator(scan, noise, w=gc.table_of(case, scan.n_det, scan.n_t)), scan
+    return om.make_operator(scan, noise, w=gc.table_of(case, scan.n_det, scan.n_t), corr=gc.corr_of(case)), scan
 
 
 @pytest.mark.parametrize("K", [1, 16])
