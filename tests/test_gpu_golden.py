@@ -1,9 +1,9 @@
 """The CUDA path, through the C-ABI, on the hand-worked examples of
-``tests/golden/`` (Eq. 1-4; correlated noise per reading R13), at the examples' 64-sample period (generic
-kernels), repeated to 2^13 samples (the smallest size of the register-resident
-FFT kernels) and to 2^20 samples (the per-detector length of the 1024-detector
-workload, the four-step split 256 x 2048).  Every A m scales by the number of
-repeats K."""
+``tests/golden/`` (Eq. 1-4; correlated noise per reading R13), at the examples'
+64-sample period (generic kernels), repeated to 2^13 samples (the smallest size
+of the register-resident FFT kernels) and to 2^20 samples (the per-detector
+length of the 1024-detector workload, the four-step split 256 x 2048).  Every
+A m scales by the number of repeats K."""
 import numpy as np
 import pytest
 
