@@ -141,7 +141,9 @@ const char* cmm_version(void);
  * (1, cos 2a, sin 2a), a = psi + phi, for TQU maps (Sec. Test setup).  Samples off
  * the map (unless periodic) and samples of masked pixels have a zero row.  A pixel is
  * masked when its unit-weight hit block sum_t P_t P_t^T has no hits or reciprocal
- * condition number below 1e-3.  The tables are copied.
+ * condition number below 1e-3.  The tables are copied.  Limits: ny * nx <= 2^28
+ * pixels (the kernels index the 4-wide per-pixel accumulators in 32 bits),
+ * 1 <= n_det <= 65535; otherwise CMM_ERR_ARG.
  */
 int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det,
                         const int32_t* det_off, const double* det_pol, int64_t n_samp,

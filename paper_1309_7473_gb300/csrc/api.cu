@@ -215,8 +215,9 @@ int cmm_pointing_create(cmm_ctx* ctx, const cmm_map_geom* geom, int32_t n_det, c
                         const double* det_pol, int64_t n_samp, const int32_t* bore, cmm_pointing** out) {
   if (!ctx || !geom || !det_off || !det_pol || !bore || !out) return fail(CMM_ERR_ARG, "null argument");
   *out = nullptr;
-  if (geom->ny <= 0 || geom->nx <= 0 || (long long)geom->ny * geom->nx > (1LL << 30))
-    return fail(CMM_ERR_ARG, "bad map size");
+  // 4 (npix + 1) accumulator entries must stay below 2^31 for the kernels' 32-bit indices
+  if (geom->ny <= 0 || geom->nx <= 0 || (long long)geom->ny * geom->nx > (1LL << 28))
+    return fail(CMM_ERR_ARG, "bad map size (1 <= ny * nx <= 2^28)");
   if (geom->ncomp != 1 && geom->ncomp != 3) return fail(CMM_ERR_ARG, "ncomp must be 1 or 3");
   if (n_det <= 0 || n_samp <= 0 || n_det > 65535) return fail(CMM_ERR_ARG, "bad detector or sample count");
   // ranges under which the fixed-point pointing is exact in int32

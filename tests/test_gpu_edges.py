@@ -91,6 +91,8 @@ def test_rejected_inputs(cmm, ctx):
         cmm.cmm_pointing_create(ctx.h, scan.ny, scan.nx, 3, False, far, scan.det_pol, scan.bore)
     with pytest.raises(cmm.CmmError):
         cmm.cmm_pointing_create(ctx.h, scan.ny, scan.nx, 2, False, scan.det_off, scan.det_pol, scan.bore)
+    with pytest.raises(cmm.CmmError, match="map size"):   # beyond 2^28 pixels, before any allocation
+        cmm.cmm_pointing_create(ctx.h, 1 << 14, (1 << 14) + 1, 3, False, scan.det_off, scan.det_pol, scan.bore)
     with pytest.raises(cmm.CmmError):
         cmm.cmm_noise_create(ctx.h, scan.n_t, scan.f_samp, np.array([-1.0]), np.array([1.0]), np.array([3.5]))
     op = cmm.Operator(ctx, scan, noise, precision=1)
