@@ -313,6 +313,7 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": measured_traffic(dom, chunk_dets, args),
+                     "binding_unit": measured_units(dom, args),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                      "algorithmic_bytes_per_launch": per_launch_bytes[dom]},
         "apply": {"ms": prof[4], "samples_per_s": n_s / (prof[4] / 1e3), "algorithmic_GBps": apply_gbs,
@@ -460,6 +461,24 @@ def kernel_sources_digest():
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()
+
+
+def measured_units(dom, args):
+    """L1TEX data-pipe and issue-slot utilisation (% of peak) of the dominant pass
+    from the same committed ncu capture as the traffic; None when it does not apply
+    to the current kernels or configuration."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+        digest = kernel_sources_digest()
+    except (OSError, ValueError):
+        return None
+    key = f"{args.prec}/{args.pointing}/{args.n_t}"
+    if rec.get("kernel_sources_sha256") != digest or key not in rec.get("l1tex_pct_of_peak", {}):
+        return None
+    return {"l1tex_pct_of_peak": rec["l1tex_pct_of_peak"][key][dom],
+            "issue_active_pct": rec["issue_active_pct"][key][dom],
+            "source": "ncu --set full, profiles/apply_kernels_64x2p20_full.md"}
 
 
 def measured_traffic(dom, chunk_dets, args):
