@@ -253,8 +253,10 @@ def run_ours(args, rank, world):
             op.set_pixel_cache(False)
             prof_otf = cmm.cmm_profile_apply(op.h, b, mo, 3)
             op.set_pixel_cache(True)
-    names = ["k_tod_fwd (pointing+gather+FFT pass 1)", "k_tod_filter (FFT pass 2 + N^-1)",
-             "k_tod_inv_bin (inverse FFT pass + P^T)"]
+    fast = args.prec != "f64" and (1 << 13) <= scan.n_t <= (1 << 21)   # the register-FFT kernels
+    pre = "k_fast_" if fast else "k_tod_"
+    names = [pre + "fwd (pointing + gather + column FFTs)", pre + "filter (row FFTs + N^-1)",
+             pre + "inv_bin (inverse column FFTs + P^T)"]
     chunk_dets = min(op_chunk(op, scan, args), scan.n_det)
     elt = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
     # filter pass: 8 B/sample; with correlated noise split (r+w) + cross-detector read + merge (r+w)
@@ -266,6 +268,7 @@ def run_ours(args, rank, world):
     achieved = per_launch_bytes[dom] / (prof[dom] / 1e3) / 1e9
     apply_bytes = (elt + per_launch_bytes[1] // (chunk_dets * scan.n_t)) * n_s + 16 * scan.n_t + scan.npix * (3 * 8 * 2 + 16 * 2)
     apply_gbs = apply_bytes / (prof[4] / 1e3) / 1e9
+    traffic = measured_traffic(dom, chunk_dets, args)
 
     cufft = cufft_filter_ms(scan, noise, dev, stream) if args.prec == "f32" else None
 
@@ -312,7 +315,9 @@ def run_ours(args, rank, world):
         "gpu_launches": None,
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": measured_traffic(dom, chunk_dets, args),
+                     "traffic": traffic,
+                     # the ncu DRAM bytes of the pass over its CUDA-event time: what HBM actually moved
+                     "dram_frac": None if traffic is None else traffic / (prof[dom] / 1e3) / 1e9 / peak,
                      "binding_unit": measured_units(dom, args),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                      "algorithmic_bytes_per_launch": per_launch_bytes[dom]},
