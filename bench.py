@@ -253,7 +253,7 @@ def run_ours(args, rank, world):
             op.set_pixel_cache(False)
             prof_otf = cmm.cmm_profile_apply(op.h, b, mo, 3)
             op.set_pixel_cache(True)
-    fast = args.prec != "f64" and (1 << 13) <= scan.n_t <= (1 << 21)   # the register-FFT kernels
+    fast = args.prec != "f64" and (1 << 13) <= scan.n_t <= (1 << 20)   # the register-FFT kernels
     pre = "k_fast_" if fast else "k_tod_"
     names = [pre + "fwd (pointing + gather + column FFTs)", pre + "filter (row FFTs + N^-1)",
              pre + "inv_bin (inverse column FFTs + P^T)"]

@@ -296,7 +296,7 @@ def test_pcg_circulant_config1(cmm, ctx):
 
 
 # ---------------------------------------------------------------- fast-path sizes
-# The FP32 kernels with register-resident FFTs serve n_samp = 2^13 .. 2^21; these
+# The FP32 kernels with register-resident FFTs serve n_samp = 2^13 .. 2^20; these
 # cases run them on the ACT-like focal plane at the bench's per-detector sizes
 # (2^20 samples = the launch configuration of the 1024-detector bench) on a few
 # detectors spread over the focal plane, which the oracle evaluates in seconds.
