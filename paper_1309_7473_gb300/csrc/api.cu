@@ -847,9 +847,13 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
   const int64_t npix = pt->npix;
   const int nb = nc == 1 ? 1 : 6;
   CMM_TRY(fft2_plan_init<T>(pc->plan, pt->ny, pt->nx));
+  // the build (q, its transform and the per-mode inverse) is FP64 in every precision
+  // mode; only the apply's transforms follow the operator's precision
+  Fft2Plan plan64;
+  CMM_TRY(fft2_plan_init<double>(plan64, pt->ny, pt->nx));
   double* blocks = nullptr;
   double* rows = nullptr;
-  void* qplanes = nullptr;
+  double2* qplanes = nullptr;
   unsigned long long* scratch = nullptr;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
@@ -857,11 +861,12 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
     dfree(rows);
     dfree(qplanes);
     dfree(scratch);
+    dfree(plan64.tw);
   };
   auto run = [&]() -> int {
     CMM_TRY(dalloc(&blocks, sizeof(double) * nb * npix));
     CMM_TRY(dalloc(&rows, sizeof(double) * nc * nc * npix));
-    CMM_TRY(dalloc(&qplanes, sizeof(V2<T>) * nc * nc * npix));
+    CMM_TRY(dalloc(&qplanes, sizeof(double2) * nc * nc * npix));
     CMM_TRY(dalloc(&scratch, sizeof(unsigned long long) * 2));
     CMM_TRY(dalloc(&pc->sig, sizeof(double) * nb * npix));
     CMM_TRY(dalloc(&pc->sig_inv, sizeof(double) * nb * npix));
@@ -889,10 +894,10 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
     // Eq. 13 + symmetrisation + Gaussian taper, then Eq. 11: H = conj(F q)
     double taper = (o && o->taper_sigma_px > 0 && std::isfinite(o->taper_sigma_px)) ? o->taper_sigma_px : 0.0;
     pc->taper = taper;
-    CMM_TRY(launch_circ_q<T>(nc, rows, pc->sig_inv, (int)ref, pt->ny, pt->nx, taper, (V2<T>*)qplanes, st));
-    CMM_TRY(fft2<T>(pc->plan, (V2<T>*)qplanes, nc * nc, -1, nullptr, st));
+    CMM_TRY(launch_circ_q<double>(nc, rows, pc->sig_inv, (int)ref, pt->ny, pt->nx, taper, qplanes, st));
+    CMM_TRY(fft2<double>(plan64, qplanes, nc * nc, -1, nullptr, st));
     const double eps = (o && o->pd_eps > 0) ? o->pd_eps : 1e-6;
-    CMM_TRY(launch_mode_inverse<T>(nc, (const V2<T>*)qplanes, npix, eps, pc->hinv, scratch, st));
+    CMM_TRY(launch_mode_inverse<double>(nc, qplanes, npix, eps, pc->hinv, scratch, st));
     unsigned long long h[2];
     CMM_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
     CMM_CUDA(cudaStreamSynchronize(st));
