@@ -14,7 +14,7 @@ R1  noise filter w_d(f) = 1 / (sigma_d^2 (1 + (f/f_knee)^-alpha)), f_k = k f_s /
     with f_knee = 0 meaning white noise.
 R2  the DC bin, where the law diverges, takes the first non-zero bin's value.
 R3  diag(N^-1) in Eq. 3 / Eq. 7 is the exact diagonal of the circulant filter,
-    the mean of w over the two-sided DFT grid.
+    the mean of w over the two-sided DFT grid (option: the white level 1/sigma_d^2).
 R4  Sigma in Eq. 7 is the symmetric positive square root of each block; a pixel
     whose unit-weight hit block has reciprocal condition < RCOND_MIN (or no hits)
     is masked: its samples are cut from P everywhere.
@@ -150,6 +150,17 @@ def filter_weights(noise, n_t, f_samp):
             psd = np.full(f.shape, noise.sigma[d] ** 2)
         out[d] = 1.0 / psd
     return out
+
+
+def white_weights(noise):
+    """R3's alternative detector weight: the white level 1 / sigma_d^2 of the law R1."""
+    return 1.0 / noise.sigma ** 2
+
+
+def detector_weights(op, white=False):
+    """The per-detector diag(N^-1) of Eq. 3 and Eq. 7: R3 (exact circulant diagonal),
+    or with ``white`` its alternative 1 / sigma_d^2."""
+    return white_weights(op.noise) if white else ninv_diagonal(op.w, op.scan.n_t)
 
 
 def ninv_diagonal(w, n_t):
@@ -348,8 +359,8 @@ class BlockPrecon:
     """M = (per-pixel block of P^T D P)^-1 with D = diag(N^-1) (binned, Eq. 3-4)
     or D = I (Jacobi, Eq. 5, a = 1)."""
 
-    def __init__(self, op, kind="binned"):
-        u = ninv_diagonal(op.w, op.scan.n_t) if kind == "binned" else None
+    def __init__(self, op, kind="binned", white=False):
+        u = detector_weights(op, white) if kind == "binned" else None
         self.blocks = hit_blocks(op.scan, u, op.mask)
         self.inv = _block_inverse(self.blocks, op.mask)
 
@@ -439,7 +450,7 @@ class TiledCirculantPrecon:
     M = sum_t D_t M_t D_t, D_t = diag(sqrt(phi_t)) on every Stokes component
     (symmetric positive definite whenever every M_t is)."""
 
-    def __init__(self, op, tiles=(2, 2), taper_sigma=math.inf, pd_eps=PD_EPS):
+    def __init__(self, op, tiles=(2, 2), taper_sigma=math.inf, pd_eps=PD_EPS, white=False):
         nc, ny, nx = op.shape
         ty, tx = tiles
         self.shape = op.shape
@@ -448,7 +459,8 @@ class TiledCirculantPrecon:
         for i in range(ty):
             for j in range(tx):
                 ref = tile_reference(op.mask, ny, nx, int((i + 0.5) * ny / ty), int((j + 0.5) * nx / tx))
-                self.parts.append(CirculantPrecon(op, taper_sigma=taper_sigma, ref=ref, pd_eps=pd_eps))
+                self.parts.append(CirculantPrecon(op, taper_sigma=taper_sigma, ref=ref, pd_eps=pd_eps,
+                                                  white=white))
 
     def __call__(self, r):
         z = np.zeros(self.shape)
@@ -470,12 +482,12 @@ class CirculantPrecon:
     """M_C = Sigma^-1 F^-1 ((Fq)*)^-1 F Sigma^-T (Eq. 12), built from the rows
     A e_{ref,gamma} (Eq. 6, Eq. 13)."""
 
-    def __init__(self, op, taper_sigma=math.inf, ref=None, pd_eps=PD_EPS):
+    def __init__(self, op, taper_sigma=math.inf, ref=None, pd_eps=PD_EPS, white=False):
         scan = op.scan
         nc, ny, nx = op.shape
         self.nc, self.ny, self.nx = nc, ny, nx
         # Eq. 7: Sigma^T Sigma = binned block
-        u = ninv_diagonal(op.w, scan.n_t)
+        u = detector_weights(op, white)
         blocks = hit_blocks(scan, u, op.mask)
         self.sigma, self.sigma_inv = _sym_sqrt(blocks, op.mask)
         self.ref = reference_pixel(op.mask, ny, nx) if ref is None else int(ref)

@@ -320,6 +320,28 @@ def test_flexible_cg_equals_pcg_for_fixed_preconditioner(tiny):
 # preconditioners (Eq. 3-5, 7-13)
 # ---------------------------------------------------------------------------
 
+def test_white_level_weights_alternative_of_R3(tiny):
+    """R3's alternative weight 1/sigma_d^2 (Eq. 3): for the law R1 every bin weight is
+    at most the white level, so the exact circulant diagonal lies below it, with
+    equality for white noise, where both binned preconditioners coincide (and, the
+    binned blocks being all of A there, equal A^-1)."""
+    op = tiny
+    exact = om.detector_weights(op)
+    white = om.detector_weights(op, white=True)
+    np.testing.assert_allclose(white, 1.0 / op.noise.sigma ** 2, rtol=0, atol=0)
+    assert np.all(exact < white)
+    wn = gen.noise_params(op.scan.n_det, sigma=1.0, fknee=0.0, alpha=3.5, scatter=0.2, cfg=101)
+    wn.fknee[:] = 0.0
+    opw = om.make_operator(op.scan, wn)
+    np.testing.assert_allclose(om.detector_weights(opw), om.detector_weights(opw, white=True), rtol=1e-14)
+    r = gen.random_maps(3, op.scan.ny, op.scan.nx, 1, cfg=102)[0] * opw.mask.reshape(op.scan.ny, op.scan.nx)
+    z1 = om.BlockPrecon(opw)(r)
+    z2 = om.BlockPrecon(opw, white=True)(r)
+    np.testing.assert_allclose(z1, z2, rtol=1e-12, atol=1e-14)
+    # 1/f noise: the blocks scale detector by detector, so the two differ
+    assert not np.allclose(om.BlockPrecon(op)(r), om.BlockPrecon(op, white=True)(r))
+
+
 def test_binned_blocks_are_block_diagonal_of_PtDP():
     """M_B^-1 (Eq. 4) is the per-pixel block of P^T diag(N^-1) P, with diag(N^-1) the
     diagonal of the dense inverse covariance."""
