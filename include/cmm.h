@@ -87,6 +87,10 @@ typedef struct {
                                w_i(y) w_j(x) with raised-cosine windows w_i (centres
                                (i + 1/2) n / t, half-width n / t, the outer ones held at 1
                                towards the edges) summing to 1 (Summary section's variant) */
+  int32_t white_diag;    /* != 0: the detector weights diag(N^-1)_d of Eq. 3 and Eq. 7 are the
+                            white level 1 / sigma_d^2 of the noise law instead of the exact
+                            diagonal of the Fourier-diagonal N_d^-1 (the mean of w_d(f) over
+                            the DFT grid); BINNED, CIRCULANT and CIRC_TILED */
 } cmm_precon_opts;
 
 typedef struct {

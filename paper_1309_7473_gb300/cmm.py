@@ -38,7 +38,7 @@ class MapGeom(C.Structure):
 
 class PreconOpts(C.Structure):
     _fields_ = [("taper_sigma_px", C.c_double), ("ref_pixel", C.c_int64), ("pd_eps", C.c_double),
-                ("tiles_y", C.c_int32), ("tiles_x", C.c_int32)]
+                ("tiles_y", C.c_int32), ("tiles_x", C.c_int32), ("white_diag", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -292,8 +292,9 @@ def cmm_dot(op, x, y):
     return out.value
 
 
-def cmm_precon_create(op, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0)):
-    opts = PreconOpts(float(taper_sigma_px), int(ref_pixel), float(pd_eps), int(tiles[0]), int(tiles[1]))
+def cmm_precon_create(op, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0), white_diag=False):
+    opts = PreconOpts(float(taper_sigma_px), int(ref_pixel), float(pd_eps), int(tiles[0]), int(tiles[1]),
+                      1 if white_diag else 0)
     h = C.c_void_p()
     _check(_lib.cmm_precon_create(op, kind, C.byref(opts), C.byref(h)))
     return h
@@ -510,10 +511,11 @@ class Operator:
 
 
 class Precon:
-    def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0)):
+    def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0),
+                 white_diag=False):
         self.op = op
         self.kind = kind
-        self.h = cmm_precon_create(op.h, kind, taper_sigma_px, ref_pixel, pd_eps, tiles)
+        self.h = cmm_precon_create(op.h, kind, taper_sigma_px, ref_pixel, pd_eps, tiles, white_diag)
 
     def apply(self, r, out=None):
         out = self.op.new_map() if out is None else out

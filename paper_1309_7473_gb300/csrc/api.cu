@@ -299,6 +299,7 @@ static void free_noise(cmm_noise* nz) {
   dfree(nz->coef64);
   dfree(nz->coef32);
   dfree(nz->diag);
+  dfree(nz->white);
   dfree(nz->corr_V);
   dfree(nz->corr_par);
   dfree(nz->wtab64);
@@ -324,9 +325,11 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
   if (n_det <= 0 || n_samp < 2 || !(f_samp > 0)) return fail(CMM_ERR_ARG, "bad noise sizes");
   std::vector<double4_32a> c64(n_det);
   std::vector<float4> c32(n_det);
+  std::vector<double> white(n_det);
   for (int d = 0; d < n_det; ++d) {
     if (!(sigma[d] > 0) || fknee[d] < 0 || !std::isfinite(alpha[d])) return fail(CMM_ERR_ARG, "bad noise parameter");
     const double iv = 1.0 / (sigma[d] * sigma[d]);
+    white[d] = iv;
     if (fknee[d] == 0.0) {
       c64[d] = double4_32a{iv, 0.0, 0.0, 1.0};
     } else {
@@ -345,6 +348,7 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
   int s = dalloc(&nz->coef64, sizeof(double4_32a) * n_det);
   if (s == CMM_OK) s = dalloc(&nz->coef32, sizeof(float4) * n_det);
   if (s == CMM_OK) s = dalloc(&nz->diag, sizeof(double) * n_det);
+  if (s == CMM_OK) s = dalloc(&nz->white, sizeof(double) * n_det);
   if (s != CMM_OK) {
     cmm_noise_destroy(nz);
     return s;
@@ -353,6 +357,7 @@ int cmm_noise_create(cmm_ctx* ctx, int32_t n_det, int64_t n_samp, double f_samp,
     cudaStream_t st = ctx->stream;
     CMM_CUDA(cudaMemcpyAsync(nz->coef64, c64.data(), sizeof(double4_32a) * n_det, cudaMemcpyHostToDevice, st));
     CMM_CUDA(cudaMemcpyAsync(nz->coef32, c32.data(), sizeof(float4) * n_det, cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaMemcpyAsync(nz->white, white.data(), sizeof(double) * n_det, cudaMemcpyHostToDevice, st));
     k_noise_diag<<<n_det, 256, 0, st>>>(nz->coef64, n_samp, nz->diag);
     CMM_LAUNCH_CHECK();
     nz->diag_host.resize(n_det);
@@ -838,6 +843,12 @@ static int64_t pick_reference(const std::vector<uint8_t>& mask, int ny, int nx) 
 
 }  // extern "C"
 
+// Detector weights diag(N^-1)_d of Eq. 3 and Eq. 7: the exact diagonal of the
+// circulant filter, or with opts->white_diag the white level 1 / sigma_d^2.
+static const double* precon_weights(const cmm_op* op, const cmm_precon_opts* o) {
+  return (o && o->white_diag) ? op->nz->white : op->nz->diag;
+}
+
 template <typename T>
 static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
   cmm_op* op = pc->op;
@@ -875,7 +886,7 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
     CMM_TRY(dalloc(&pc->tmp, sizeof(double) * nc * npix));
     // Eq. 7: Sigma^T Sigma = binned blocks
     CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * npix, st));
-    CMM_TRY(launch_hit_blocks(pt, op->nz->diag, pt->mask, blocks, nullptr));
+    CMM_TRY(launch_hit_blocks(pt, precon_weights(op, o), pt->mask, blocks, nullptr));
     CMM_TRY(launch_block_sqrt(nc, npix, blocks, pt->mask, pc->sig, pc->sig_inv, st));
     // reference pixel
     std::vector<uint8_t> mask(npix);
@@ -934,7 +945,8 @@ int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm
     if (s == CMM_OK) {
       auto run = [&]() -> int {
         CMM_CUDA(cudaMemsetAsync(blocks, 0, sizeof(double) * nb * pt->npix, st));
-        CMM_TRY(launch_hit_blocks(pt, kind == CMM_PRECON_BINNED ? op->nz->diag : nullptr, pt->mask, blocks, nullptr));
+        CMM_TRY(launch_hit_blocks(pt, kind == CMM_PRECON_BINNED ? precon_weights(op, opts) : nullptr, pt->mask,
+                                  blocks, nullptr));
         CMM_TRY(launch_block_inverse(pt->ncomp, pt->npix, blocks, pt->mask, pc->inv, st));
         CMM_CUDA(cudaStreamSynchronize(st));
         return CMM_OK;

@@ -125,6 +125,7 @@ struct cmm_noise {
   double* wtab64 = nullptr;    // optional [n_det][n_t/2 + 1] tabulated w_d(f_k) (replaces the law)
   float* wtab32 = nullptr;
   double* diag = nullptr;      // [n_det] diag(N^-1)
+  double* white = nullptr;     // [n_det] 1 / sigma^2, the white level of the law
   std::vector<double> diag_host;
   // noise correlated between detectors: N(f) = D(f) + V E(f) V^T (r modes, 0 = none)
   int corr_r = 0;

@@ -234,6 +234,21 @@ def test_circulant_precon(cmm, ctx, prec, ncomp, taper):
         assert pc.clamped() == ref.n_clamped
 
 
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_white_level_weights(cmm, ctx, ncomp):
+    """The alternative reading of diag(N^-1) in Eq. 3 and Eq. 7 (white level
+    1/sigma_d^2) against the oracle, binned and circulant, and unlike the default."""
+    scan, noise = small(ncomp)
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    r = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=212)[0]
+    zb = host(cmm.Precon(op, cmm.PRECON_BINNED, white_diag=True).apply(dev(r)))
+    assert rel(zb, om.BlockPrecon(oop, "binned", white=True)(r)) < 1e-11
+    assert rel(zb, host(cmm.Precon(op, cmm.PRECON_BINNED).apply(dev(r)))) > 1e-3
+    zc = host(cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=3.0, white_diag=True).apply(dev(r)))
+    assert rel(zc, om.CirculantPrecon(oop, taper_sigma=3.0, white=True)(r)) < 1e-9
+
+
 def test_circulant_exact_on_bccb_gpu(cmm, ctx):
     scan, noise = small(3, periodic=True)
     op = cmm.Operator(ctx, scan, noise, precision=0)
