@@ -142,7 +142,7 @@ def oracle_rate(args, seconds, rank=0):
 
     import gen
     from oracle import mapmaker as om
-    scan, noise = gen.config2(real=rank, n_det=args.n_det, n_t=args.n_t)
+    scan, noise = gen.act_patch(real=rank, n_det=args.n_det, n_t=args.n_t)
     n_sub = 4
     sub = scan.subset(np.arange(n_sub))
     nsub = noise.subset(np.arange(n_sub))
@@ -201,7 +201,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(device=dev)
     prec = {"f32": cmm.PREC_F32, "f64": cmm.PREC_F64, "bf16": cmm.PREC_BF16}[args.prec]
     t_setup = time.perf_counter()
-    scan, noise = gen.config2(real=rank, n_det=args.n_det, n_t=args.n_t)
+    scan, noise = gen.act_patch(real=rank, n_det=args.n_det, n_t=args.n_t)
     n_s = scan.n_det * scan.n_t
     with torch.cuda.stream(stream):
         ctx = cmm.Context(dev, stream=stream.cuda_stream)
@@ -349,7 +349,7 @@ def run_learned(args):
     from paper_1309_7473_gb300 import cmm, learned
     widths = (16, 32, 48, 96)
     ctx = cmm.Context(0)
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F64)
     pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
 
@@ -523,7 +523,7 @@ def run_anorm(args):
            "config": {"workload": "1024 det x 2^20 samples, 1200x900 TQU, noise-free TOD, FP32 operator, "
                                   f"circulant taper {args.taper} px", "iterations_marked": marks}, "scans": {}}
     for label, acc in (("instant", None), ("accel_1.5deg_s2", 1.5)):
-        scan, noise = gen.config2(accel_deg_s2=acc)
+        scan, noise = gen.act_patch(accel_deg_s2=acc)
         ctx = cmm.Context(0)
         op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F32)
         op.set_pixel_cache(True)
@@ -562,7 +562,7 @@ def run_spectra(args):
     every, maxit, nbins = 20, 1000, 20
     pix = np.deg2rad(0.5 / 60)
     lmax = 20000.0
-    scan, noise = gen.config2()
+    scan, noise = gen.act_patch()
     ctx = cmm.Context(0)
     op = cmm.Operator(ctx, scan, noise, precision=cmm.PREC_F32)
     op.set_pixel_cache(True)
@@ -619,7 +619,7 @@ def run_batch(args):
     from paper_1309_7473_gb300 import build
     build.build()
     from paper_1309_7473_gb300 import cmm
-    probs = [gen.config4(k) for k in range(args.batch)]
+    probs = [gen.uneven_problem(k) for k in range(args.batch)]
     n_s = [sc.n_det * sc.n_t for sc, _ in probs]
     # device memory: spectrum chunk (4 B/sample, at most 8 GB) per operator + tables
     need = sum(min(4 * n, 8 << 30) + 32 * sc.n_t + 200 * sc.npix for n, (sc, _) in zip(n_s, probs))

@@ -226,14 +226,16 @@ def bccb_scan(ny, nx, n_t, diagonal=False, ncomp=3):
 
 
 # ---------------------------------------------------------------------------
-# the five workloads (config 1: tiny; config 2: ACT-like patch; 3: precision study
-# on config 1; 4: batch of uneven solves; 5: learned-correction data on config 1)
+# the workloads: the tiny patch (32 detectors x 2^16 samples, 64x64 map), the
+# ACT-like patch (1024 detectors x 2^20 samples, 1200x900 map) and the uneven
+# problems of the batched solves; the precision study and the learned-correction
+# data use the tiny patch
 # ---------------------------------------------------------------------------
 
 PIX_ARCMIN = 0.5
 
 
-def config1(real=0, ncomp=3):
+def tiny_patch(real=0, ncomp=3):
     """32 detectors on a 4x8 grid at 1', 2^16 samples at 400 Hz, 1 deg/s, 2 deg throw,
     30 deg sky rotation, 64x64 map at 0.5'; sigma=1, f_knee=2 Hz, alpha=3.5."""
     px_per_deg = 60.0 / PIX_ARCMIN
@@ -246,7 +248,7 @@ def config1(real=0, ncomp=3):
     return scan, noise
 
 
-def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3, accel_deg_s2=None):
+def act_patch(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3, accel_deg_s2=None):
     """1024 detectors on a hex focal plane 1 deg across, 2^20 samples at 400 Hz,
     10 deg throw, a rising half at phi = 25 +- 15 deg and a setting half at
     phi = -25 -+ 15 deg, 1200x900 map at 0.5'; sigma lognormal (mean 1, 20 %),
@@ -258,7 +260,7 @@ def config2(real=0, n_det=1024, n_t=1 << 20, ny=900, nx=1200, ncomp=3, accel_deg
                      speed_px_s=1.0 * px_per_deg, throw_px=10.0 * px_per_deg,
                      segments=((0.5, 10.0, 40.0, True), (0.5, -10.0, -40.0, False)),
                      ncomp=ncomp, accel_px_s2=None if accel_deg_s2 is None else accel_deg_s2 * px_per_deg)
-    return scan, config2_noise(real, n_det)
+    return scan, act_patch_noise(real, n_det)
 
 
 @dataclasses.dataclass
@@ -298,19 +300,19 @@ def corr_noise(det_off, r=3, amp=(3.0, 1.0, 1.0), fknee=(2.0, 1.0, 1.0), alpha=(
                      np.asarray(alpha[:r], float))
 
 
-CONFIG4_MAPS = ((256, 256), (240, 320), (360, 480), (450, 600), (600, 800), (750, 1000), (900, 1200))
+UNEVEN_MAP_SIZES = ((256, 256), (240, 320), (360, 480), (450, 600), (600, 800), (750, 1000), (900, 1200))
 
 
-def config4(k, real=0, ncomp=3):
+def uneven_problem(k, real=0, ncomp=3):
     """Problem k of the batched Monte-Carlo workload: seeded n_det from
     {128, 256, 512, 1024}, n_t from {2^18, 2^19, 2^20} and a 5-smooth map size from
-    256x256 to 1200x900 (ny x nx) at 0.5'; hex focal plane at 1.667', the config-2
-    scan law (rising and setting halves) with a throw of 0.8 of the map width; the
-    config-1 noise law (sigma 1, f_knee 2 Hz, alpha 3.5)."""
+    256x256 to 1200x900 (ny x nx) at 0.5'; hex focal plane at 1.667', the scan law of
+    the ACT-like patch (rising and setting halves) with a throw of 0.8 of the map
+    width; the noise law of the tiny patch (sigma 1, f_knee 2 Hz, alpha 3.5)."""
     g = rng(4, 1000 * real + k, "misc")
     n_det = int(g.choice([128, 256, 512, 1024]))
     n_t = int(g.choice([1 << 18, 1 << 19, 1 << 20]))
-    ny, nx = CONFIG4_MAPS[int(g.integers(len(CONFIG4_MAPS)))]
+    ny, nx = UNEVEN_MAP_SIZES[int(g.integers(len(UNEVEN_MAP_SIZES)))]
     rings = 1
     while 3 * rings * (rings + 1) + 1 < n_det:
         rings += 1
@@ -323,7 +325,7 @@ def config4(k, real=0, ncomp=3):
     return scan, noise
 
 
-def config2_noise(real, n_det):
+def act_patch_noise(real, n_det):
     s = math.sqrt(math.log(1.04))
     mu = -0.5 * math.log(1.04)
     sigma = np.exp(rng(2, real, "sigma").normal(mu, s, size=n_det))
@@ -334,7 +336,7 @@ def config2_noise(real, n_det):
 def small_scan(*, cfg=100, real=0, ny=16, nx=16, n_t=1 << 12, ncols=4, nrows=2,
                spacing_px=1.5, throw_px=None, speed_px_s=None, rot=15.0, ncomp=3,
                f_samp=400.0):
-    """A scaled-down config-1 scan for fast tests; speed defaults to 0.3 px/sample."""
+    """A scaled-down tiny-patch scan for fast tests; speed defaults to 0.3 px/sample."""
     focal = grid_focal_plane(ncols, nrows, spacing_px)
     if throw_px is None:
         throw_px = 1.5 * nx

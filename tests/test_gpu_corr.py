@@ -62,8 +62,8 @@ def test_apply_A_correlated_small(cmm, ctx, prec, r):
     assert rel(host(op.apply(dev(m))), om.apply_A(om.make_operator(scan, noise), m)) < TOL[prec]
 
 
-def test_apply_A_correlated_config2_subset(cmm, ctx):
-    full, fnoise = gen.config2(n_t=1 << 18)
+def test_apply_A_correlated_act_patch_subset(cmm, ctx):
+    full, fnoise = gen.act_patch(n_t=1 << 18)
     dets = np.array([0, 301, 602, 903, 17, 1023])
     scan, noise = full.subset(dets), fnoise.subset(dets)
     corr = gen.corr_noise(scan.det_off)
@@ -75,7 +75,7 @@ def test_apply_A_correlated_config2_subset(cmm, ctx):
 
 
 def test_correlated_symmetry_rhs_and_pcg(cmm, ctx):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     corr = gen.corr_noise(scan.det_off)
     op = cmm.Operator(ctx, scan, noise, precision=1, corr=corr)
     oop = om.make_operator(scan, noise, corr=corr)

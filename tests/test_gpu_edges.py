@@ -54,7 +54,7 @@ def test_white_noise_T_only_is_hit_count(cmm, ctx, prec, cached):
 
 def test_beyond_fast_path_sizes(cmm, ctx):
     """n_samp = 2^21 runs the generic FP32 kernels; parity with the oracle."""
-    full, fnoise = gen.config2(n_t=1 << 21)
+    full, fnoise = gen.act_patch(n_t=1 << 21)
     dets = np.array([5, 700])
     scan, noise = full.subset(dets), fnoise.subset(dets)
     op = cmm.Operator(ctx, scan, noise, precision=1)
@@ -67,13 +67,13 @@ def test_beyond_fast_path_sizes(cmm, ctx):
 def test_single_detector(cmm, ctx, prec):
     """One detector constrains T; with TQU its per-pixel blocks are rank one, every
     pixel fails the conditioning test and A is exactly zero (on both sides)."""
-    full, fnoise = gen.config1(ncomp=1)
+    full, fnoise = gen.tiny_patch(ncomp=1)
     scan, noise = full.subset(np.array([7])), fnoise.subset(np.array([7]))
     op = cmm.Operator(ctx, scan, noise, precision=prec)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=3, ncomp=1)
     assert rel(op.apply(dev(m)).cpu().numpy(), om.apply_A(oop, m)) < {0: 1e-10, 1: 1e-5, 2: 2e-2}[prec]
-    full3, _ = gen.config1()
+    full3, _ = gen.tiny_patch()
     scan3 = full3.subset(np.array([7]))
     op3 = cmm.Operator(ctx, scan3, noise, precision=prec)
     assert op3.pointing.mask()[1] == 0 and not om.pixel_mask(scan3).any()
@@ -81,7 +81,7 @@ def test_single_detector(cmm, ctx, prec):
 
 
 def test_rejected_inputs(cmm, ctx):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     bad_nt = gen.small_scan(cfg=342, ny=8, nx=8, n_t=1000, ncols=2, nrows=1)   # not a power of two
     with pytest.raises(cmm.CmmError):
         cmm.Operator(ctx, bad_nt, gen.noise_params(bad_nt.n_det))
@@ -116,7 +116,7 @@ def test_smallest_sample_count(cmm, ctx, prec):
 
 
 def test_zero_rhs_solves_to_zero(cmm, ctx):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=1)
     pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
     b = dev(np.zeros((3, scan.ny, scan.nx)))

@@ -1,6 +1,6 @@
 """The learned correction: GPU U-Net forward and gradients against the FP64
 oracle, training, and flexible PCG with M_C followed by the trained network
-against plain PCG with M_C on held-out configuration-1 realisations.
+against plain PCG with M_C on held-out tiny-patch realisations.
 
 Tolerances: the GPU network keeps weights and activations in BF16 (8 mantissa
 bits, relative rounding 2^-9 = 2e-3 per stored value) with FP32 accumulation;
@@ -114,8 +114,8 @@ def realisation(scan, noise, oop, real):
     return d
 
 
-def test_learned_correction_config1(cmm, ctx):
-    """Config 5 (reduced): pairs from FP64 M_C solves of 16 seeded config-1
+def test_learned_correction_tiny_patch(cmm, ctx):
+    """Learned correction (reduced): pairs from FP64 M_C solves of 16 seeded tiny-patch
     realisations, a short training with sign augmentation, then on held-out data:
     the trained correction lowers the A-norm error of one preconditioner
     application, e - (z + s U(z/s)) against e - z, and flexible PCG with M_C + U
@@ -124,7 +124,7 @@ def test_learned_correction_config1(cmm, ctx):
     to fewer flexible-CG iterations (flexible CG with a varying preconditioner
     loses the Krylov optimality that makes PCG with a fixed M_C fast)."""
     from paper_1309_7473_gb300 import learned
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     oop = om.make_operator(scan, noise)
     op = cmm.Operator(ctx, scan, noise, precision=0)
     pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)

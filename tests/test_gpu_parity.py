@@ -67,7 +67,7 @@ def small(ncomp=3, periodic=False, cfg=201):
 
 @pytest.mark.parametrize("ncomp", [1, 3])
 def test_mask_bit_exact(cmm, ctx, ncomp):
-    for scan in (small(ncomp)[0], gen.config1(ncomp=ncomp)[0],
+    for scan in (small(ncomp)[0], gen.tiny_patch(ncomp=ncomp)[0],
                  gen.small_scan(cfg=202, ny=16, nx=16, n_t=1 << 10, ncols=2, nrows=1, ncomp=ncomp)):
         pt = cmm.Pointing(ctx, scan)
         mask, n_good = pt.mask()
@@ -77,7 +77,7 @@ def test_mask_bit_exact(cmm, ctx, ncomp):
 
 
 def test_noise_diagonal(cmm, ctx):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     nz = cmm.Noise(ctx, noise, scan.n_t, scan.f_samp)
     w = om.filter_weights(noise, scan.n_t, scan.f_samp)
     assert rel(nz.diag(), om.ninv_diagonal(w, scan.n_t)) < 1e-13
@@ -162,8 +162,8 @@ def test_apply_A_periodic(cmm, ctx, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-def test_apply_A_config1(cmm, ctx, prec):
-    scan, noise = gen.config1()
+def test_apply_A_tiny_patch(cmm, ctx, prec):
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=prec)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
@@ -194,7 +194,7 @@ def test_project_and_rhs(cmm, ctx, prec):
 
 
 def test_A_symmetric_on_gpu(cmm, ctx):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=0)
     x, y = gen.random_maps(3, scan.ny, scan.nx, 2, cfg=206)
     mask = op.pointing.mask()[0].reshape(scan.ny, scan.nx)
@@ -264,8 +264,8 @@ def test_circulant_exact_on_bccb_gpu(cmm, ctx):
 # ---------------------------------------------------------------- solves
 
 @pytest.mark.parametrize("graph", [True, False])
-def test_pcg_binned_config1_matches_oracle(cmm, ctx, graph):
-    scan, noise = gen.config1()
+def test_pcg_binned_tiny_patch_matches_oracle(cmm, ctx, graph):
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=0)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
@@ -291,8 +291,8 @@ def test_pcg_binned_config1_matches_oracle(cmm, ctx, graph):
     assert info.true_rel_resid == pytest.approx(true_o, rel=0.2)
 
 
-def test_pcg_circulant_config1(cmm, ctx):
-    scan, noise = gen.config1()
+def test_pcg_circulant_tiny_patch(cmm, ctx):
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=0)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
@@ -319,7 +319,7 @@ def test_pcg_circulant_config1(cmm, ctx):
 @pytest.mark.parametrize("log_nt", [13, 17, 18, 19, 20])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
-    full, fnoise = gen.config2(n_t=1 << log_nt)
+    full, fnoise = gen.act_patch(n_t=1 << log_nt)
     dets = np.array([0, 300, 611, 1023, 17])
     scan, noise = full.subset(dets), fnoise.subset(dets)
     op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=2)
@@ -334,8 +334,8 @@ def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_apply_A_turnaround_scan(cmm, ctx, prec):
-    """Config-2 detectors on the scan with finite-acceleration turnarounds."""
-    full, fnoise = gen.config2(n_t=1 << 18, accel_deg_s2=1.5)
+    """ACT-like patch detectors on the scan with finite-acceleration turnarounds."""
+    full, fnoise = gen.act_patch(n_t=1 << 18, accel_deg_s2=1.5)
     dets = np.array([3, 500, 1000])
     scan, noise = full.subset(dets), fnoise.subset(dets)
     op = cmm.Operator(ctx, scan, noise, precision=prec)
@@ -359,7 +359,7 @@ def test_apply_A_fast_small_ragged(cmm, ctx, ncomp):
 def test_full_size_symmetry_and_rhs(cmm, ctx):
     """At the bench's full size (1024 x 2^20, 1200x900): x^T A y = y^T A x, and the
     right-hand side of noise-free data P m equals A m."""
-    scan, noise = gen.config2()
+    scan, noise = gen.act_patch()
     op = cmm.Operator(ctx, scan, noise, precision=1)
     x, y = gen.random_maps(3, scan.ny, scan.nx, 2, cfg=211)
     mask = op.pointing.mask()[0].reshape(scan.ny, scan.nx)
@@ -376,12 +376,12 @@ def test_full_size_symmetry_and_rhs(cmm, ctx):
     assert rel(host(op.apply(m)), b2) < 1e-6
 
 
-# ---------------------------------------------------------------- precision modes (config 3)
+# ---------------------------------------------------------------- precision modes (tiny patch)
 
 @pytest.fixture(scope="module")
-def cfg1_solution():
-    """Config 1, noise-free data: the FP64 oracle's tightly converged solution."""
-    scan, noise = gen.config1()
+def tiny_solution():
+    """Tiny patch, noise-free data: the FP64 oracle's tightly converged solution."""
+    scan, noise = gen.tiny_patch()
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
     d = om.project(oop, m)
@@ -393,10 +393,10 @@ def cfg1_solution():
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("cg_f32", [False, True])
-def test_precision_grid_config1(cmm, ctx, cfg1_solution, prec, cg_f32):
+def test_precision_grid_tiny_patch(cmm, ctx, tiny_solution, prec, cg_f32):
     """TOD/filter in FP32 or BF16 storage x CG in FP64 or FP32 with residual
     replacement every 50 iterations: converges to 1e-6 with the stated errors."""
-    scan, noise, d, b_ref, x_ref, info_ref = cfg1_solution
+    scan, noise, d, b_ref, x_ref, info_ref = tiny_solution
     op = cmm.Operator(ctx, scan, noise, precision=prec)
     b = op.rhs(torch.as_tensor(d, dtype=torch.float32, device="cuda:0"))
     pc = cmm.Precon(op, cmm.PRECON_BINNED)
@@ -410,8 +410,8 @@ def test_precision_grid_config1(cmm, ctx, cfg1_solution, prec, cg_f32):
     assert err < (2e-5 if prec == 1 else 2e-2)
 
 
-def test_flexible_cg_matches_pcg_gpu(cmm, ctx, cfg1_solution):
-    scan, noise, d, b_ref, x_ref, _ = cfg1_solution
+def test_flexible_cg_matches_pcg_gpu(cmm, ctx, tiny_solution):
+    scan, noise, d, b_ref, x_ref, _ = tiny_solution
     op = cmm.Operator(ctx, scan, noise, precision=0)
     pc = cmm.Precon(op, cmm.PRECON_BINNED)
     b = dev(b_ref)
@@ -423,7 +423,7 @@ def test_flexible_cg_matches_pcg_gpu(cmm, ctx, cfg1_solution):
     assert rel(host(x1), x_ref) < 1e-6
 
 
-# ---------------------------------------------------------------- batched solves and tuning (config 4)
+# ---------------------------------------------------------------- batched solves and tuning (uneven problems)
 
 def test_batch_solve_matches_individual_solves(cmm):
     """Uneven problems solved together in one graph per check interval give the same
@@ -470,7 +470,7 @@ def test_batch_solve_matches_individual_solves(cmm):
 
 
 def test_autotune_keeps_parity(cmm, ctx, tmp_path):
-    scan, noise = gen.config1()
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=1)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
@@ -503,8 +503,8 @@ def test_tiled_circulant_matches_oracle(cmm, ctx, prec):
     assert rel(host(one.apply(dev(r))), host(circ.apply(dev(r)))) < 1e-12
 
 
-def test_tiled_circulant_pcg_config1(cmm, ctx):
-    scan, noise = gen.config1()
+def test_tiled_circulant_pcg_tiny_patch(cmm, ctx):
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=0)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=332)

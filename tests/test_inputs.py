@@ -3,7 +3,7 @@ finite-acceleration turnarounds and the batched-workload problem draws."""
 import numpy as np
 
 import gen
-from gen.inputs import CONFIG4_MAPS, rng, sweep_offsets
+from gen.inputs import UNEVEN_MAP_SIZES, rng, sweep_offsets
 
 F = 400.0
 
@@ -40,13 +40,13 @@ def test_sweep_large_acceleration_approaches_triangle():
     assert np.abs(fast - tri).max() < 1e-3
 
 
-def test_config4_draws():
+def test_uneven_problem_draws():
     seen = set()
     for k in range(64):
         g = rng(4, k, "misc")
         nd = int(g.choice([128, 256, 512, 1024]))
         nt = int(g.choice([1 << 18, 1 << 19, 1 << 20]))
-        m = CONFIG4_MAPS[int(g.integers(len(CONFIG4_MAPS)))]
+        m = UNEVEN_MAP_SIZES[int(g.integers(len(UNEVEN_MAP_SIZES)))]
         seen.add((nd, nt, m))
         for n in m:   # 5-smooth map sides for the mixed-radix map FFT
             for p in (2, 3, 5):
@@ -54,6 +54,6 @@ def test_config4_draws():
                     n //= p
             assert n == 1
     assert len(seen) > 20
-    scan, noise = gen.config4(1)
+    scan, noise = gen.uneven_problem(1)
     assert (scan.n_det, scan.n_t) == (128, 1 << 18) and (scan.ny, scan.nx) == (450, 600)
     assert np.all(noise.sigma == 1.0) and np.all(noise.fknee == 2.0)

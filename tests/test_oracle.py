@@ -121,7 +121,7 @@ def test_pointing_is_nearest_pixel_of_exact_position():
 
 
 def test_polarisation_angle_is_psi_plus_phi():
-    scan, _ = gen.config1()
+    scan, _ = gen.tiny_patch()
     dets = np.arange(4)
     w = om.sample_weights(scan, dets)
     phi = np.arctan2(scan.bore[:, 3].astype(float), scan.bore[:, 2].astype(float))

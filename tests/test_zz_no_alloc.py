@@ -63,8 +63,8 @@ def test_noalloc_matches_apply_A_on_consecutive_calls(cmm, ctx, prec):
             assert rel(out, ref) < TOL[prec]
 
 
-def test_noalloc_config1(cmm, ctx):
-    scan, noise = gen.config1()
+def test_noalloc_tiny_patch(cmm, ctx):
+    scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=1)
     m = maps(scan, 305)
     ref = op.apply(m)
