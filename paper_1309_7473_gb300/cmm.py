@@ -511,6 +511,11 @@ class Operator:
 
 
 class Precon:
+    """A preconditioner of an operator: PRECON_BINNED / _JACOBI (per-pixel blocks),
+    _CIRCULANT (taper_sigma_px, ref_pixel, pd_eps), _CIRC_TILED (tiles = (ty, tx));
+    white_diag weights the detectors by 1/sigma^2 instead of the exact diagonal of
+    N^-1 (binned and circulant kinds)."""
+
     def __init__(self, op: Operator, kind, taper_sigma_px=0.0, ref_pixel=-1, pd_eps=0.0, tiles=(0, 0),
                  white_diag=False):
         self.op = op
@@ -567,7 +572,9 @@ class UNet:
 
 def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=10, use_graph=True,
           history=False, cg_f32=False, resid_replace=0, flexible=False, true_resid=True):
-    """PCG on A x = b; returns (x, info, resid_hist, anorm_terms)."""
+    """PCG on A x = b; returns (x, info, resid_hist, anorm_terms).  info.rel_resid is
+    the recursive ||r|| / ||b||; info.true_rel_resid recomputes ||b - A x|| / ||b||
+    from the returned x (one more application of A; -1 with true_resid=False)."""
     import torch
     x0_given = x is not None
     x = op.new_map() if x is None else x
