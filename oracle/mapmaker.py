@@ -28,7 +28,8 @@ R8  the regularising Gaussian (Sec. Regularization) is g(k) = exp(-|k|^2 / (2 s^
 R9  the reference pixel is (ny // 2, nx // 2), else the nearest unmasked pixel
     (ties: smallest linear index).
 R10 pointing is the integer fixed-point rule below; polarisation angle on the sky
-    is psi_d + phi_t.
+    is psi_d + phi_t, phi_t the angle of the fixed-point rotation pair (the pair
+    normalised for the response; positions use the integer pair as it is).
 R11 PCG starts from x0 = 0 and stops when ||r_k|| / ||b|| <= tol.
 R12 the A-norm error estimate of the Results footnote estimates the SQUARE of
     the error A-norm: ||x_i - x||_A^2 ~ sum_{j=i}^{i+d-1} alpha_j r_j^T z_j.
@@ -87,14 +88,20 @@ def sample_pixels(scan, dets):
 
 def sample_weights(scan, dets):
     """Rows of P: (1,) for T-only maps, (1, cos 2a, sin 2a) with a = psi_d + phi_t for
-    TQU maps (Sec. Test setup), by angle addition from the tabulated cos/sin."""
+    TQU maps (Sec. Test setup), by angle addition from the tabulated cos/sin.
+
+    phi_t is the angle of the fixed-point pair (cphi, sphi), whose length differs
+    from one by the table's rounding (up to ~2^-16): the double angle is therefore
+    formed from the normalised pair, cos 2phi = (c^2 - s^2) / (c^2 + s^2) and
+    sin 2phi = 2 c s / (c^2 + s^2) (R10), so the row is the paper's unit response."""
     nd = len(np.atleast_1d(dets))
     if scan.ncomp == 1:
         return np.ones((1, nd, scan.n_t))
     cf = scan.bore[:, 2].astype(np.float64) * 2.0 ** -15
     sf = scan.bore[:, 3].astype(np.float64) * 2.0 ** -15
-    c2f = cf * cf - sf * sf
-    s2f = 2.0 * cf * sf
+    r2 = cf * cf + sf * sf
+    c2f = (cf * cf - sf * sf) / r2
+    s2f = 2.0 * cf * sf / r2
     c2p = scan.det_pol[dets, 0][:, None]
     s2p = scan.det_pol[dets, 1][:, None]
     c = c2p * c2f[None, :] - s2p * s2f[None, :]

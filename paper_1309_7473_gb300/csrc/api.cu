@@ -73,12 +73,15 @@ __global__ void k_noise_diag(const double4_32a* __restrict__ coef, long long n_t
   if (threadIdx.x == 0) out[d] = sh[0] / (double)n_t;
 }
 
-// (cos 2phi, sin 2phi) per sample from the 2^-15 fixed-point rotation, in FP64, stored in FP32.
+// (cos 2phi, sin 2phi) per sample, phi the angle of the 2^-15 fixed-point rotation
+// pair (c, s): the double angle of the normalised pair, (c^2 - s^2, 2 c s) / (c^2 + s^2),
+// in FP64 (the integer products are exact), stored in FP32.
 __global__ void k_rot2(const int4* __restrict__ bore, long long n, float2* __restrict__ out) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int4 b = bore[t];
-    const double cf = (double)b.z * 0x1p-15, sf = (double)b.w * 0x1p-15;
-    out[t] = make_float2((float)(cf * cf - sf * sf), (float)(2.0 * cf * sf));
+    const double cf = (double)b.z, sf = (double)b.w;
+    const double r2 = cf * cf + sf * sf;
+    out[t] = make_float2((float)((cf * cf - sf * sf) / r2), (float)(2.0 * cf * sf / r2));
   }
 }
 

@@ -33,13 +33,15 @@ __device__ __forceinline__ int sample_pixel(const int4 b, const int2 o, int ny, 
   return iy * nx + ix;
 }
 
-// Response (cos 2a, sin 2a), a = psi_d + phi_t, by angle addition.
+// Response (cos 2a, sin 2a), a = psi_d + phi_t, by angle addition; phi_t is the angle
+// of the fixed-point rotation pair (c, s), whose double angle is (c^2 - s^2, 2 c s)
+// over c^2 + s^2 (the pair's length differs from one by its rounding).
 template <typename T>
 __device__ __forceinline__ void sample_response(const int4 b, const V2<T> pol, T& c, T& s) {
-  const T q = (T)3.0517578125e-05;  // 2^-15
-  const T cf = (T)b.z * q, sf = (T)b.w * q;
-  const T c2 = cf * cf - sf * sf;
-  const T s2 = (T)2 * cf * sf;
+  const T cf = (T)b.z, sf = (T)b.w;
+  const T r2 = cf * cf + sf * sf;
+  const T c2 = (cf * cf - sf * sf) / r2;
+  const T s2 = (T)2 * cf * sf / r2;
   c = pol.x * c2 - pol.y * s2;
   s = pol.y * c2 + pol.x * s2;
 }

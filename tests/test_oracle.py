@@ -127,10 +127,14 @@ def test_polarisation_angle_is_psi_plus_phi():
     phi = np.arctan2(scan.bore[:, 3].astype(float), scan.bore[:, 2].astype(float))
     psi = 0.5 * np.arctan2(scan.det_pol[dets, 1], scan.det_pol[dets, 0])
     ang = 2 * (psi[:, None] + phi[None, :])
-    r2 = (scan.bore[:, 2].astype(float) ** 2 + scan.bore[:, 3].astype(float) ** 2) / 2.0 ** 30
     np.testing.assert_allclose(w[0], 1.0)
-    np.testing.assert_allclose(w[1], np.cos(ang) * r2, atol=1e-12)
-    np.testing.assert_allclose(w[2], np.sin(ang) * r2, atol=1e-12)
+    np.testing.assert_allclose(w[1], np.cos(ang), atol=1e-13)
+    np.testing.assert_allclose(w[2], np.sin(ang), atol=1e-13)
+    # the response row is the paper's unit row (1, cos 2a, sin 2a), although the
+    # fixed-point rotation pairs are not exactly of unit length
+    np.testing.assert_allclose(w[1] ** 2 + w[2] ** 2, 1.0, atol=1e-14)
+    r2 = (scan.bore[:, 2].astype(float) ** 2 + scan.bore[:, 3].astype(float) ** 2) / 2.0 ** 30
+    assert np.abs(r2 - 1.0).max() > 1e-6
 
 
 # ---------------------------------------------------------------------------
