@@ -46,9 +46,10 @@ def parse():
                     help="Gaussian taper of the circulant preconditioner in pixels (10: best of the sweep "
                          "{5, 10, 20, 40, inf} on this scan; the paper's ACT value 20 is solved beside it)")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-6 solves")
-    ap.add_argument("--pointing", choices=["cached", "on-the-fly"], default="cached",
-                    help="cached: pixel index per sample stored once (4 B/sample); on-the-fly: recomputed "
-                         "in both column passes of every application")
+    ap.add_argument("--pointing", choices=["cached", "on-the-fly"], default="on-the-fly",
+                    help="on-the-fly: pixels recomputed from the boresight and detector offsets in both "
+                         "column passes of every application (the method's pointing, no stored P); cached: "
+                         "a pixel index per sample stored once (4 B/sample), timed beside it")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--corr-modes", type=int, default=0,
                     help="noise correlated between detectors: r focal-plane modes (common, x, y gradient)")
@@ -135,20 +136,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_rate(args, seconds, rank=0):
-    """Samples/s of the FP64 CPU oracle's A-application on a bounded sample of the
-    workload (the first few detectors of the same scan)."""
+ORACLE_DETS = 4   # detectors per worker's sample
+
+
+def _oracle_worker(job):
+    """One host core: the FP64 oracle's A-application on its own ORACLE_DETS
+    detectors of the workload, repeated for `seconds` after one untimed warm-up.
+    Returns (samples processed, seconds)."""
+    n_det, n_t, rank, first, seconds = job
     import numpy as np
 
     import gen
     from oracle import mapmaker as om
-    scan, noise = gen.act_patch(real=rank, n_det=args.n_det, n_t=args.n_t)
-    n_sub = 4
-    sub = scan.subset(np.arange(n_sub))
-    nsub = noise.subset(np.arange(n_sub))
-    mask = om.pixel_mask(sub)
-    op = om.make_operator(sub, nsub, mask)
+    scan, noise = gen.act_patch(real=rank, n_det=n_det, n_t=n_t)
+    dets = (first + np.arange(ORACLE_DETS)) % scan.n_det
+    sub, nsub = scan.subset(dets), noise.subset(dets)
+    op = om.make_operator(sub, nsub, om.pixel_mask(sub))
     m = gen.sky_map(scan.ny, scan.nx, cfg=2, real=rank)
+    om.apply_A(op, m)
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -157,10 +162,60 @@ def oracle_rate(args, seconds, rank=0):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    rate = reps * n_sub * scan.n_t / el
-    sample = (f"{reps} oracle A-applications of {n_sub} of {scan.n_det} detectors "
-              f"({n_sub * scan.n_t} samples each) in {el:.1f} s")
-    return rate, sample
+    return reps * ORACLE_DETS * scan.n_t, el
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+class OraclePool:
+    """Worker processes for the oracle timing, one per host core, started with the
+    spawn method (no fork of a process that holds a CUDA context).  Each worker
+    runs the plain oracle on a disjoint set of detectors; numpy's threads are
+    limited to one per worker."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores, self.model = host_cpu()
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def rate(self, args, seconds, rank=0):
+        jobs = [(args.n_det, args.n_t, rank, k * ORACLE_DETS, seconds) for k in range(self.cores)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+        samples = sum(r[0] for r in res)
+        span = max(r[1] for r in res)
+        rate = samples / span
+        sample = (f"{self.cores} processes x FP64 oracle A-applications of {ORACLE_DETS} of {args.n_det} "
+                  f"detectors ({ORACLE_DETS * args.n_t} samples each), {samples / (ORACLE_DETS * args.n_t):.0f} "
+                  f"applications in {span:.1f} s ({wall:.1f} s with set-up)")
+        return rate, sample
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def baseline(self, rate, sample):
+        return {"value": rate, "unit": UNIT, "cores": self.cores, "kind": "oracle", "sample": sample,
+                "nproc": self.cores, "cpu_model": self.model}
 
 
 def job_ms(ms, world, device):
@@ -244,15 +299,18 @@ def run_ours(args, rank, world):
     ms_step = ms / args.steps
     value = job_value(n_s, args.steps, ms, world)
 
-    # per-pass durations of the A-application (CUDA events between its kernels)
+    # per-pass durations of the A-application (CUDA events between its kernels),
+    # and the same with the other pointing mode beside it
     with torch.cuda.stream(stream):
         mo = op.new_map()
         prof = cmm.cmm_profile_apply(op.h, b, mo, 5)
-        prof_otf = None
-        if args.pointing == "cached" and prec != cmm.PREC_F64:
-            op.set_pixel_cache(False)
-            prof_otf = cmm.cmm_profile_apply(op.h, b, mo, 3)
-            op.set_pixel_cache(True)
+        prof_other = None
+        if prec != cmm.PREC_F64:
+            cached = args.pointing == "cached"
+            op.set_pixel_cache(not cached)
+            prof_other = cmm.cmm_profile_apply(op.h, b, mo, 3)
+            op.set_pixel_cache(cached)
+            torch.cuda.empty_cache()
     fast = args.prec != "f64" and (1 << 13) <= scan.n_t <= (1 << 20)   # the register-FFT kernels
     pre = "k_fast_" if fast else "k_tod_"
     names = [pre + "fwd (pointing + gather + column FFTs)", pre + "filter (row FFTs + N^-1)",
@@ -272,18 +330,25 @@ def run_ours(args, rank, world):
 
     cufft = cufft_filter_ms(scan, noise, dev, stream) if args.prec == "f32" else None
 
-    # end to end through the host-buffer entry point: H2D map, A, D2H map per step
-    m_host = torch.empty((3, scan.ny, scan.nx), dtype=torch.float64).pin_memory()
-    m_host.copy_(m_sky.cpu())
-    out_host = torch.empty_like(m_host).pin_memory()
-    mi, mo_np = m_host.numpy(), out_host.numpy()
-    cmm.cmm_apply_A_host(op.h, mi, mo_np)
-    t0 = time.perf_counter()
-    n_e2e = max(3, args.steps // 2)
-    for _ in range(n_e2e):
-        cmm.cmm_apply_A_host(op.h, mi, mo_np)
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+    # end to end through the host-buffer solve (cmm_solve_host): the same steps as
+    # `value` (K circulant-PCG iterations) with b copied in from pinned host memory
+    # and the iterate x copied back, host wall clock around the call
+    b_host = torch.empty((3, scan.ny, scan.nx), dtype=torch.float64).pin_memory()
+    b_host.copy_(b.cpu())
+    x_host = torch.zeros_like(b_host).pin_memory()
+    bh, xh = b_host.numpy(), x_host.numpy()
     map_bytes = 3 * scan.npix * 8
+    with torch.cuda.stream(stream):
+        cmm.cmm_solve_host(op.h, pc.h, bh, xh, tol=0.0, maxit=args.warmup, check_every=args.warmup,
+                           true_resid=False)
+        t0 = time.perf_counter()
+        cmm.cmm_solve_host(op.h, pc.h, bh, xh, tol=0.0, maxit=args.steps, check_every=args.steps,
+                           true_resid=False)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        # and a whole solve to 1e-6 from host b to host x (preconditioner already built)
+        t0 = time.perf_counter()
+        info_e2e = cmm.cmm_solve_host(op.h, pc.h, bh, xh, tol=1e-6, maxit=2000, check_every=10)
+        e2e_solve_s = time.perf_counter() - t0
 
     solves = None
     if not args.no_solve:
@@ -324,10 +389,20 @@ def run_ours(args, rank, world):
         "apply": {"ms": prof[4], "samples_per_s": n_s / (prof[4] / 1e3), "algorithmic_GBps": apply_gbs,
                   "frac_of_measured_hbm": apply_gbs / peak,
                   "ms_per_pass": {"fwd": prof[0], "filter": prof[1], "inv_bin": prof[2], "map_copies": prof[3]},
-                  "det_chunk": chunk_dets,
-                  "on_the_fly_pointing_ms": None if prof_otf is None else prof_otf[4]},
-        "e2e": {"value": n_s / e2e_s, "unit": UNIT, "h2d_bytes_per_step": map_bytes, "d2h_bytes_per_step": map_bytes,
-                "step": "cmm_apply_A_host: H2D map, A, D2H map"},
+                  "det_chunk": chunk_dets, "pointing": args.pointing,
+                  ("cached_pointing_ms" if args.pointing != "cached" else "on_the_fly_pointing_ms"):
+                      None if prof_other is None else prof_other[4],
+                  ("cached_pointing_ms_per_pass" if args.pointing != "cached" else "on_the_fly_ms_per_pass"):
+                      None if prof_other is None else {"fwd": prof_other[0], "filter": prof_other[1],
+                                                       "inv_bin": prof_other[2]}},
+        "e2e": {"value": n_s / e2e_s, "unit": UNIT, "h2d_bytes_per_step": map_bytes / args.steps,
+                "d2h_bytes_per_step": map_bytes / args.steps, "ms_per_step": 1e3 * e2e_s,
+                "step": f"cmm_solve_host: b H2D from pinned host memory, {args.steps} circulant-PCG iterations "
+                        "(the timed steps of value), x D2H; host wall clock; copies per call over the steps",
+                "solve_to_1e-6": {"seconds": round(e2e_solve_s, 4), "iterations": info_e2e.iterations,
+                                  "status": cmm.STATUS[info_e2e.status],
+                                  "what": "cmm_solve_host from host b to host x, circulant preconditioner "
+                                          "built beforehand, exit residual check included"}},
         "solves_to_1e-6": solves,
         "cufft_comparison": cufft,
         "setup_seconds": round(setup_s, 2),
@@ -688,16 +763,16 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        cores = 1
+        pool = OraclePool()
         rates = []
         t_all = time.perf_counter()
         per = max(1.0, args.cpu_seconds / max(1, args.steps))
-        for _ in range(args.warmup):
-            oracle_rate(args, 0.1)
+        pool.rate(args, 0.1)   # warm-up: workers start, import and build their operators
         sample = ""
         for _ in range(args.steps):
-            r, sample = oracle_rate(args, per)
+            r, sample = pool.rate(args, per)
             rates.append(r)
+        pool.close()
         value = statistics.mean(rates)
         el = time.perf_counter() - t_all
         print(json.dumps({
@@ -705,7 +780,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": pool.baseline(value, f"{args.steps} steps of: {sample}"),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return 0
     if args.workload == "learned":
@@ -724,13 +799,16 @@ def main():
         if rank == 0:
             print(json.dumps(run_spectra(args)))
         return 0
+    # the oracle's worker processes start before this process touches the GPU
+    pool = OraclePool() if rank == 0 and world == 1 else None
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
-    if rank == 0:
-        rate, sample = oracle_rate(args, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if pool is not None:
+        rate, sample = pool.rate(args, args.cpu_seconds)
+        pool.close()
+        out["cpu_baseline"] = pool.baseline(rate, sample)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -106,12 +106,15 @@ typedef struct {
   int32_t snapshot_max;   /* number of snapshot slots */
   int32_t batch_width;    /* cmm_batch_solve: concurrent lanes (<= 0: automatic) */
   int32_t skip_true_resid; /* != 0: no exit check of ||b - A x|| (true_rel_resid = -1) */
+  int32_t resume;      /* != 0: continue from the state of cmm_solve_state_load; x holds that
+                          state's iterate x_k, the count goes on from k (maxit counts from 0) */
 } cmm_solve_opts;
 
 typedef struct {
   int32_t iterations;   /* A-applications inside the loop */
-  int32_t status;       /* CMM_OK, CMM_ERR_NOT_CONVERGED or CMM_ERR_BREAKDOWN */
-  double rel_resid;     /* last recursive ||r|| / ||b|| */
+  int32_t status;       /* CMM_OK, CMM_ERR_NOT_CONVERGED or CMM_ERR_BREAKDOWN (p^T A p <= 0,
+                           r^T z <= 0, or a non-finite value in b, x0 or a CG scalar) */
+  double rel_resid;     /* last recursive ||r|| / ||b|| (-1 when b is not finite) */
   double seconds;       /* wall time of the call */
   double true_rel_resid; /* ||b - A x|| / ||b|| recomputed from the returned x at exit
                             (one more A-application, inside `seconds`); -1 when
@@ -298,6 +301,30 @@ int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped);
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x,
               const cmm_solve_opts* opts, double* resid_hist, double* anorm_terms,
               double* snapshots, cmm_solve_info* info);
+
+/* cmm_solve from host memory: b_host (and x_host when opts->x0_given or
+ * opts->resume) are copied to device buffers of the operator (allocated on the
+ * first call), the solve runs as cmm_solve without history or snapshots, and the
+ * solution is copied back to x_host; waits.  b_host, x_host: host double
+ * [ncomp][ny][nx] (pinned memory makes the copies asynchronous). */
+int cmm_solve_host(cmm_op* op, cmm_precon* pc, const double* b_host, double* x_host,
+                   const cmm_solve_opts* opts, cmm_solve_info* info);
+
+/* Checkpoint and resume of a solve.  The paper writes intermediate maps every 5
+ * steps (Sec. Test setup); a checkpoint here keeps the whole PCG state, so that a
+ * solve stopped after k iterations (maxit reached) and resumed continues the same
+ * iterates as one that was never stopped (FP64 mode: equal to the rounding of the
+ * operator's atomic sums).  The caller keeps x_k (the stopped solve's x).
+ * state: device double [*n_doubles] = (r_k, p_{k-1}, r_{k-1}) of ncomp*ny*nx each,
+ * then rho_{k-1}, k, ||r_k|| / ||b||, the FP32-CG flag and a format tag; it may go
+ * through host memory and another process.  cmm_solve_state_save copies the state
+ * of this operator's last cmm_solve (CMM_ERR_ARG if there is none or it broke
+ * down) and waits; cmm_solve_state_load makes it the state that the next
+ * cmm_solve with opts->resume continues (CMM_ERR_ARG if the buffer is not a saved
+ * state), and waits.  Resume with the same b, preconditioner and CG mode. */
+int cmm_solve_state_size(cmm_op* op, int64_t* n_doubles);
+int cmm_solve_state_save(cmm_op* op, double* state);
+int cmm_solve_state_load(cmm_op* op, const double* state);
 
 /* ---------------------------------------------------------------- learned correction
  * A U-Net (no counterpart in the paper) that refines the circulant preconditioner

@@ -45,7 +45,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
                 ("resid_replace", C.c_int32), ("flexible", C.c_int32), ("snapshot_every", C.c_int32),
-                ("snapshot_max", C.c_int32), ("batch_width", C.c_int32), ("skip_true_resid", C.c_int32)]
+                ("snapshot_max", C.c_int32), ("batch_width", C.c_int32), ("skip_true_resid", C.c_int32),
+                ("resume", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -87,6 +88,10 @@ _SIGS = {
     "cmm_precon_apply": [_vp, _vp, _vp],
     "cmm_precon_clamped": [_vp, C.POINTER(_i64)],
     "cmm_solve": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), _vp, _vp, _vp, C.POINTER(SolveInfo)],
+    "cmm_solve_host": [_vp, _vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)],
+    "cmm_solve_state_size": [_vp, C.POINTER(_i64)],
+    "cmm_solve_state_save": [_vp, _vp],
+    "cmm_solve_state_load": [_vp, _vp],
     "cmm_precon_set_correction": [_vp, _vp],
     "cmm_harvest_pairs": [_vp, _vp, _i32, _vp, _vp, _vp],
     "cmm_unet_create": [_vp, _i32, _i32, _i32, _vp, _i32, _PP],
@@ -316,17 +321,47 @@ def cmm_precon_clamped(pc):
 
 def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
               resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False,
-              snapshots=None, snapshot_every=1, true_resid=True):
+              snapshots=None, snapshot_every=1, true_resid=True, resume=False):
     snap_max = 0 if snapshots is None else snapshots.shape[0]
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0,
                      1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0, int(snapshot_every),
-                     int(snap_max), 0, 0 if true_resid else 1)
+                     int(snap_max), 0, 0 if true_resid else 1, 1 if resume else 0)
     info = SolveInfo()
     _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
                           _dev(resid_hist, numel=None, name="resid_hist"),
                           _dev(anorm_terms, numel=None, name="anorm_terms"),
                           _dev(snapshots, name="snapshots"), C.byref(info)))
     return info
+
+
+def cmm_solve_host(op, pc, b_host, x_host, tol=1e-6, maxit=500, check_every=10, x0_given=False,
+                   true_resid=True, resume=False):
+    """cmm_solve on host float64 arrays (numpy, or pinned CPU torch tensors via .numpy())."""
+    import numpy as np
+    for name, a in (("b", b_host), ("x", x_host)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
+    opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 1 if x0_given else 0, 0, 0, 0, 0, 0, 0,
+                     0 if true_resid else 1, 1 if resume else 0)
+    info = SolveInfo()
+    _check(_lib.cmm_solve_host(op, pc, b_host.ctypes.data, x_host.ctypes.data, C.byref(opts), C.byref(info)))
+    return info
+
+
+def cmm_solve_state_size(op):
+    n = C.c_int64()
+    _check(_lib.cmm_solve_state_size(op, C.byref(n)))
+    return int(n.value)
+
+
+def cmm_solve_state_save(op, state):
+    import torch
+    _check(_lib.cmm_solve_state_save(op, _dev(state, torch.float64, name="state")))
+
+
+def cmm_solve_state_load(op, state):
+    import torch
+    _check(_lib.cmm_solve_state_load(op, _dev(state, torch.float64, name="state")))
 
 
 def cmm_harvest_pairs(pc, snapshots, count, x_star, inputs, targets):
@@ -400,7 +435,7 @@ def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f3
     n = len(ops)
     arr = lambda items: (C.c_void_p * n)(*[C.c_void_p(v if isinstance(v, int) else v.value) for v in items])
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0,
-                     0, 0, int(width), 0 if true_resid else 1)
+                     0, 0, int(width), 0 if true_resid else 1, 0)
     infos = (SolveInfo * n)()
     _check(_lib.cmm_batch_solve(n, arr(ops), arr(pcs), arr([t.data_ptr() for t in bs]),
                                 arr([t.data_ptr() for t in xs]), C.byref(opts), infos))

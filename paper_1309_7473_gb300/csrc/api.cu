@@ -399,6 +399,7 @@ static void free_op(cmm_op* op) {
   dfree(op->corr_s);
   dfree(op->sol);
   dfree(op->sol_state);
+  dfree(op->host_bx);
   cmm_ctx* c = op->ctx;
   cmm_pointing* pt = op->pt;
   cmm_noise* nz = op->nz;
@@ -1087,11 +1088,12 @@ struct SolveBufs {
 };
 
 // ||b - A x|| / ||b|| recomputed from x (one A-application), in the op's CG
-// scratch (q and r_old slots); the check the recursive residual is compared with.
+// scratch (q and z slots: r, p and r_old stay as the solve left them, for a
+// checkpoint); the check the recursive residual is compared with.
 static int true_residual(cmm_op* op, const double* b, const double* x, double bnorm2, double* out) {
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   double* q = op->sol + 3 * n;
-  double* r = op->sol + 4 * n;
+  double* r = op->sol + n;
   CMM_TRY(apply_A_dev(op, x, q));
   CMM_TRY(launch_sub(r, b, q, n, op->ctx->stream));
   double rr = 0.0;
@@ -1130,6 +1132,60 @@ static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBuf
   return CMM_OK;
 }
 
+// ------------------------------------------------------------------ checkpoint / resume
+// State layout (doubles): r_k [n], p_{k-1} [n], r_{k-1} [n], then kStateScalars
+// scalars: rho_{k-1}, k, ||r_k|| / ||b||, FP32-CG flag, a format tag.
+constexpr int kStateScalars = 8;
+constexpr double kStateTag = 1309.7473;
+
+int cmm_solve_state_size(cmm_op* op, int64_t* n_doubles) {
+  if (!op || !n_doubles) return fail(CMM_ERR_ARG, "null argument");
+  *n_doubles = 3 * (int64_t)op->pt->ncomp * op->pt->npix + kStateScalars;
+  return CMM_OK;
+}
+
+int cmm_solve_state_save(cmm_op* op, double* state) {
+  if (!op || !state) return fail(CMM_ERR_ARG, "null argument");
+  if (!op->sol || !op->sol_state) return fail(CMM_ERR_ARG, "the operator has no solve to save");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  SolverDev h{};
+  CMM_CUDA(cudaMemcpyAsync(&h, op->sol_state, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CMM_CUDA(cudaStreamSynchronize(st));
+  if (h.status == CMM_ERR_BREAKDOWN) return fail(CMM_ERR_ARG, "the last solve broke down: nothing to resume");
+  CMM_CUDA(cudaMemcpyAsync(state, op->sol, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));              // r
+  CMM_CUDA(cudaMemcpyAsync(state + n, op->sol + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));  // p
+  CMM_CUDA(cudaMemcpyAsync(state + 2 * n, op->sol + 4 * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));  // r_old
+  const double sc[kStateScalars] = {h.rho, (double)h.iter, h.rel, (double)h.f32, kStateTag, 0, 0, 0};
+  CMM_CUDA(cudaMemcpyAsync(state + 3 * n, sc, sizeof(sc), cudaMemcpyHostToDevice, st));
+  CMM_CUDA(cudaStreamSynchronize(st));
+  return CMM_OK;
+}
+
+int cmm_solve_state_load(cmm_op* op, const double* state) {
+  if (!op || !state) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  cudaStream_t st = op->ctx->stream;
+  double sc[kStateScalars];
+  CMM_CUDA(cudaMemcpyAsync(sc, state + 3 * n, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  CMM_CUDA(cudaStreamSynchronize(st));
+  if (sc[4] != kStateTag || !(sc[1] >= 0) || !std::isfinite(sc[0]))
+    return fail(CMM_ERR_ARG, "not a solver state of cmm_solve_state_save");
+  if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (5 * n + 3 * kRedBlocks)));
+  if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
+  CMM_CUDA(cudaMemcpyAsync(op->sol, state, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CMM_CUDA(cudaMemcpyAsync(op->sol + 2 * n, state + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CMM_CUDA(cudaMemcpyAsync(op->sol + 4 * n, state + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  op->resume_rho = sc[0];
+  op->resume_iter = (int)sc[1];
+  op->resume_rel = sc[2];
+  op->resume_ready = 1;
+  CMM_CUDA(cudaStreamSynchronize(st));
+  return CMM_OK;
+}
+
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_solve_opts* opts,
               double* resid_hist, double* anorm_terms, double* snapshots, cmm_solve_info* info) {
   if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
@@ -1144,6 +1200,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   }
   if (pc->op != op) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
   if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace < 0) return fail(CMM_ERR_ARG, "bad solve options");
+  if (opts->resume && !op->resume_ready) return fail(CMM_ERR_ARG, "resume without a loaded solver state");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   const auto t0 = std::chrono::steady_clock::now();
   cmm_ctx* c = op->ctx;
@@ -1169,6 +1226,29 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   h.tol = opts->tol;
   h.maxit = opts->maxit;
   h.f32 = opts->cg_f32 ? 1 : 0;
+  if (!std::isfinite(bnorm2)) {
+    // a non-finite right-hand side: no iteration is meaningful
+    h.done = 1;
+    h.status = CMM_ERR_BREAKDOWN;
+    CMM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    CMM_CUDA(cudaStreamSynchronize(st));
+    op->resume_ready = 0;
+    info->iterations = 0;
+    info->status = CMM_ERR_BREAKDOWN;
+    info->rel_resid = -1.0;
+    info->true_rel_resid = -1.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return CMM_OK;
+  }
+  const bool resume = opts->resume != 0;
+  if (resume) {
+    h.rho = op->resume_rho;
+    h.iter = op->resume_iter;
+    h.rel = op->resume_rel;
+    h.status = CMM_ERR_NOT_CONVERGED;
+    h.done = h.iter >= h.maxit ? 1 : 0;
+    op->resume_ready = 0;
+  }
   CMM_CUDA(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   if (!(bnorm2 > 0)) {
     CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
@@ -1180,19 +1260,28 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     info->seconds = 0.0;
     return CMM_OK;
   }
-  // r0 = b - A x0 (rounded in FP32 CG), z0 = M r0, p0 = z0
-  if (opts->x0_given) {
-    CMM_TRY(apply_A_dev(op, x, v.q));
+  if (resume) {
+    // continue from the loaded state (r_k, p_{k-1}, r_{k-1}, rho_{k-1}, k) and the
+    // caller's x_k: the tail of iteration k that the interrupted solve skipped,
+    // z_k = M r_k, beta, p_k = z_k + beta p_{k-1}
+    CMM_TRY(precon_step(op, pc, v, dst, flexible));
+    CMM_TRY(launch_solver_beta(dst, v.p1, flexible ? v.p3 : nullptr, st));
+    CMM_TRY(launch_update_p(v.p, v.z, n, dst, st));
   } else {
-    CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    CMM_CUDA(cudaMemsetAsync(v.q, 0, sizeof(double) * n, st));
+    // r0 = b - A x0 (rounded in FP32 CG), z0 = M r0, p0 = z0
+    if (opts->x0_given) {
+      CMM_TRY(apply_A_dev(op, x, v.q));
+    } else {
+      CMM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+      CMM_CUDA(cudaMemsetAsync(v.q, 0, sizeof(double) * n, st));
+    }
+    CMM_TRY(launch_residual(v.r, b, v.q, n, dst, v.p2, st));
+    CMM_CUDA(cudaMemcpyAsync(v.r_old, v.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    CMM_TRY(precon_step(op, pc, v, dst, false));
+    CMM_TRY(launch_solver_init(dst, v.p1, v.p2, resid_hist, st));
+    if (snap.buf) CMM_TRY(launch_snapshot(x, v.r, n, dst, snap.every, snap.max, snap.buf, st));
+    CMM_CUDA(cudaMemcpyAsync(v.p, v.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   }
-  CMM_TRY(launch_residual(v.r, b, v.q, n, dst, v.p2, st));
-  CMM_CUDA(cudaMemcpyAsync(v.r_old, v.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  CMM_TRY(precon_step(op, pc, v, dst, false));
-  CMM_TRY(launch_solver_init(dst, v.p1, v.p2, resid_hist, st));
-  if (snap.buf) CMM_TRY(launch_snapshot(x, v.r, n, dst, snap.every, snap.max, snap.buf, st));
-  CMM_CUDA(cudaMemcpyAsync(v.p, v.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   int per = std::max(1, opts->check_every);
   if (opts->resid_replace > 0) per = std::min(per, opts->resid_replace);
   while (opts->resid_replace > 0 && opts->resid_replace % per) --per;   // per divides the replacement period
@@ -1256,6 +1345,24 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   info->true_rel_resid = -1.0;
   if (!opts->skip_true_resid) CMM_TRY(true_residual(op, b, x, h.bnorm2, &info->true_rel_resid));
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return CMM_OK;
+}
+
+int cmm_solve_host(cmm_op* op, cmm_precon* pc, const double* b_host, double* x_host, const cmm_solve_opts* opts,
+                   cmm_solve_info* info) {
+  if (!op || !pc || !b_host || !x_host || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
+  if (!op->host_bx) CMM_TRY(dalloc(&op->host_bx, sizeof(double) * 2 * n));
+  double* b = op->host_bx;
+  double* x = op->host_bx + n;
+  cudaStream_t st = op->ctx->stream;
+  CMM_CUDA(cudaMemcpyAsync(b, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (opts->x0_given || opts->resume)
+    CMM_CUDA(cudaMemcpyAsync(x, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CMM_TRY(cmm_solve(op, pc, b, x, opts, nullptr, nullptr, nullptr, info));
+  CMM_CUDA(cudaMemcpyAsync(x_host, x, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CMM_CUDA(cudaStreamSynchronize(st));
   return CMM_OK;
 }
 

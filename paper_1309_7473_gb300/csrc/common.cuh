@@ -156,8 +156,12 @@ struct cmm_op {
   double* tmp_a = nullptr;     // [ncomp*npix] device temporaries
   double* tmp_b = nullptr;
   const int* done = nullptr;   // solver stop flag seen by every kernel (nullptr: none)
-  double* sol = nullptr;       // PCG vectors r, z, p, q and reduction partials
+  double* sol = nullptr;       // PCG vectors r, z, p, q, r_old and reduction partials
   void* sol_state = nullptr;   // PCG scalars (SolverDev)
+  double* host_bx = nullptr;   // [2][ncomp*npix] device b and x of cmm_solve_host
+  int resume_ready = 0;        // a solver state was loaded (cmm_solve_state_load)
+  int resume_iter = 0;         // its iteration count, rho and relative residual
+  double resume_rho = 0.0, resume_rel = 0.0;
 };
 
 namespace cmm {

@@ -297,12 +297,14 @@ __global__ void k_solver_check(SolverDev* st, const double* __restrict__ partial
     st->rr = rr;
     st->iter += 1;
     const double rel = sqrt(rr / st->bnorm2);
-    st->rel = rel;
     if (hist) hist[st->iter] = rel;
     if (!isfinite(rr)) {
-      st->status = CMM_ERR_BREAKDOWN;
+      st->status = CMM_ERR_BREAKDOWN;   // st->rel keeps the last finite residual
       st->done = 1;
-    } else if (rel <= st->tol) {
+      return;
+    }
+    st->rel = rel;
+    if (rel <= st->tol) {
       st->status = CMM_OK;
       st->done = 1;
     } else if (st->iter >= st->maxit) {
@@ -370,14 +372,14 @@ __global__ void k_solver_init(SolverDev* st, const double* __restrict__ partial_
     st->rho = rz;
     st->iter = 0;
     const double rel = sqrt(rr / st->bnorm2);
-    st->rel = rel;
+    st->rel = isfinite(rel) ? rel : -1.0;   // -1: the starting residual is not finite
     if (hist) hist[0] = rel;
     st->done = 0;
     st->status = CMM_ERR_NOT_CONVERGED;
     if (rel <= st->tol) {
       st->status = CMM_OK;
       st->done = 1;
-    } else if (!(rz > 0.0) || !isfinite(rz)) {
+    } else if (!isfinite(rel) || !(rz > 0.0) || !isfinite(rz)) {
       st->status = CMM_ERR_BREAKDOWN;
       st->done = 1;
     } else if (st->maxit <= 0) {

@@ -23,7 +23,9 @@ def test_reference_arm_json_line():
     assert out["higher_is_better"] is True and out["value"] > 0
     assert out["steps"] == 1 and out["warmup"] == 0
     cb = out["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == out["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["sample"]
+    # the oracle runs on every host core, one worker process each, and says which CPU
+    assert cb["cores"] == cb["nproc"] == (os.cpu_count() or 1) and cb["cpu_model"]
     assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
     assert out["config"]["n_det"] == 1024 and out["config"]["n_samp"] == 1 << 20

@@ -82,3 +82,40 @@ def test_noalloc_rejects_oversize(cmm, ctx):
     out = torch.zeros_like(m)
     with pytest.raises(cmm.CmmError, match="static scratch"):
         cmm.cmm_apply_A_noalloc(op.h, m, out)
+
+
+def test_noalloc_detectors_in_several_passes(cmm, ctx):
+    """A 512x512 TQU map leaves room in the static array for the spectra of only
+    three of the eight detectors at 2^20 samples (F32): the detectors go through
+    it in passes of three, three and two, reusing the spectrum region."""
+    op, scan = operator(cmm, ctx, 1, 3, 307, 512, 512, 1 << 20)
+    assert scan.n_det == 8
+    m = maps(scan, 308)
+    ref = op.apply(m)
+    for _ in range(2):
+        out = torch.full_like(ref, float("nan"))
+        cmm.cmm_apply_A_noalloc(op.h, m, out)
+        torch.cuda.synchronize()
+        assert rel(out, ref) < TOL[1]
+
+
+def test_noalloc_bf16_storage(cmm, ctx):
+    """BF16 spectrum storage (4 bytes per complex value in the array): the same
+    numbers as cmm_apply_A up to the order of the FP32 reductions."""
+    op, scan = operator(cmm, ctx, 2, 3, 309, 64, 48, 1 << 16, chunk=2)
+    m = maps(scan, 310)
+    ref = op.apply(m)
+    for _ in range(2):
+        out = torch.zeros_like(ref)
+        cmm.cmm_apply_A_noalloc(op.h, m, out)
+        torch.cuda.synchronize()
+        assert rel(out, ref) < TOL[1]
+
+
+def test_noalloc_rejects_correlated_noise(cmm, ctx):
+    op, scan = operator(cmm, ctx, 1, 3, 311, 24, 20, 1 << 12)
+    op.noise.set_correlated(gen.corr_noise(scan.det_off, r=1))
+    m = maps(scan, 312)
+    out = torch.zeros_like(m)
+    with pytest.raises(cmm.CmmError, match="correlated"):
+        cmm.cmm_apply_A_noalloc(op.h, m, out)
