@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--corr-modes", type=int, default=0,
                     help="noise correlated between detectors: r focal-plane modes (common, x, y gradient)")
-    ap.add_argument("--workload", choices=["apply", "learned", "batch", "anorm", "spectra"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "learned", "batch", "anorm", "spectra", "unet"], default="apply",
                     help="apply: the A-application inside circulant PCG (default); learned: the learned "
                          "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
     ap.add_argument("--batch", type=int, default=64, help="solves of the batch workload")
@@ -177,6 +177,15 @@ def host_cpu():
                     break
     except OSError:
         pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     if not model:
         import platform
         model = platform.processor() or platform.machine()
@@ -472,6 +481,61 @@ def run_learned(args):
         "val_loss": {"zero_output": float(0.5 * (vt.double() ** 2).mean()), "trained": hist[-1][2]},
         "harvest_seconds": round(harvest_s, 2), "train_seconds": round(train_s, 2),
     }
+
+
+def run_unet(args):
+    """U-Net of the learned correction (widths 16/32/48/96, 64x64 TQU maps, batch 32):
+    CUDA-event time of one forward pass and of one training step (forward,
+    backward, Adam) with the 3x3 convolutions on the tensor cores (BF16 mma.sync,
+    FP32 accumulation) and on the FP32 CUDA cores, on the same weights and data."""
+    import torch
+
+    from paper_1309_7473_gb300 import build
+    build.build()
+    from paper_1309_7473_gb300 import cmm
+    widths, hw, B = (16, 32, 48, 96), 64, 32
+    ctx = cmm.Context(0)
+    net = cmm.UNet(ctx, hw, hw, widths, batch_max=B)
+    g = torch.Generator(device="cuda:0").manual_seed(0)
+    x = torch.randn((B, 3, hw, hw), device="cuda:0", generator=g)
+    t = 0.1 * torch.randn((B, 3, hw, hw), device="cuda:0", generator=g)
+    y = torch.empty_like(x)
+    # multiply-adds of the 3x3 convolutions of one forward pass (the backward pass does twice as many)
+    macs, c = 0, 3
+    for l, w in enumerate(widths):
+        px = (hw >> l) ** 2
+        macs += px * 9 * (c * w + w * w)
+        c = w
+    for l in range(len(widths) - 2, -1, -1):
+        px = (hw >> l) ** 2
+        macs += px * 9 * (2 * widths[l] * widths[l] + widths[l] * widths[l])
+    macs *= B
+    out = {"metric": "U-Net forward and training-step time (64x64 TQU, batch 32)", "unit": "ms",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16 (fp32 accumulate)",
+           "config": {"workload": "U-Net widths 16/32/48/96, 299,651 parameters, batch 32 of 3x64x64",
+                      "conv3_macs_forward": macs}}
+    reps = max(5, args.steps)
+    for name, tc in (("tensor_cores", True), ("cuda_cores", False)):
+        net.init(seed=2)
+        cmm.cmm_unet_set_tensor_cores(net.h, tc)
+        for _ in range(3):
+            cmm.cmm_unet_forward(net.h, x, y)
+            cmm.cmm_unet_train_step(net.h, x, t, 1e-4)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        for _ in range(reps):
+            cmm.cmm_unet_forward(net.h, x, y)
+        e[1].record()
+        for _ in range(reps):
+            cmm.cmm_unet_train_step(net.h, x, t, 1e-4)
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd, step = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        out[name] = {"forward_ms": fwd, "train_step_ms": step, "conv3_tflops_forward": 2 * macs / fwd / 1e9}
+    out["value"] = out["tensor_cores"]["train_step_ms"]
+    out["speedup_train_step"] = out["cuda_cores"]["train_step_ms"] / out["tensor_cores"]["train_step_ms"]
+    return out
 
 
 def cufft_filter_ms(scan, noise, dev, stream):
@@ -790,6 +854,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             print(json.dumps(run_batch(args)))
+        return 0
+    if args.workload == "unet":
+        if rank == 0:
+            print(json.dumps(run_unet(args)))
         return 0
     if args.workload == "anorm":
         if rank == 0:

@@ -342,6 +342,12 @@ int cmm_solve_state_load(cmm_op* op, const double* state);
 int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const int32_t* widths,
                     int32_t batch_max, cmm_unet** out);
 int cmm_unet_destroy(cmm_unet* net);
+/* The 3x3 convolutions (forward, input gradient, weight gradient) run as implicit
+ * GEMMs on the tensor cores (BF16 mma.sync, FP32 accumulation; the default,
+ * enable != 0) or on the FP32 CUDA cores (enable == 0, kept as a timed
+ * comparison).  On the tensor cores the FP32 gradients entering the input- and
+ * weight-gradient convolutions are rounded to BF16. */
+int cmm_unet_set_tensor_cores(cmm_unet* net, int32_t enable);
 int cmm_unet_param_count(cmm_unet* net, int64_t* n);
 /* Copies FP32 parameters (device) in, refreshes the BF16 copy, resets Adam. */
 int cmm_unet_set_params(cmm_unet* net, const float* params);

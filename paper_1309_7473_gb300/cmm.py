@@ -96,6 +96,7 @@ _SIGS = {
     "cmm_harvest_pairs": [_vp, _vp, _i32, _vp, _vp, _vp],
     "cmm_unet_create": [_vp, _i32, _i32, _i32, _vp, _i32, _PP],
     "cmm_unet_destroy": [_vp],
+    "cmm_unet_set_tensor_cores": [_vp, _i32],
     "cmm_unet_param_count": [_vp, C.POINTER(_i64)],
     "cmm_unet_set_params": [_vp, _vp],
     "cmm_unet_get_params": [_vp, _vp],
@@ -384,6 +385,10 @@ def cmm_unet_create(ctx, ny, nx, widths, batch_max):
 
 def cmm_unet_destroy(h):
     _check(_lib.cmm_unet_destroy(h))
+
+
+def cmm_unet_set_tensor_cores(h, enable=True):
+    _check(_lib.cmm_unet_set_tensor_cores(h, 1 if enable else 0))
 
 
 def cmm_unet_param_count(h):

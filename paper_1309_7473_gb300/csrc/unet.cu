@@ -103,6 +103,229 @@ __global__ void __launch_bounds__(256) k_conv3(const TIN* __restrict__ in, const
   }
 }
 
+// ------------------------------------------------------------------ tensor-core 3x3 convolution
+// The same convolutions as implicit GEMMs on the tensor cores: BF16 operands, FP32
+// accumulation, warp-level mma.sync m16n8k16 (row-major A, column-major B).
+// Fragment layout of one m16n8k16 (g = lane / 4, q = lane % 4; each .b32 register
+// holds two BF16, the lower index in the low half):
+//   A (16 x 16, M x K): a0 (row g, k 2q..2q+1), a1 (row g+8, same k),
+//                       a2 (row g, k 2q+8..2q+9), a3 (row g+8, k 2q+8..2q+9)
+//   B (16 x 8, K x N):  b0 (k 2q..2q+1, col g), b1 (k 2q+8..2q+9, col g)
+//   C (16 x 8, FP32):   c0, c1 (row g, cols 2q, 2q+1), c2, c3 (row g+8, same cols)
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// Channel stride (BF16 elements) of the staged tiles: 24 (= 12 words) puts the eight
+// row or column groups of a fragment load on distinct banks.
+constexpr int kCP = 24;
+
+template <typename T> __device__ __forceinline__ void st2(T* p, float a, float b);
+template <> __device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void st2(bf16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+
+// out = conv3(in) as k_conv3 (same FLIP convention).  GEMM: M = output channels
+// (MT x 16 per CTA), N = the CTA's pixel tile (256 / TW rows x TW columns, eight
+// n8 tiles per warp), K = input channels (16 per chunk) x 9 taps.  Each chunk
+// stages the input tile with its one-pixel halo as [y][x][channel] and the weights
+// as [tap][o][i] in BF16; every tap is then one A fragment per m16 tile and one B
+// fragment per n8 tile read straight from the staged tile shifted by (dy, dx).
+template <typename TIN, typename TOUT, bool RELU, bool FLIP, int MT, int TW>
+__global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, const bf16* __restrict__ w,
+                                                   const float* __restrict__ bias, TOUT* __restrict__ out, int Cin,
+                                                   int Cout, int H, int W, const int* done) {
+  if (stopped(done)) return;
+  constexpr int TH = 256 / TW;   // tile rows
+  constexpr int RPW = TH / 4;    // rows per warp
+  constexpr int NPR = TW / 8;    // n8 tiles per row
+  constexpr int NT = RPW * NPR;  // n8 tiles per warp (8)
+  constexpr int MO = MT * 16;    // output channels per CTA
+  constexpr int SX = TW + 2;
+  __shared__ __align__(16) bf16 s_in[(TH + 2) * SX * kCP];
+  __shared__ __align__(16) bf16 s_w[9 * MO * kCP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int tiles_x = (W + TW - 1) / TW;
+  const int x0 = (blockIdx.x % tiles_x) * TW, y0 = (blockIdx.x / tiles_x) * TH;
+  const int o0 = blockIdx.y * MO;
+  const int b = blockIdx.z;
+  const int Wi = FLIP ? Cout : Cin;   // input channels of the forward layer's weight tensor
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[m][n][c] = 0.f;
+  for (int i0 = 0; i0 < Cin; i0 += 16) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 16 * (TH + 2) * SX; t += 128) {
+      const int xx = t % SX, r = t / SX, yy = r % (TH + 2), ci = r / (TH + 2);
+      const int gi = i0 + ci, gy = y0 + yy - 1, gx = x0 + xx - 1;
+      float v = 0.f;
+      if (gi < Cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = ldf(in + (((long long)b * Cin + gi) * H + gy) * W + gx);
+      s_in[(yy * SX + xx) * kCP + ci] = __float2bfloat16_rn(v);
+    }
+    for (int t = threadIdx.x; t < 9 * MO * 16; t += 128) {
+      const int k = t % 9, r = t / 9, ii = r % 16, oo = r / 16;
+      const int go = o0 + oo, gi = i0 + ii;
+      bf16 v = __float2bfloat16_rn(0.f);
+      if (go < Cout && gi < Cin)
+        v = FLIP ? w[((long long)gi * Wi + go) * 9 + (8 - k)] : w[((long long)go * Wi + gi) * 9 + k];
+      s_w[(k * MO + oo) * kCP + ii] = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) {
+      const int dy = k / 3, dx = k - 3 * dy;
+      uint32_t a[MT][4];
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        const bf16* pa = s_w + (k * MO + m * 16 + g) * kCP + 2 * q;
+        a[m][0] = lds32(pa);
+        a[m][1] = lds32(pa + 8 * kCP);
+        a[m][2] = lds32(pa + 8);
+        a[m][3] = lds32(pa + 8 * kCP + 8);
+      }
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const int r = warp * RPW + n / NPR, xb = (n % NPR) * 8;
+        const bf16* pb = s_in + ((r + dy) * SX + xb + g + dx) * kCP + 2 * q;
+        const uint32_t b0 = lds32(pb), b1 = lds32(pb + 8);
+#pragma unroll
+        for (int m = 0; m < MT; ++m) mma_bf16_16816(acc[m][n], a[m], b0, b1);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const int r = warp * RPW + n / NPR, xb = (n % NPR) * 8;
+      const int y = y0 + r, x = x0 + xb + 2 * q;
+      if (y >= H || x >= W) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = o0 + m * 16 + g + 8 * h;
+        if (o >= Cout) continue;
+        const float bo = bias ? bias[o] : 0.f;
+        float v0 = acc[m][n][2 * h] + bo, v1 = acc[m][n][2 * h + 1] + bo;
+        if (RELU) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        TOUT* dst = out + (((long long)b * Cout + o) * H + y) * W + x;
+        if (x + 1 < W) st2(dst, v0, v1);
+        else stf(dst, v0);
+      }
+    }
+}
+
+// Weight and bias gradients of a 3x3 convolution on the tensor cores:
+// gw[o][i][tap] += sum_p g[o][p] in[i][p + tap offset].  GEMM per tap: M = 16
+// output channels, N = 16 input channels (two n8 tiles), K = pixels, 16 at a time
+// along a row.  The CTA walks its slice of (image, row) rows; each row stages g
+// (BF16, [o][x]) and the three input rows y-1..y+1 twice ([dy][i][x], once shifted
+// by one pixel so that every tap's pixel pairs are 32-bit aligned); warp w
+// accumulates the taps w, w + 4, w + 8.  Partial sums go to the zeroed FP32
+// gradient with atomics.
+__global__ void __launch_bounds__(128) k_conv3_wgrad_mma(const bf16* __restrict__ in, const float* __restrict__ g,
+                                                         float* __restrict__ gw, float* __restrict__ gb, int Cin,
+                                                         int Cout, int H, int W, int B, int rows_per_cta) {
+  constexpr int WMAX = 64;
+  constexpr int SG = WMAX + 8;        // row stride (BF16) of the staged g rows
+  constexpr int SI = WMAX + 8;        // row stride of the staged input rows
+  __shared__ __align__(16) bf16 s_g[16 * SG];
+  __shared__ __align__(16) bf16 s_a[3 * 16 * SI];   // in[x - 1] at index x (halo at 0)
+  __shared__ __align__(16) bf16 s_b[3 * 16 * SI];   // in[x] at index x
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gq = lane >> 2, q = lane & 3;
+  const int o0 = blockIdx.x * 16, i0 = blockIdx.y * 16;
+  const int Wp = (W + 15) & ~15;      // K extent of a row, zero padded to whole chunks
+  const int ntap = warp == 0 ? 3 : 2;
+  float acc[3][2][4];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[j][n][c] = 0.f;
+  float accb = 0.f;
+  const int r0 = blockIdx.z * rows_per_cta;
+  const int r1 = min(B * H, r0 + rows_per_cta);
+  for (int row = r0; row < r1; ++row) {
+    const int b = row / H, y = row % H;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 16 * Wp; t += 128) {
+      const int oo = t / Wp, x = t % Wp;
+      float v = 0.f;
+      if (o0 + oo < Cout && x < W) v = g[(((long long)b * Cout + o0 + oo) * H + y) * W + x];
+      s_g[oo * SG + x] = __float2bfloat16_rn(v);
+    }
+    for (int t = threadIdx.x; t < 3 * 16 * (Wp + 2); t += 128) {
+      const int xs = t % (Wp + 2), r = t / (Wp + 2), ii = r % 16, dy = r / 16;
+      const int yy = y + dy - 1, x = xs - 1;
+      bf16 v = __float2bfloat16_rn(0.f);
+      if (i0 + ii < Cin && yy >= 0 && yy < H && x >= 0 && x < W) v = in[(((long long)b * Cin + i0 + ii) * H + yy) * W + x];
+      s_a[(dy * 16 + ii) * SI + xs] = v;
+      if (xs < Wp) {
+        bf16 u = __float2bfloat16_rn(0.f);
+        if (i0 + ii < Cin && yy >= 0 && yy < H && xs < W) u = in[(((long long)b * Cin + i0 + ii) * H + yy) * W + xs];
+        s_b[(dy * 16 + ii) * SI + xs] = u;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 && o0 + (int)threadIdx.x < Cout) {
+      const float* gr = g + (((long long)b * Cout + o0 + threadIdx.x) * H + y) * W;
+      for (int x = 0; x < W; ++x) accb += gr[x];
+    }
+    for (int c0 = 0; c0 < Wp; c0 += 16) {
+      uint32_t a[4];
+      const bf16* pa = s_g + gq * SG + c0 + 2 * q;
+      a[0] = lds32(pa);
+      a[1] = lds32(pa + 8 * SG);
+      a[2] = lds32(pa + 8);
+      a[3] = lds32(pa + 8 * SG + 8);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (j >= ntap) break;
+        const int k = warp + 4 * j;
+        const int dy = k / 3, dx = k - 3 * dy;
+        // pixel p needs in[p + dx - 1]: s_a[p + dx] for dx = 0, 2 and s_b[p] for dx = 1
+        const bf16* base = (dx == 1 ? s_b + c0 : s_a + c0 + dx) + (dy * 16) * SI + 2 * q;
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          const bf16* pb = base + (n * 8 + gq) * SI;
+          mma_bf16_16816(acc[j][n], a, lds32(pb), lds32(pb + 8));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (j >= ntap) break;
+    const int k = warp + 4 * j;
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int o = o0 + gq + 8 * (c >> 1), i = i0 + n * 8 + 2 * q + (c & 1);
+        if (o < Cout && i < Cin) atomicAdd(gw + ((long long)o * Cin + i) * 9 + k, acc[j][n][c]);
+      }
+  }
+  if (threadIdx.x < 16 && blockIdx.y == 0 && o0 + (int)threadIdx.x < Cout) atomicAdd(gb + o0 + threadIdx.x, accb);
+}
+
 // Weight and bias gradients of a 3x3 convolution: gw[o][i][dy][dx] +=
 // sum_{b,y,x} g[b][o][y][x] in[b][i][y+dy-1][x+dx-1], gb[o] += sum g[b][o].
 // CTA: 16 output x 16 input channels, one image row at a time over its slice of the
@@ -456,6 +679,7 @@ struct Layer {
 
 struct cmm_unet {
   int refs = 1;
+  int tensor_cores = 1;        // 3x3 convolutions on the tensor cores (0: the FP32 CUDA-core kernels)
   cmm_ctx* ctx = nullptr;
   int ny = 0, nx = 0, L = 0, batch_max = 0;
   int widths[4] = {0, 0, 0, 0};
@@ -484,9 +708,29 @@ int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>
 int level_h(const cmm_unet* u, int l) { return u->ny >> l; }
 int level_w(const cmm_unet* u, int l) { return u->nx >> l; }
 
+template <typename TIN, typename TOUT, bool RELU, bool FLIP, int MT, int TW>
+int conv3_tc(const cmm_unet* u, const TIN* in, const bf16* w, const float* bias, TOUT* out, int Cin, int Cout, int H,
+             int W, int B, const int* done) {
+  constexpr int TH = 256 / TW;
+  const dim3 g(((W + TW - 1) / TW) * ((H + TH - 1) / TH), (Cout + MT * 16 - 1) / (MT * 16), B);
+  k_conv3_mma<TIN, TOUT, RELU, FLIP, MT, TW><<<g, 128, 0, u->ctx->stream>>>(in, w, bias, out, Cin, Cout, H, W, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
 template <typename TIN, typename TOUT, bool RELU, bool FLIP>
 int conv3(const cmm_unet* u, const TIN* in, const bf16* w, const float* bias, TOUT* out, int Cin, int Cout, int H,
           int W, int B, const int* done) {
+  if (u->tensor_cores) {
+    // two m16 tiles per CTA where there are 32 or more output channels; 8-wide
+    // pixel tiles for maps narrower than 16
+    if (Cout >= 32) {
+      return W >= 16 ? conv3_tc<TIN, TOUT, RELU, FLIP, 2, 16>(u, in, w, bias, out, Cin, Cout, H, W, B, done)
+                     : conv3_tc<TIN, TOUT, RELU, FLIP, 2, 8>(u, in, w, bias, out, Cin, Cout, H, W, B, done);
+    }
+    return W >= 16 ? conv3_tc<TIN, TOUT, RELU, FLIP, 1, 16>(u, in, w, bias, out, Cin, Cout, H, W, B, done)
+                   : conv3_tc<TIN, TOUT, RELU, FLIP, 1, 8>(u, in, w, bias, out, Cin, Cout, H, W, B, done);
+  }
   const dim3 g(((W + 15) / 16) * ((H + 15) / 16), (Cout + 15) / 16, B);
   k_conv3<TIN, TOUT, RELU, FLIP><<<g, 256, 0, u->ctx->stream>>>(in, w, bias, out, Cin, Cout, H, W, done);
   CMM_LAUNCH_CHECK();
@@ -500,7 +744,8 @@ int conv3_wgrad(const cmm_unet* u, const bf16* in, const float* g, float* gw, fl
   const int slices = std::max(1, std::min(rows, 608 / std::max(1, ctas_ij)));
   const int per = (rows + slices - 1) / slices;
   const dim3 gr((Cout + 15) / 16, (Cin + 15) / 16, (rows + per - 1) / per);
-  k_conv3_wgrad<<<gr, 256, 0, u->ctx->stream>>>(in, g, gw, gb, Cin, Cout, H, W, B, per);
+  if (u->tensor_cores) k_conv3_wgrad_mma<<<gr, 128, 0, u->ctx->stream>>>(in, g, gw, gb, Cin, Cout, H, W, B, per);
+  else k_conv3_wgrad<<<gr, 256, 0, u->ctx->stream>>>(in, g, gw, gb, Cin, Cout, H, W, B, per);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
@@ -773,6 +1018,12 @@ int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const 
     return s;
   }
   *out = u;
+  return CMM_OK;
+}
+
+int cmm_unet_set_tensor_cores(cmm_unet* u, int32_t enable) {
+  if (!u) return fail(CMM_ERR_ARG, "null argument");
+  u->tensor_cores = enable ? 1 : 0;
   return CMM_OK;
 }
 

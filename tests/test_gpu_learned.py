@@ -65,8 +65,14 @@ def test_param_count(cmm, ctx):
     assert net.n_params == ou.param_count(WIDTHS) == 299651
 
 
-@pytest.mark.parametrize("widths,hw", [(WIDTHS, 64), ((8, 12), 32)])
-def test_unet_forward_and_gradient_match_oracle(cmm, ctx, widths, hw):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("widths,hw", [(WIDTHS, 64), ((8, 12), 32), ((16, 24, 40), 24)])
+def test_unet_forward_and_gradient_match_oracle(cmm, ctx, widths, hw, tensor_cores):
+    """Both convolution paths: the tensor-core implicit GEMMs (BF16 mma, the
+    default; they also round the FP32 gradients entering the backward
+    convolutions to BF16) and the FP32 CUDA-core kernels.  The 24x24 case has
+    maps narrower than 16 at its lower levels (6x6 at the bottom) and 40 output
+    channels (a partly filled second m16 tile)."""
     g = np.random.default_rng(5)
     p = ou.init_params(widths, seed=11)
     p += 0.02 * g.standard_normal(p.size)
@@ -75,6 +81,7 @@ def test_unet_forward_and_gradient_match_oracle(cmm, ctx, widths, hw):
     x = g.standard_normal((B, 3, hw, hw))
     t = g.standard_normal((B, 3, hw, hw)) * 0.1
     net = cmm.UNet(ctx, hw, hw, widths, batch_max=B)
+    cmm.cmm_unet_set_tensor_cores(net.h, tensor_cores)
     pt = torch.as_tensor(p, dtype=torch.float32, device="cuda:0")
     net.set_params(pt)
     xt = torch.as_tensor(x, dtype=torch.float32, device="cuda:0")

@@ -474,17 +474,26 @@ def test_full_map_solve_matches_oracle(cmm, ctx, act_map_solution, kind):
 
 
 def test_full_map_solve_f32_operator(cmm, ctx, act_map_solution):
-    """The same solve with the FP32 operator (FP64 CG) to 1e-6: the error per Stokes
-    component against the oracle's tightly converged solution stays below 2e-5."""
+    """The same solve with the FP32 operator (FP64 CG) stopped at a residual of 1e-6:
+    its error per Stokes component against the oracle's tightly converged solution
+    is that of the FP64 operator stopped at the same residual (the CG truncation,
+    larger in Q and U, whose maps are ten times weaker than T) plus at most 1e-5,
+    and below 1e-4."""
     scan, noise, oop, d, b_ref, xo, io = act_map_solution
-    op = cmm.Operator(ctx, scan, noise, precision=1)
-    b = op.rhs(torch.as_tensor(d, dtype=torch.float32, device="cuda:0"))
-    pc = cmm.Precon(op, cmm.PRECON_BINNED)
-    x, info, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=500)
-    assert info.status == 0
-    errs = stokes_errors(host(x), xo, oop.mask)
-    print(f"full-map F32 solve: {info.iterations} it, error per Stokes {errs[0]:.2e} {errs[1]:.2e} {errs[2]:.2e}")
-    assert max(errs) < 2e-5
+    errs = {}
+    for prec in (0, 1):
+        op = cmm.Operator(ctx, scan, noise, precision=prec)
+        dt = torch.float64 if prec == 0 else torch.float32
+        b = op.rhs(torch.as_tensor(d, dtype=dt, device="cuda:0"))
+        pc = cmm.Precon(op, cmm.PRECON_BINNED)
+        x, info, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=500)
+        assert info.status == 0
+        errs[prec] = stokes_errors(host(x), xo, oop.mask)
+        print(f"full-map solve to 1e-6, precision {prec}: {info.iterations} it, error per Stokes T/Q/U "
+              f"{errs[prec][0]:.2e} {errs[prec][1]:.2e} {errs[prec][2]:.2e}")
+    assert max(errs[1]) < 1e-4
+    for c in range(3):
+        assert errs[1][c] <= errs[0][c] + 1e-5
 
 
 def test_full_size_symmetry_and_rhs(cmm, ctx):
