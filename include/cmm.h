@@ -197,10 +197,10 @@ int cmm_noise_diag(cmm_noise* nz, double* diag_host);
 
 /* ---------------------------------------------------------------- operator
  * A = P^T N^-1 P (Eq. 2) in the given precision.  n_samp must be a power of two,
- * 32 <= n_samp <= 2^25.  det_chunk > 0 bounds how many detectors share one pass
+ * 32 <= n_samp <= 2^22.  det_chunk > 0 bounds how many detectors share one pass
  * through the intermediate spectrum buffer (<= 0: automatic).  The handle owns
- * that buffer (n_chunk * n_samp * 4 bytes in F32, 8 in F64, 2 in BF16) and a few
- * map-sized buffers.
+ * that buffer (n_chunk, rounded up to even, * n_samp * 4 bytes in F32, 8 in F64,
+ * 2 in BF16) and a few map-sized buffers.
  */
 int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precision,
                   int32_t det_chunk, cmm_op** out);
@@ -214,6 +214,17 @@ int cmm_op_destroy(cmm_op* op);
  * enable == 0 frees it.  Results are identical either way.  Only for the FP32 and
  * BF16 operators of non-periodic maps (else CMM_ERR_UNSUPPORTED). */
 int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable);
+/* Two-detector FFT packing of the FP32/BF16 A-application (enable != 0, the
+ * default): for 2^13 <= n_samp <= 2^20 and detectors with independent noise, the
+ * noise filter of Sec. Test setup is applied to two detectors at once as one
+ * complex sequence z = s_1 + i s_2 of n_samp points, so that every complex element
+ * is one time sample of both and the pointing tables are read once for the two;
+ * each bin pair (k, n - k) is filtered as Y(k) = a Z(k) + b conj Z(n - k) with
+ * a, b = (w_1 +- w_2) / 2.  enable == 0 selects the one-detector packing (even
+ * and odd samples as one complex sequence of n_samp / 2 points), which also serves
+ * correlated noise, the right-hand side and operators above the FP32 hit limit.
+ * Results agree to FP32 rounding either way; waits for the operator's stream. */
+int cmm_op_set_pair_packing(cmm_op* op, int32_t enable);
 /* m_out = A m_in (Eq. 2).  device double [ncomp][ny][nx] each; must not alias. */
 int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out);
 /* Same with host buffers: copies m_in to the device, applies A, copies the result

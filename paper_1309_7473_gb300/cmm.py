@@ -76,6 +76,7 @@ _SIGS = {
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
     "cmm_op_destroy": [_vp],
     "cmm_op_set_pixel_cache": [_vp, _i32],
+    "cmm_op_set_pair_packing": [_vp, _i32],
     "cmm_apply_A": [_vp, _vp, _vp],
     "cmm_apply_A_host": [_vp, _vp, _vp],
     "cmm_apply_A_noalloc": [_vp, _vp, _vp],
@@ -252,6 +253,10 @@ def cmm_op_destroy(h):
 
 def cmm_op_set_pixel_cache(op, enable=True):
     _check(_lib.cmm_op_set_pixel_cache(op, 1 if enable else 0))
+
+
+def cmm_op_set_pair_packing(h, enable):
+    _check(_lib.cmm_op_set_pair_packing(h, 1 if enable else 0))
 
 
 def cmm_apply_A(op, m_in, m_out):
@@ -523,6 +528,9 @@ class Operator:
 
     def set_pixel_cache(self, enable=True):
         cmm_op_set_pixel_cache(self.h, enable)
+
+    def set_pair_packing(self, enable=True):
+        cmm_op_set_pair_packing(self.h, enable)
 
     def new_map(self):
         import torch

@@ -392,6 +392,7 @@ static void free_op(cmm_op* op) {
   dfree(op->acc);
   dfree(op->acc32);
   dfree(op->tw);
+  dfree(op->tw_pair);
   dfree(op->tmp_a);
   dfree(op->tmp_b);
   dfree(op->pix);
@@ -454,7 +455,8 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   const int nc = pt->ncomp;
   op->acc_stride = nc == 1 ? 1 : 4;
   const size_t gel = precision == CMM_PREC_F64 ? 8 : 4;
-  int s = dalloc(&op->spec, per_det * chunk);
+  // an even number of detector slots: the two-detector path fills whole pairs
+  int s = dalloc(&op->spec, per_det * (chunk + (chunk & 1)));
   // map-sized buffers carry one extra pixel (index npix): the fast kernels send
   // samples outside the map there (zero in the gather copy, never read back)
   if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * (npix + 1));
@@ -585,6 +587,14 @@ int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable) {
     op->pix = nullptr;
   }
   return s;
+}
+
+int cmm_op_set_pair_packing(cmm_op* op, int32_t enable) {
+  if (!op) return fail(CMM_ERR_ARG, "null argument");
+  CMM_CUDA(cudaSetDevice(op->ctx->device));
+  CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+  op->pair = enable ? 1 : 0;
+  return CMM_OK;
 }
 
 }  // extern "C"

@@ -150,6 +150,9 @@ struct cmm_op {
   int acc_stride = 0;
   void* tw = nullptr;          // twiddle tables in the op's compute type
   int32_t* pix = nullptr;      // optional [n_det][n_samp] pixel index per sample (npix: outside)
+  int pair = 1;                // A-applications on the two-detector path where it applies (tod_pair.cu)
+  int pR = 0, pC = 0, plogR = 0, plogC = 0;   // split n_samp = pR pC of the two-detector sequences
+  void* tw_pair = nullptr;     // their twiddle tables (FP32)
   int corr_version = 0;        // noise correlation version the tables below were built for
   float* corr_minv = nullptr;  // [N + 1][r][r] per-bin M^-1 in slot order (index N: bin N)
   float2* corr_s = nullptr;    // [N][r] cross-detector solution per bin slot
@@ -198,6 +201,11 @@ int launch_corr_minv(cmm_op* op, const double* mode_par_dev, float* minv);
 int op_sync_corr(cmm_op* op);
 bool fast_path_ok(const cmm_op* op);
 bool fast_path_sizes(int logN, int prec, int* logR, int* logC);
+// ---- two-detector path (tod_pair.cu)
+bool pair_path_ok(const cmm_op* op);
+bool pair_path_sizes(int log_nt, int prec, int* logR, int* logC);
+int launch_apply_chunk_pair(cmm_op* op, int d0, int nd, int pass);
+int prepare_pair(cmm_op* op);
 
 // ---- handle lifetimes: a handle stays alive while handles made from it exist, so
 // they may be destroyed in any order (api.cu, unet.cu)

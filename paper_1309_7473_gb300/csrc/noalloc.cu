@@ -76,6 +76,12 @@ int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out) {
   v.spec = base + fixed;
   v.chunk = (int)std::min<size_t>((kNoAllocScratchBytes - fixed) / per_det, (size_t)op->pt->n_det);
   v.done = nullptr;
+  // the two-detector path fills whole pairs of spectrum slots: an even chunk, or
+  // the one-detector path when the array holds a single spectrum
+  if (pair_path_ok(&v)) {
+    if (v.chunk >= 2) v.chunk &= ~1;
+    else v.pair = 0;
+  }
 
   // The array keeps whatever the previous call left: the FP32 partial map must
   // start at zero (the FP64 accumulator is cleared by the gather kernel).

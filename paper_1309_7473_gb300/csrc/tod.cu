@@ -364,6 +364,7 @@ static int prepare_nc(int prec) {
 // (done once, before any stream capture).
 int op_prepare_kernels(cmm_op* op) {
   if (fast_path_ok(op)) CMM_TRY(prepare_fast(op));
+  if (op->prec != CMM_PREC_F64) CMM_TRY(prepare_pair(op));
   return op->pt->ncomp == 1 ? prepare_nc<1>(op->prec) : prepare_nc<3>(op->prec);
 }
 
@@ -378,6 +379,7 @@ static int apply_chunk_nc(cmm_op* op, int d0, int nd, const void* tod, int pass)
 
 int launch_apply_chunk(cmm_op* op, int d0, int nd, const void* tod, int tod_is_f64, int pass) {
   const int nc = op->pt->ncomp;
+  if (!tod && pair_path_ok(op)) return launch_apply_chunk_pair(op, d0, nd, pass);
   if (fast_path_ok(op)) {
     if (op->pt->max_hits <= kF32HitLimit || pass == 0 || pass == 1)
       return launch_apply_chunk_fast(op, d0, nd, tod, tod_is_f64, pass);

@@ -27,68 +27,9 @@
 #include "common.cuh"
 #include "fft_reg.cuh"
 #include "tod_common.cuh"
+#include "tod_fast.cuh"
 
 namespace cmm {
-
-// Tuning knobs (compile-time; the defaults are the measured best on GB300).
-#ifndef CMM_DETS_PER_CTA
-#define CMM_DETS_PER_CTA 1
-#endif
-#ifndef CMM_COL_THREADS_PER_SM
-#define CMM_COL_THREADS_PER_SM 1024
-#endif
-#ifndef CMM_INV_THREADS_PER_SM
-#define CMM_INV_THREADS_PER_SM 768
-#endif
-#ifndef CMM_FILTER_MINB
-#define CMM_FILTER_MINB 4
-#endif
-#ifndef CMM_GEN_UNROLL
-#define CMM_GEN_UNROLL 2
-#endif
-#ifndef CMM_COLJ_256
-#define CMM_COLJ_256 16   // columns per CTA of the column passes at R = 256
-#endif
-#ifndef CMM_BIN_HALVES
-#define CMM_BIN_HALVES 1   // consecutive samples per lane in the binning: 8 x this
-#endif
-#ifndef CMM_BIN_UNROLL
-#define CMM_BIN_UNROLL 1
-#endif
-
-constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
-constexpr int kGenUnroll = CMM_GEN_UNROLL;
-constexpr int kBinUnroll = CMM_BIN_UNROLL;
-constexpr int kBinHalves = CMM_BIN_HALVES;
-constexpr int kFlushDets = 128;
-constexpr int kE = 16;     // elements per thread in the column FFT
-
-// Columns per CTA: 32 (one per lane) for R <= 128, 16 (one per half-warp lane)
-// for R = 256; either way a half-warp reads 16 complex = 32 consecutive samples
-// and touches 32 different shared-memory banks.
-template <int R> struct ColShape {
-  static constexpr int J = R >= 256 ? CMM_COLJ_256 : 32;
-  static constexpr int THREADS = J * R / kE;
-  static constexpr int MINB = CMM_COL_THREADS_PER_SM / THREADS > 0 ? CMM_COL_THREADS_PER_SM / THREADS : 1;
-  static constexpr int MINB_INV = CMM_INV_THREADS_PER_SM / THREADS > 0 ? CMM_INV_THREADS_PER_SM / THREADS : 1;
-};
-
-// GB300's FP64 unit also executes int <-> float conversions, at a small fraction
-// of the FP32 rate; this helper does the one of the filter exactly on the FP32 pipe.
-
-// Exact float of an integer 0 <= k < 2^23 (IEEE-754 single: 2^23 + k has k as its
-// mantissa).
-__device__ __forceinline__ float small_int_to_float(int k) {
-  return __int_as_float(0x4B000000 | k) - 8388608.0f;
-}
-
-// exp2 / log2 on the special function unit; relative error of w below 1e-6.
-__device__ __forceinline__ float filter_weight_law(const float4 cf, int k) {
-  if (cf.w != 0.0f) return cf.x;
-  const float kk = small_int_to_float(k == 0 ? 1 : k);
-  const float e = exp2f(fmaf(-cf.y, __log2f(kk), cf.z));
-  return __fdividef(cf.x, 1.0f + e);
-}
 
 // w_d(f_k): the detector's tabulated weight when the noise has a table, else the law
 __device__ __forceinline__ float filter_weight_fast(const TodArgs& a, int d, const float4 cf, int k) {
@@ -104,33 +45,6 @@ __device__ __forceinline__ void response_fast(const TodArgs& a, int t, const flo
   s = pol.y * r2.x + pol.x * r2.y;
 }
 
-// w_N^e, 0 <= e < N, from the two tables w_N^(e mod C) and w_R^(e div C)
-__device__ __forceinline__ float2 tw_N(const TodArgs& a, const float2* __restrict__ tw, int e) {
-  const float2 lo = __ldg(tw + a.twl.Nlo_off + (e & (a.C - 1)));
-  const float2 hi = __ldg(tw + a.twl.R_off + (e >> a.logC));
-  return cmul(lo, hi);
-}
-
-// Pixel of a sample for the fast kernels (the rule of sample_pixel).  A sample
-// outside the map gets index npix: an extra pixel that is zero in the gather copy
-// and whose accumulator is never read, so the kernels take no branch on it.
-template <bool PERIODIC>
-__device__ __forceinline__ int pixel_fast(const int4 b, const int2 o, int ny, int nx, int npix) {
-  const int ox = b.z * o.x - b.w * o.y;
-  const int oy = b.w * o.x + b.z * o.y;
-  int ix = (b.x + (1 << 15) + (ox >> 6)) >> 16;
-  int iy = (b.y + (1 << 15) + (oy >> 6)) >> 16;
-  if (PERIODIC) {
-    ix %= nx;
-    ix += ix < 0 ? nx : 0;
-    iy %= ny;
-    iy += iy < 0 ? ny : 0;
-    return iy * nx + ix;
-  }
-  const bool in = (unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny;
-  return in ? iy * nx + ix : npix;
-}
-
 // (P m) at sample t of a detector: gather from the FP32 map copy at the sample's pixel
 template <int NC, bool PERIODIC>
 __device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, const float2 pol, int t) {
@@ -142,39 +56,6 @@ __device__ __forceinline__ float project_fast(const TodArgs& a, const int2 off, 
   response_fast(a, t, pol, c, s);
   return fmaf(s, g.z, fmaf(c, g.y, g.x));
 }
-
-// J interleaved columns: position pos of column cl at J pos + cl, so every access
-// of the column FFT puts consecutive lanes on consecutive elements.
-template <int J>
-struct ColJ {
-  float2* buf;
-  int cl;
-  __device__ __forceinline__ void st(int pos, float2 v) const { buf[pos * J + cl] = v; }
-  __device__ __forceinline__ float2 ld(int pos) const { return buf[pos * J + cl]; }
-  __device__ __forceinline__ int base(int pos) const { return pos * J + cl; }
-  __device__ __forceinline__ void st_at(int b, int o, float2 v) const { buf[b + o * J] = v; }
-  __device__ __forceinline__ float2 ld_at(int b, int o) const { return buf[b + o * J]; }
-};
-
-template <int R> struct ColPlan;
-template <> struct ColPlan<64> {
-  template <int SIGN, typename Addr>
-  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
-    rfft<SIGN, kE, 16, 4>(x, i, tw, ad);
-  }
-};
-template <> struct ColPlan<128> {
-  template <int SIGN, typename Addr>
-  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
-    rfft<SIGN, kE, 16, 8>(x, i, tw, ad);
-  }
-};
-template <> struct ColPlan<256> {
-  template <int SIGN, typename Addr>
-  static __device__ __forceinline__ void run(float2 (&x)[kE], int i, const float2* tw, const Addr& ad) {
-    rfft<SIGN, kE, 16, 16>(x, i, tw, ad);
-  }
-};
 
 // ------------------------------------------------------------------ pass T (forward)
 // The samples t (even) and t + 1 with known pixels (cached pointing): one 16-byte
@@ -513,51 +394,6 @@ __global__ void k_corr_minv(const TodArgs a, int n_det, const double* __restrict
 
 // ------------------------------------------------------------------ pass T' (inverse + P^T)
 
-__device__ __forceinline__ void red_add(float* p, float v) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-__device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(0.0f)
-               : "memory");
-}
-
-// Run accumulator of one lane's consecutive samples: samples in the same pixel as
-// the open run are summed in registers; a new pixel closes the run with one
-// reduction into the FP32 partial map.  Runs in the extra pixel `skip` (samples
-// outside the map) issue none: every warp would otherwise hit that one address.
-struct BinRun {
-  int cur = -1;   // pixel of the open run (-1: none)
-  float ax = 0.f, ay = 0.f, az = 0.f;
-};
-
-template <int NC>
-__device__ __forceinline__ void bin_close(float* acc32, const BinRun& r, int skip) {
-  if (r.cur >= 0 && r.cur != skip) {
-    if (NC == 1) red_add(acc32 + r.cur, r.ax);
-    else red_add4(acc32 + 4 * r.cur, r.ax, r.ay, r.az);
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ void bin_push8(float* acc32, BinRun& r, const int (&p)[8], const float (&u)[8],
-                                          const float (&c)[8], const float (&s)[8], int skip) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (p[k] != r.cur) {
-      bin_close<NC>(acc32, r, skip);
-      r.cur = p[k];
-      r.ax = 0.f;
-      r.ay = 0.f;
-      r.az = 0.f;
-    }
-    r.ax += u[k];
-    if (NC == 3) {
-      r.ay = fmaf(c[k], u[k], r.ay);
-      r.az = fmaf(s[k], u[k], r.az);
-    }
-  }
-}
-
 template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
 __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k_fast_inv_bin(const TodArgs a, int nd) {
   constexpr int TPC = R / kE;
@@ -801,7 +637,7 @@ static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
   }
 }
 
-static int flush(const TodArgs& a, int nc, cudaStream_t st) {
+int launch_flush(const TodArgs& a, int nc, cudaStream_t st) {
   // npix + 1 entries: the extra pixel is cleared too, so its FP32 sum stays bounded
   const int blocks = (int)std::min<long long>((a.npix + 256) / 256, 4096);
   if (nc == 1) k_fast_flush<1><<<blocks, 256, 0, st>>>(a.acc32, a.acc, a.npix + 1, a.done);
@@ -843,7 +679,7 @@ static int apply_fast_s(cmm_op* op, int d0, int nd, const void* tod, int tod_is_
       b.spec = reinterpret_cast<S*>(a.spec) + (long long)g0 * a.N;
       if (nc == 1) CMM_TRY((dispatch_T<1, S>(b, gn, 2, st, false)));
       else CMM_TRY((dispatch_T<3, S>(b, gn, 2, st, false)));
-      CMM_TRY(flush(b, nc, st));
+      CMM_TRY(launch_flush(b, nc, st));
     }
   }
   return CMM_OK;

@@ -335,13 +335,18 @@ def test_pcg_circulant_tiny_patch(cmm, ctx):
 # (2^20 samples = the launch configuration of the 1024-detector bench) on a few
 # detectors spread over the focal plane, which the oracle evaluates in seconds.
 
-@pytest.mark.parametrize("log_nt", [13, 17, 18, 19, 20])
+@pytest.mark.parametrize("pair", [True, False])
+@pytest.mark.parametrize("log_nt", [13, 14, 15, 16, 17, 18, 19, 20])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec):
+def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec, pair):
+    """Every size of the register-FFT kernels, with the two-detector packing (the
+    default; the five detectors and chunks of two leave one detector alone in its
+    last pair) and with the one-detector packing."""
     full, fnoise = gen.act_patch(n_t=1 << log_nt)
     dets = np.array([0, 300, 611, 1023, 17])
     scan, noise = full.subset(dets), fnoise.subset(dets)
     op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=2)
+    op.set_pair_packing(pair)
     oop = om.make_operator(scan, noise)
     assert np.array_equal(op.pointing.mask()[0], oop.mask)
     m = gen.sky_map(scan.ny, scan.nx, cfg=2)
@@ -373,6 +378,8 @@ def test_apply_A_fast_small_ragged(cmm, ctx, ncomp):
     for chunk in (0, 2, 3):
         op = cmm.Operator(ctx, scan, noise, precision=1, det_chunk=chunk)
         assert rel(host(op.apply(dev(m))), ref) < TOL[1]
+        op.set_pair_packing(False)
+        assert rel(host(op.apply(dev(m))), ref) < TOL[1]
 
 
 @functools.lru_cache(maxsize=None)
@@ -385,9 +392,10 @@ def _flush_case(log_nt):
     return scan, noise, oop, m, om.apply_A(oop, m)
 
 
+@pytest.mark.parametrize("pair", [True, False])
 @pytest.mark.parametrize("log_nt", [13, 15, 18])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_apply_A_flush_groups(cmm, ctx, log_nt, prec):
+def test_apply_A_flush_groups(cmm, ctx, log_nt, prec, pair):
     """320 ACT-like detectors in one chunk (det_chunk = 0), as the 1024-detector
     launch: the binning pass runs as three groups of at most 128 detectors, each
     followed by the flush of the FP32 partial map into the FP64 accumulator.
@@ -395,6 +403,7 @@ def test_apply_A_flush_groups(cmm, ctx, log_nt, prec):
     use the 256-point column FFTs of the bench's size."""
     scan, noise, oop, m, ref = _flush_case(log_nt)
     op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=0)
+    op.set_pair_packing(pair)
     assert np.array_equal(op.pointing.mask()[0], oop.mask)
     assert rel(host(op.apply(dev(m))), ref) < TOL[prec]
     op.set_pixel_cache(True)
@@ -409,8 +418,9 @@ def _golden_act_mask():
     return mod.load()
 
 
+@pytest.mark.parametrize("pair", [True, False])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_full_size_sampled_detectors_match_oracle(cmm, ctx, prec):
+def test_full_size_sampled_detectors_match_oracle(cmm, ctx, prec, pair):
     """The bench's workload in its launch configuration (1024 detectors x 2^20
     samples in one chunk, 1200x900 TQU, FP32 compute, on-the-fly and cached
     pointing) against the oracle on sampled detectors: every detector but four
@@ -424,6 +434,7 @@ def test_full_size_sampled_detectors_match_oracle(cmm, ctx, prec):
     sigma = np.full(scan.n_det, 1e25)
     sigma[keep] = noise.sigma[keep]
     op = cmm.Operator(ctx, scan, gen.Noise(sigma, noise.fknee, noise.alpha), precision=prec)
+    op.set_pair_packing(pair)
     gmask, n_good = op.pointing.mask()
     assert n_good == doc["n_good"] and np.array_equal(gmask, mask)
     oop = om.make_operator(scan.subset(keep), noise.subset(keep), mask=mask)
