@@ -58,7 +58,11 @@ def parse():
                          "correction on 64x64 patches (train on 90 realisations, evaluate on 20)")
     ap.add_argument("--batch", type=int, default=64, help="solves of the batch workload")
     ap.add_argument("--batch-iters", type=int, default=20, help="PCG iterations timed per solve")
-    ap.add_argument("--learned-reals", type=int, default=100)
+    ap.add_argument("--batch-small", action="store_true",
+                    help="batch workload at the small corner of its distribution: every solve 128 detectors "
+                         "x 2^18 samples on a 256x256 TQU map")
+    ap.add_argument("--learned-reals", type=int, default=220,
+                    help="realisations of the learned workload (90 percent train: about 20k pairs)")
     ap.add_argument("--learned-epochs", type=int, default=15)
     return ap.parse_args()
 
@@ -474,23 +478,43 @@ def run_learned(args):
     train_s = time.perf_counter() - t0
     pcl = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
     cmm.cmm_precon_set_correction(pcl.h, net.h)
-    rows = []
+    pcb = cmm.Precon(op, cmm.PRECON_BINNED)
+    # on 20 held-out realisations: binned PCG, PCG(M_C), the corrected preconditioner
+    # in flexible CG (Polak-Ribiere form and FCG(8)), and PCG(M_C) started from the
+    # corrected preconditioner applied to b
+    forms = {"binned": [], "plain_mc": [], "learned_fpcg": [], "learned_fcg8": [], "learned_x0": []}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        info = fn()
+        torch.cuda.synchronize()
+        return info.iterations, time.perf_counter() - t, info.status
+
     for real in range(10_000, 10_020):
         b = rhs(real)
-        _, i0, _, _ = cmm.solve(op, pc, b, tol=1e-6, maxit=1000)
-        _, i1, _, _ = cmm.solve(op, pcl, b, tol=1e-6, maxit=1000)
-        rows.append((i0.iterations, i0.seconds, i1.iterations, i1.seconds, i1.status))
-    n = len(rows)
+        forms["binned"].append(timed(lambda: cmm.solve(op, pcb, b, tol=1e-6, maxit=2000)[1]))
+        forms["plain_mc"].append(timed(lambda: cmm.solve(op, pc, b, tol=1e-6, maxit=1000)[1]))
+        forms["learned_fpcg"].append(timed(lambda: cmm.solve(op, pcl, b, tol=1e-6, maxit=1000)[1]))
+        forms["learned_fcg8"].append(timed(lambda: cmm.solve(op, pcl, b, tol=1e-6, maxit=1000, flexible=True,
+                                                             window=8)[1]))
+
+        def from_x0():
+            x0 = pcl.apply(b)
+            return cmm.solve(op, pc, b, x=x0, tol=1e-6, maxit=1000)[1]
+        forms["learned_x0"].append(timed(from_x0))
+    summary = {k: {"iterations_mean": sum(r[0] for r in v) / len(v), "seconds_mean": sum(r[1] for r in v) / len(v),
+                   "all_converged": all(r[2] == 0 for r in v)} for k, v in forms.items()}
+    n = len(forms["plain_mc"])
     return {
-        "metric": "iterations to 1e-6, flexible PCG(M_C + U-Net) vs PCG(M_C)", "unit": "iterations",
-        "higher_is_better": False, "value": sum(r[2] for r in rows) / n, "n_gpus": 1, "steps": n,
-        "warmup": 0, "dtype": "f64 solve, bf16 network", "data": "synthetic",
+        "metric": "iterations to 1e-6, corrected preconditioner (FCG(8) with M_C + U-Net) vs PCG(M_C)",
+        "unit": "iterations", "higher_is_better": False, "value": summary["learned_fcg8"]["iterations_mean"],
+        "n_gpus": 1, "steps": n, "warmup": 0, "dtype": "f64 solve, bf16 network", "data": "synthetic",
         "config": {"workload": "32 det x 2^16 samples, 64x64 TQU, taper 8 px; U-Net widths 16/32/48/96",
                    "realisations": args.learned_reals, "train_realisations": n_train,
-                   "pairs_train": int(ti.shape[0]), "epochs": args.learned_epochs},
-        "plain_mc": {"iterations_mean": sum(r[0] for r in rows) / n, "seconds_mean": sum(r[1] for r in rows) / n},
-        "learned": {"iterations_mean": sum(r[2] for r in rows) / n, "seconds_mean": sum(r[3] for r in rows) / n,
-                    "all_converged": all(r[4] == 0 for r in rows)},
+                   "pairs_train": int(ti.shape[0]) // 2, "pairs_train_with_sign_flips": int(ti.shape[0]),
+                   "epochs": args.learned_epochs},
+        "solves": summary,
         "val_loss": {"zero_output": float(0.5 * (vt.double() ** 2).mean()), "trained": hist[-1][2]},
         "harvest_seconds": round(harvest_s, 2), "train_seconds": round(train_s, 2),
     }
@@ -771,7 +795,8 @@ def run_batch(args):
     from paper_1309_7473_gb300 import build
     build.build()
     from paper_1309_7473_gb300 import cmm
-    probs = [gen.uneven_problem(k) for k in range(args.batch)]
+    small = (128, 1 << 18, 256, 256)
+    probs = [gen.uneven_problem(k, sizes=small if args.batch_small else None) for k in range(args.batch)]
     n_s = [sc.n_det * sc.n_t for sc, _ in probs]
     # device memory: spectrum chunk (4 B/sample, at most 8 GB) per operator + tables
     need = sum(min(4 * n, 8 << 30) + 32 * sc.n_t + 200 * sc.npix for n, (sc, _) in zip(n_s, probs))
@@ -800,7 +825,7 @@ def run_batch(args):
     cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=2, check_every=2, true_resid=False)   # warm-up
     torch.cuda.synchronize()
     by_width = {}
-    for w in (0, 2, 4):
+    for w in (0, 2, 4, 8):
         t0 = time.perf_counter()
         cmm.cmm_batch_solve(hs, ph, bs, xs, tol=0.0, maxit=it, check_every=it, width=w, true_resid=False)
         torch.cuda.synchronize()
@@ -816,8 +841,10 @@ def run_batch(args):
         "metric": "samples/s per batched P^T N^-1 P apply (circulant PCG, uneven solves)",
         "value": total / batched_s, "unit": "samples/s", "higher_is_better": True, "n_gpus": 1,
         "steps": it, "warmup": 2, "dtype": "f32 (FP64 CG)", "data": "synthetic",
-        "config": {"workload": f"{args.batch} seeded solves: n_det in {{128..1024}}, n_samp in {{2^18..2^20}}, "
-                               f"maps 256x256..1200x900 TQU, circulant taper {args.taper} px",
+        "config": {"workload": (f"{args.batch} seeded solves, each 128 det x 2^18 samples on 256x256 TQU"
+                                if args.batch_small else
+                                f"{args.batch} seeded solves: n_det in {{128..1024}}, n_samp in {{2^18..2^20}}, "
+                                f"maps 256x256..1200x900 TQU") + f", circulant taper {args.taper} px",
                    "samples_per_iteration": sum(n_s), "pointing": "cached" if cache else "on-the-fly",
                    "sizes": sorted({(sc.n_det, sc.n_t, sc.ny, sc.nx) for sc, _ in probs})[:8]},
         "batched_seconds": batched_s, "batched_seconds_by_width": by_width, "sequential_seconds": seq_s,

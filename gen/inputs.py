@@ -303,16 +303,20 @@ def corr_noise(det_off, r=3, amp=(3.0, 1.0, 1.0), fknee=(2.0, 1.0, 1.0), alpha=(
 UNEVEN_MAP_SIZES = ((256, 256), (240, 320), (360, 480), (450, 600), (600, 800), (750, 1000), (900, 1200))
 
 
-def uneven_problem(k, real=0, ncomp=3):
+def uneven_problem(k, real=0, ncomp=3, sizes=None):
     """Problem k of the batched Monte-Carlo workload: seeded n_det from
     {128, 256, 512, 1024}, n_t from {2^18, 2^19, 2^20} and a 5-smooth map size from
     256x256 to 1200x900 (ny x nx) at 0.5'; hex focal plane at 1.667', the scan law of
     the ACT-like patch (rising and setting halves) with a throw of 0.8 of the map
-    width; the noise law of the tiny patch (sigma 1, f_knee 2 Hz, alpha 3.5)."""
+    width; the noise law of the tiny patch (sigma 1, f_knee 2 Hz, alpha 3.5).
+    sizes = (n_det, n_t, ny, nx) fixes the sizes (e.g. the smallest corner of the
+    distribution, 128 detectors x 2^18 samples on 256x256) and keeps the rest."""
     g = rng(4, 1000 * real + k, "misc")
     n_det = int(g.choice([128, 256, 512, 1024]))
     n_t = int(g.choice([1 << 18, 1 << 19, 1 << 20]))
     ny, nx = UNEVEN_MAP_SIZES[int(g.integers(len(UNEVEN_MAP_SIZES)))]
+    if sizes is not None:
+        n_det, n_t, ny, nx = (int(v) for v in sizes)
     rings = 1
     while 3 * rings * (rings + 1) + 1 < n_det:
         rings += 1

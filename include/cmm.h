@@ -108,6 +108,10 @@ typedef struct {
   int32_t skip_true_resid; /* != 0: no exit check of ||b - A x|| (true_rel_resid = -1) */
   int32_t resume;      /* != 0: continue from the state of cmm_solve_state_load; x holds that
                           state's iterate x_k, the count goes on from k (maxit counts from 0) */
+  int32_t fcg_window;  /* flexible CG only: m = 2..8 keeps the last m directions and makes each
+                          new one A-conjugate to them, p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j,
+                          step alpha = p^T r / p^T A p (truncated flexible CG, Notay 2000); 0 or 1:
+                          the Polak-Ribiere form above.  Not with resume or resid_replace. */
 } cmm_solve_opts;
 
 typedef struct {

@@ -555,10 +555,13 @@ class SolveInfo:
     iterates: list | None = None
 
 
-def pcg(apply_a, apply_m, b, tol=1e-6, maxit=1000, x0=None, flexible=False, keep_iterates=False):
+def pcg(apply_a, apply_m, b, tol=1e-6, maxit=1000, x0=None, flexible=False, keep_iterates=False, window=1):
     """PCG on A x = b with preconditioner M (R11); with ``flexible`` the
     Polak-Ribiere beta = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k) (flexible CG) is used.
-    Returns (x, SolveInfo)."""
+    With ``flexible`` and ``window`` m > 1: truncated flexible CG, FCG(m) (Notay 2000),
+    see fcg().  Returns (x, SolveInfo)."""
+    if flexible and window > 1:
+        return fcg(apply_a, apply_m, b, window, tol=tol, maxit=maxit, x0=x0, keep_iterates=keep_iterates)
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply_a(x) if x0 is not None else b.copy()
     bnorm = math.sqrt(float(np.vdot(b, b)))
@@ -592,6 +595,49 @@ def pcg(apply_a, apply_m, b, tol=1e-6, maxit=1000, x0=None, flexible=False, keep
             beta = rho_new / rho
         p = z_new + beta * p
         z, rho = z_new, rho_new
+    return x, SolveInfo(k, converged, hist, terms, iters)
+
+
+def fcg(apply_a, apply_m, b, window, tol=1e-6, maxit=1000, x0=None, keep_iterates=False):
+    """Truncated flexible conjugate gradients FCG(m), m = ``window`` (Notay 2000, for a
+    preconditioner that changes from one iteration to the next, such as M_C followed
+    by a nonlinear learned correction).  Each new direction is the preconditioned
+    residual made A-conjugate to the previous m directions,
+        p_i = z_i - sum_{j = i-m}^{i-1} (z_i^T A p_j / p_j^T A p_j) p_j,
+    and the step is alpha_i = p_i^T r_i / p_i^T A p_i.  For a fixed symmetric positive
+    definite M it produces the PCG iterates (exact arithmetic).  SolveInfo.terms
+    holds alpha_i p_i^T r_i.  Returns (x, SolveInfo)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - apply_a(x) if x0 is not None else b.copy()
+    bnorm = math.sqrt(float(np.vdot(b, b)))
+    hist = [math.sqrt(float(np.vdot(r, r))) / bnorm]
+    terms = []
+    iters = [x.copy()] if keep_iterates else None
+    converged = hist[0] <= tol
+    kept = []   # (p_j, A p_j, p_j^T A p_j) of the last `window` steps
+    k = 0
+    p = apply_m(r)
+    while not converged and k < maxit:
+        q = apply_a(p)
+        pq = float(np.vdot(p, q))
+        alpha = float(np.vdot(p, r)) / pq
+        terms.append(alpha * float(np.vdot(p, r)))
+        x = x + alpha * p
+        r = r - alpha * q
+        kept.append((p, q, pq))
+        if len(kept) > window:
+            kept.pop(0)
+        k += 1
+        hist.append(math.sqrt(float(np.vdot(r, r))) / bnorm)
+        if keep_iterates:
+            iters.append(x.copy())
+        if hist[-1] <= tol:
+            converged = True
+            break
+        z = apply_m(r)
+        p = z.copy()
+        for pj, qj, pqj in kept:
+            p = p - (float(np.vdot(z, qj)) / pqj) * pj
     return x, SolveInfo(k, converged, hist, terms, iters)
 
 

@@ -46,7 +46,7 @@ class SolveOpts(C.Structure):
                 ("use_graph", C.c_int32), ("x0_given", C.c_int32), ("cg_f32", C.c_int32),
                 ("resid_replace", C.c_int32), ("flexible", C.c_int32), ("snapshot_every", C.c_int32),
                 ("snapshot_max", C.c_int32), ("batch_width", C.c_int32), ("skip_true_resid", C.c_int32),
-                ("resume", C.c_int32)]
+                ("resume", C.c_int32), ("fcg_window", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -327,11 +327,11 @@ def cmm_precon_clamped(pc):
 
 def cmm_solve(op, pc, b, x, tol=1e-6, maxit=500, check_every=10, use_graph=True, x0_given=False,
               resid_hist=None, anorm_terms=None, cg_f32=False, resid_replace=0, flexible=False,
-              snapshots=None, snapshot_every=1, true_resid=True, resume=False):
+              snapshots=None, snapshot_every=1, true_resid=True, resume=False, window=1):
     snap_max = 0 if snapshots is None else snapshots.shape[0]
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1 if use_graph else 0, 1 if x0_given else 0,
                      1 if cg_f32 else 0, int(resid_replace), 1 if flexible else 0, int(snapshot_every),
-                     int(snap_max), 0, 0 if true_resid else 1, 1 if resume else 0)
+                     int(snap_max), 0, 0 if true_resid else 1, 1 if resume else 0, int(window))
     info = SolveInfo()
     _check(_lib.cmm_solve(op, pc, _dev(b, name="b"), _dev(x, name="x"), C.byref(opts),
                           _dev(resid_hist, numel=None, name="resid_hist"),
@@ -348,7 +348,7 @@ def cmm_solve_host(op, pc, b_host, x_host, tol=1e-6, maxit=500, check_every=10, 
         if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
             raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 1 if x0_given else 0, 0, 0, 0, 0, 0, 0,
-                     0 if true_resid else 1, 1 if resume else 0)
+                     0 if true_resid else 1, 1 if resume else 0, 1)
     info = SolveInfo()
     _check(_lib.cmm_solve_host(op, pc, b_host.ctypes.data, x_host.ctypes.data, C.byref(opts), C.byref(info)))
     return info
@@ -445,7 +445,7 @@ def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f3
     n = len(ops)
     arr = lambda items: (C.c_void_p * n)(*[C.c_void_p(v if isinstance(v, int) else v.value) for v in items])
     opts = SolveOpts(float(tol), int(maxit), int(check_every), 1, 0, 1 if cg_f32 else 0, 0, 1 if flexible else 0,
-                     0, 0, int(width), 0 if true_resid else 1, 0)
+                     0, 0, int(width), 0 if true_resid else 1, 0, 1)
     infos = (SolveInfo * n)()
     _check(_lib.cmm_batch_solve(n, arr(ops), arr(pcs), arr([t.data_ptr() for t in bs]),
                                 arr([t.data_ptr() for t in xs]), C.byref(opts), infos))
@@ -619,7 +619,7 @@ class UNet:
 
 
 def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=10, use_graph=True,
-          history=False, cg_f32=False, resid_replace=0, flexible=False, true_resid=True):
+          history=False, cg_f32=False, resid_replace=0, flexible=False, true_resid=True, window=1):
     """PCG on A x = b; returns (x, info, resid_hist, anorm_terms).  info.rel_resid is
     the recursive ||r|| / ||b||; info.true_rel_resid recomputes ||b - A x|| / ||b||
     from the returned x (one more application of A; -1 with true_resid=False)."""
@@ -629,5 +629,5 @@ def solve(op: Operator, pc: Precon, b, x=None, tol=1e-6, maxit=500, check_every=
     hist = torch.zeros(maxit + 1, dtype=torch.float64, device=b.device) if history else None
     terms = torch.zeros(max(maxit, 1), dtype=torch.float64, device=b.device) if history else None
     info = cmm_solve(op.h, pc.h, b, x, tol, maxit, check_every, use_graph, x0_given, hist, terms,
-                     cg_f32, resid_replace, flexible, true_resid=true_resid)
+                     cg_f32, resid_replace, flexible, true_resid=true_resid, window=window)
     return x, info, hist, terms

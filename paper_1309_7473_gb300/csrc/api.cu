@@ -401,6 +401,7 @@ static void free_op(cmm_op* op) {
   dfree(op->sol);
   dfree(op->sol_state);
   dfree(op->host_bx);
+  dfree(op->fcg);
   cmm_ctx* c = op->ctx;
   cmm_pointing* pt = op->pt;
   cmm_noise* nz = op->nz;
@@ -1126,16 +1127,33 @@ struct Snap {
   int every = 0, max = 0;
 };
 
+// Rings of truncated flexible CG, FCG(m): P, Q [win][n] and the window partials
+struct Fcg {
+  double *P = nullptr, *Q = nullptr, *wpart = nullptr;
+  int win = 1;
+};
+
 static int solve_iteration(cmm_op* op, cmm_precon* pc, double* x, const SolveBufs& v, SolverDev* dst,
-                           double* hist, double* anorm, bool flexible, const Snap& snap = Snap()) {
+                           double* hist, double* anorm, bool flexible, const Snap& snap = Snap(),
+                           const Fcg& fcg = Fcg()) {
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   cudaStream_t st = op->ctx->stream;
+  const bool ring = fcg.win > 1;
   CMM_TRY(apply_A_dev(op, v.p, v.q));
   CMM_TRY(launch_dot_partial_cg(v.p, v.q, n, dst, v.p1, st));
   CMM_TRY(launch_solver_alpha(dst, v.p1, anorm, st));
-  CMM_TRY(launch_update_xr(x, v.r, flexible ? v.r_old : nullptr, v.p, v.q, n, dst, v.p2, st));
+  if (ring) CMM_TRY(launch_update_xr_ring(x, v.r, v.p, v.q, n, dst, fcg.P, fcg.Q, v.p2, st));
+  else CMM_TRY(launch_update_xr(x, v.r, flexible ? v.r_old : nullptr, v.p, v.q, n, dst, v.p2, st));
   CMM_TRY(launch_solver_check(dst, v.p2, hist, st));
   if (snap.buf) CMM_TRY(launch_snapshot(x, v.r, n, dst, snap.every, snap.max, snap.buf, st));
+  if (ring) {
+    // z = M r, then p = z made A-conjugate to the kept directions, rho = p^T r
+    CMM_TRY(precon_step(op, pc, v, dst, false));
+    CMM_TRY(launch_window_dots(v.z, fcg.Q, n, dst, fcg.wpart, st));
+    CMM_TRY(launch_window_beta(dst, fcg.wpart, st));
+    CMM_TRY(launch_update_p_window(v.p, v.z, fcg.P, v.r, n, dst, v.p2, st));
+    return launch_solver_rho_pr(dst, v.p2, st);
+  }
   CMM_TRY(precon_step(op, pc, v, dst, flexible));
   CMM_TRY(launch_solver_beta(dst, v.p1, flexible ? v.p3 : nullptr, st));
   CMM_TRY(launch_update_p(v.p, v.z, n, dst, st));
@@ -1211,14 +1229,33 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   if (pc->op != op) return fail(CMM_ERR_ARG, "preconditioner belongs to another operator");
   if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace < 0) return fail(CMM_ERR_ARG, "bad solve options");
   if (opts->resume && !op->resume_ready) return fail(CMM_ERR_ARG, "resume without a loaded solver state");
+  if (opts->fcg_window < 0 || opts->fcg_window > kMaxWin) return fail(CMM_ERR_ARG, "fcg_window must be 0..8");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   const auto t0 = std::chrono::steady_clock::now();
   cmm_ctx* c = op->ctx;
   cudaStream_t st = c->stream;
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   const bool flexible = opts->flexible != 0 || pc->kind == CMM_PRECON_CIRC_LEARNED;
+  Fcg fcg;
+  fcg.win = flexible ? std::max(1, (int)opts->fcg_window) : 1;
+  if (fcg.win > 1 && (opts->resume || opts->resid_replace > 0))
+    return fail(CMM_ERR_UNSUPPORTED, "fcg_window > 1 with resume or residual replacement");
   if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (5 * n + 3 * kRedBlocks)));
   if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
+  if (fcg.win > 1) {
+    const int64_t need = 2 * (int64_t)fcg.win * n + (int64_t)fcg.win * kRedBlocks;
+    if (op->fcg_doubles < need) {
+      CMM_CUDA(cudaStreamSynchronize(op->ctx->stream));
+      dfree(op->fcg);
+      op->fcg = nullptr;
+      op->fcg_doubles = 0;
+      CMM_TRY(dalloc(&op->fcg, sizeof(double) * need));
+      op->fcg_doubles = need;
+    }
+    fcg.P = op->fcg;
+    fcg.Q = op->fcg + (int64_t)fcg.win * n;
+    fcg.wpart = op->fcg + 2 * (int64_t)fcg.win * n;
+  }
   SolveBufs v;
   v.r = op->sol;
   v.z = v.r + n;
@@ -1236,6 +1273,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
   h.tol = opts->tol;
   h.maxit = opts->maxit;
   h.f32 = opts->cg_f32 ? 1 : 0;
+  h.win = fcg.win;
   if (!std::isfinite(bnorm2)) {
     // a non-finite right-hand side: no iteration is meaningful
     h.done = 1;
@@ -1304,7 +1342,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
       CMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       int s2 = CMM_OK;
       for (int i = 0; i < per && s2 == CMM_OK; ++i)
-        s2 = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap);
+        s2 = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap, fcg);
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       if (s2 != CMM_OK) return s2;
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
@@ -1324,7 +1362,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
       }
     } else {
       for (int i = 0; i < per && status == CMM_OK; ++i)
-        status = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap);
+        status = solve_iteration(op, pc, x, v, dst, resid_hist, anorm_terms, flexible, snap, fcg);
       if (status != CMM_OK) break;
     }
     launched += per;
@@ -1474,8 +1512,8 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
     for (int j = 0; j < i; ++j)
       if (ops[j] == ops[i]) return fail(CMM_ERR_ARG, "an operator appears twice in the batch");
   }
-  if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace != 0)
-    return fail(CMM_ERR_ARG, "bad batch solve options (residual replacement is per solve)");
+  if (opts->maxit < 0 || !(opts->tol >= 0) || opts->resid_replace != 0 || opts->fcg_window > 1)
+    return fail(CMM_ERR_ARG, "bad batch solve options (residual replacement and fcg_window are per solve)");
   CMM_CUDA(cudaSetDevice(ops[0]->ctx->device));
   for (int i = 0; i < n; ++i) CMM_TRY(op_sync_corr(ops[i]));
   const auto t0 = std::chrono::steady_clock::now();

@@ -162,6 +162,8 @@ struct cmm_op {
   double* sol = nullptr;       // PCG vectors r, z, p, q, r_old and reduction partials
   void* sol_state = nullptr;   // PCG scalars (SolverDev)
   double* host_bx = nullptr;   // [2][ncomp*npix] device b and x of cmm_solve_host
+  double* fcg = nullptr;       // rings of truncated flexible CG (directions, A times them, partials)
+  int64_t fcg_doubles = 0;
   int resume_ready = 0;        // a solver state was loaded (cmm_solve_state_load)
   int resume_iter = 0;         // its iteration count, rho and relative residual
   double resume_rho = 0.0, resume_rel = 0.0;

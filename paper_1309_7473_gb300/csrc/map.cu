@@ -258,6 +258,7 @@ __global__ void k_solver_alpha(SolverDev* st, const double* __restrict__ partial
     }
     st->alpha = cg_round(st, st->rho / pq);
     if (anorm_terms) anorm_terms[st->iter] = st->alpha * st->rho;
+    if (st->win > 1) st->pq_ring[st->iter % st->win] = pq;
   }
 }
 
@@ -385,6 +386,113 @@ __global__ void k_solver_init(SolverDev* st, const double* __restrict__ partial_
     } else if (st->maxit <= 0) {
       st->done = 1;
     }
+  }
+}
+
+// ------------------------------------------------------------------ truncated flexible CG, FCG(m)
+// The last m = st->win directions p_j and q_j = A p_j live in rings P, Q ([m][n],
+// direction of iteration j in slot j mod m) with p_j^T q_j in st->pq_ring.  The new
+// direction is z made A-conjugate to them, p = z - sum_j (z^T q_j / p_j^T q_j) p_j,
+// and the step uses rho = p^T r (Notay's FCG).
+
+// x += alpha p; r -= alpha q; p and q into ring slot iter mod m; partials of r^T r
+__global__ void k_update_xr_ring(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                 const double* __restrict__ q, long long n, const SolverDev* st,
+                                 double* __restrict__ P, double* __restrict__ Q, double* __restrict__ partial) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const long long slot = st->iter % st->win;
+  double* Ps = P + slot * n;
+  double* Qs = Q + slot * n;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double pi = p[i], qi = q[i];
+    x[i] = cg_round(st, x[i] + alpha * pi);
+    const double ri = cg_round(st, r[i] - alpha * qi);
+    r[i] = ri;
+    Ps[i] = pi;
+    Qs[i] = qi;
+    acc = cg_acc(st, acc, ri * ri);
+  }
+  block_sum_store(acc, partial);
+}
+
+// partials of z^T Q_j for the kept directions j < min(iter, m): wpart[j][block]
+__global__ void k_window_dots(const double* __restrict__ z, const double* __restrict__ Q, long long n,
+                              const SolverDev* st, double* __restrict__ wpart) {
+  if (st->done) return;
+  const int nv = min(st->iter, st->win);
+  double acc[kMaxWin];
+#pragma unroll
+  for (int j = 0; j < kMaxWin; ++j) acc[j] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+#pragma unroll
+    for (int j = 0; j < kMaxWin; ++j)
+      if (j < nv) acc[j] = cg_acc(st, acc[j], zi * Q[j * n + i]);
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxWin; ++j) {
+    if (j < nv) {
+      __syncthreads();
+      block_sum_store(acc[j], wpart + (long long)j * kRedBlocks);
+    }
+  }
+}
+
+// beta_j = -z^T q_j / p_j^T q_j
+__global__ void k_window_beta(SolverDev* st, const double* __restrict__ wpart) {
+  if (st->done) return;
+  const int nv = min(st->iter, st->win);
+  for (int j = 0; j < nv; ++j) {
+    const double zq = block_sum_all(wpart + (long long)j * kRedBlocks, kRedBlocks);
+    if (threadIdx.x == 0) {
+      const double b = -zq / st->pq_ring[j];
+      st->beta_w[j] = cg_round(st, b);
+      if (!isfinite(b)) {
+        st->status = CMM_ERR_BREAKDOWN;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// p = z + sum_j beta_j P_j; partials of p^T r
+__global__ void k_update_p_window(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ P,
+                                  const double* __restrict__ r, long long n, const SolverDev* st,
+                                  double* __restrict__ partial) {
+  if (st->done) return;
+  const int nv = min(st->iter, st->win);
+  double beta[kMaxWin];
+#pragma unroll
+  for (int j = 0; j < kMaxWin; ++j) beta[j] = j < nv ? st->beta_w[j] : 0.0;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = z[i];
+#pragma unroll
+    for (int j = 0; j < kMaxWin; ++j)
+      if (j < nv) v += beta[j] * P[j * n + i];
+    v = cg_round(st, v);
+    p[i] = v;
+    acc = cg_acc(st, acc, v * r[i]);
+  }
+  block_sum_store(acc, partial);
+}
+
+// rho = p^T r, the numerator of the next step
+__global__ void k_solver_rho_pr(SolverDev* st, const double* __restrict__ partial) {
+  if (st->done) return;
+  const double pr = block_sum_all(partial, kRedBlocks);
+  if (threadIdx.x == 0) {
+    if (!(pr > 0.0) || !isfinite(pr)) {
+      st->status = CMM_ERR_BREAKDOWN;
+      st->done = 1;
+      return;
+    }
+    st->rho = cg_round(st, pr);
   }
 }
 
@@ -830,6 +938,39 @@ int launch_solver_beta(SolverDev* st, const double* p_rz, const double* p_flex, 
 
 int launch_update_p(double* p, const double* z, int64_t n, const SolverDev* st, cudaStream_t s) {
   k_update_p<<<grid_for(n), 256, 0, s>>>(p, z, n, st);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_update_xr_ring(double* x, double* r, const double* p, const double* q, int64_t n, const SolverDev* st,
+                          double* P, double* Q, double* partial, cudaStream_t s) {
+  k_update_xr_ring<<<kRedBlocks, 256, 0, s>>>(x, r, p, q, n, st, P, Q, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_window_dots(const double* z, const double* Q, int64_t n, const SolverDev* st, double* wpart,
+                       cudaStream_t s) {
+  k_window_dots<<<kRedBlocks, 256, 0, s>>>(z, Q, n, st, wpart);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_window_beta(SolverDev* st, const double* wpart, cudaStream_t s) {
+  k_window_beta<<<1, 256, 0, s>>>(st, wpart);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_update_p_window(double* p, const double* z, const double* P, const double* r, int64_t n,
+                           const SolverDev* st, double* partial, cudaStream_t s) {
+  k_update_p_window<<<kRedBlocks, 256, 0, s>>>(p, z, P, r, n, st, partial);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
+int launch_solver_rho_pr(SolverDev* st, const double* partial, cudaStream_t s) {
+  k_solver_rho_pr<<<1, 256, 0, s>>>(st, partial);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }

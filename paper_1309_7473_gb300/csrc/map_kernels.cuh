@@ -8,10 +8,15 @@ namespace cmm {
 
 // Scalars of one PCG solve, kept in device memory so that an iteration can be
 // replayed as a CUDA graph; every kernel of the loop returns early once `done`.
+constexpr int kMaxWin = 8;   // directions kept by truncated flexible CG, FCG(m)
+
 struct SolverDev {
   double rho, pq, alpha, beta, rr, rel, bnorm2, tol;
   int iter, maxit, done, status;
   int f32;        // FP32 CG vectors and scalars
+  int win;        // FCG(m): m > 1 directions kept (ring slot j mod m); <= 1: PCG / Polak-Ribiere
+  double pq_ring[kMaxWin];   // p_j^T A p_j of the kept directions
+  double beta_w[kMaxWin];    // coefficients of the new direction on them
 };
 
 struct Fft2Plan {
@@ -76,6 +81,16 @@ int launch_snapshot(const double* x, const double* r, int64_t n, const SolverDev
 int launch_solver_check(SolverDev* st, const double* partial, double* hist, cudaStream_t s);
 int launch_solver_beta(SolverDev* st, const double* p_rz, const double* p_flex, cudaStream_t s);
 int launch_update_p(double* p, const double* z, int64_t n, const SolverDev* st, cudaStream_t s);
+// FCG(m): x, r update storing p and q = A p in the ring; z^T Q_j partials; the
+// coefficients; p = z + sum_j beta_j P_j with the partials of p^T r; rho = p^T r.
+int launch_update_xr_ring(double* x, double* r, const double* p, const double* q, int64_t n, const SolverDev* st,
+                          double* P, double* Q, double* partial, cudaStream_t s);
+int launch_window_dots(const double* z, const double* Q, int64_t n, const SolverDev* st, double* wpart,
+                       cudaStream_t s);
+int launch_window_beta(SolverDev* st, const double* wpart, cudaStream_t s);
+int launch_update_p_window(double* p, const double* z, const double* P, const double* r, int64_t n,
+                           const SolverDev* st, double* partial, cudaStream_t s);
+int launch_solver_rho_pr(SolverDev* st, const double* partial, cudaStream_t s);
 
 template <typename T> int fft2_plan_init(Fft2Plan& p, int ny, int nx);
 template <typename T> int fft2(const Fft2Plan& p, V2<T>* data, int nplanes, int sign, const int* done, cudaStream_t s);

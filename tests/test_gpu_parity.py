@@ -574,6 +574,28 @@ def test_flexible_cg_matches_pcg_gpu(cmm, ctx, tiny_solution):
     assert rel(host(x1), x_ref) < 1e-6
 
 
+@pytest.mark.parametrize("window", [2, 8])
+def test_fcg_window_matches_oracle(cmm, ctx, tiny_solution, window):
+    """Truncated flexible CG, FCG(m), with a fixed preconditioner (binned, FP64): the
+    same residual history and solution as the oracle's FCG(m), which itself follows
+    PCG for a fixed preconditioner."""
+    scan, noise, d, b_ref, x_ref, _ = tiny_solution
+    op = cmm.Operator(ctx, scan, noise, precision=0)
+    oop = om.make_operator(scan, noise)
+    pc = cmm.Precon(op, cmm.PRECON_BINNED)
+    x, info, hist, _ = cmm.solve(op, pc, dev(b_ref), tol=1e-9, maxit=600, flexible=True, window=window,
+                                 history=True)
+    xo, io = om.pcg(lambda v: om.apply_A(oop, v), om.BlockPrecon(oop), b_ref, tol=1e-9, maxit=600,
+                    flexible=True, window=window)
+    assert info.status == 0 and io.converged
+    assert abs(info.iterations - io.iterations) <= 1
+    np.testing.assert_allclose(host(hist)[:15], io.rel_resid[:15], rtol=1e-6)
+    assert rel(host(x), xo) < 1e-7
+    assert max(stokes_errors(host(x), x_ref, oop.mask)) < 1e-5
+    with pytest.raises(cmm.CmmError):
+        cmm.solve(op, pc, dev(b_ref), tol=1e-9, maxit=10, flexible=True, window=9)
+
+
 # ---------------------------------------------------------------- batched solves and tuning (uneven problems)
 
 def test_batch_solve_matches_individual_solves(cmm):

@@ -320,6 +320,55 @@ def test_flexible_cg_equals_pcg_for_fixed_preconditioner(tiny):
     np.testing.assert_allclose(x1, x2, atol=1e-8 * np.abs(x1).max())
 
 
+def test_fcg_window_equals_pcg_for_fixed_preconditioner(tiny):
+    """Truncated flexible CG with a fixed SPD preconditioner follows the PCG
+    iterates (exact arithmetic): same residual history and solution."""
+    b = om.apply_A(tiny, gen.sky_map(8, 8, cfg=107))
+    mb = om.BlockPrecon(tiny)
+    x1, i1 = om.pcg(lambda v: om.apply_A(tiny, v), mb, b, tol=1e-10)
+    for m in (2, 5, 50):
+        x2, i2 = om.pcg(lambda v: om.apply_A(tiny, v), mb, b, tol=1e-10, flexible=True, window=m)
+        assert abs(i1.iterations - i2.iterations) <= 1
+        np.testing.assert_allclose(i2.rel_resid[:12], i1.rel_resid[:12], rtol=1e-6)
+        np.testing.assert_allclose(x1, x2, atol=1e-8 * np.abs(x1).max())
+
+
+def test_fcg_keeps_window_directions_conjugate(tiny, tiny_dense):
+    """With a preconditioner that changes every iteration (M_B plus a positive
+    diagonal whose weight cycles), FCG(m) keeps each step direction d_i =
+    x_{i+1} - x_i A-conjugate to the previous m ones and the new residual
+    orthogonal to them, on the dense A; with m = 1 only to the last one."""
+    a, idx = tiny_dense
+    comp, pixs = idx
+    mb = om.BlockPrecon(tiny)
+    rng = np.random.default_rng(3)
+    diag = rng.uniform(0.5, 2.0, size=tiny.shape)
+    count = [0]
+
+    def varying(r):
+        count[0] += 1
+        return mb(r) + (0.2 + 0.15 * math.sin(1.7 * count[0])) * np.where(tiny.mask.reshape(tiny.shape[1:]), diag * r, 0)
+
+    b = om.apply_A(tiny, gen.sky_map(8, 8, cfg=108))
+    flat = lambda v: v.reshape(tiny.scan.ncomp, -1)[comp, pixs]
+    for m in (1, 4, 100):
+        count[0] = 0
+        _, info = om.pcg(lambda v: om.apply_A(tiny, v), varying, b, tol=1e-12, maxit=30, flexible=True,
+                         window=m, keep_iterates=True)
+        d = [flat(info.iterates[i + 1] - info.iterates[i]) for i in range(len(info.iterates) - 1)]
+        assert len(d) >= 10
+        for i in range(1, 10):
+            r = flat(b) - a @ flat(info.iterates[i + 1])
+            for j in range(max(0, i - m), i):
+                c = abs(d[i] @ a @ d[j]) / math.sqrt((d[i] @ a @ d[i]) * (d[j] @ a @ d[j]))
+                assert c < 1e-8, (m, i, j, c)
+            assert abs(r @ d[i]) < 1e-9 * np.linalg.norm(r) * np.linalg.norm(d[i])
+        # outside the window the conjugacy is lost (the preconditioner really varies)
+        if m == 1:
+            c02 = abs(d[3] @ a @ d[1]) / math.sqrt((d[3] @ a @ d[3]) * (d[1] @ a @ d[1]))
+            assert c02 > 1e-6
+
+
 # ---------------------------------------------------------------------------
 # preconditioners (Eq. 3-5, 7-13)
 # ---------------------------------------------------------------------------
