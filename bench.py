@@ -482,7 +482,8 @@ def run_learned(args):
     # on 20 held-out realisations: binned PCG, PCG(M_C), the corrected preconditioner
     # in flexible CG (Polak-Ribiere form and FCG(8)), and PCG(M_C) started from the
     # corrected preconditioner applied to b
-    forms = {"binned": [], "plain_mc": [], "learned_fpcg": [], "learned_fcg8": [], "learned_x0": []}
+    forms = {"binned": [], "plain_mc": [], "learned_fpcg": [], "learned_fcg8": [], "learned_x0": [],
+             "control_x0_mc": []}
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -499,10 +500,12 @@ def run_learned(args):
         forms["learned_fcg8"].append(timed(lambda: cmm.solve(op, pcl, b, tol=1e-6, maxit=1000, flexible=True,
                                                              window=8)[1]))
 
-        def from_x0():
-            x0 = pcl.apply(b)
+        def from_x0(p0):
+            x0 = p0.apply(b)
             return cmm.solve(op, pc, b, x=x0, tol=1e-6, maxit=1000)[1]
-        forms["learned_x0"].append(timed(from_x0))
+        forms["learned_x0"].append(timed(lambda: from_x0(pcl)))
+        # control: the same start without the network, x0 = M_C b
+        forms["control_x0_mc"].append(timed(lambda: from_x0(pc)))
     summary = {k: {"iterations_mean": sum(r[0] for r in v) / len(v), "seconds_mean": sum(r[1] for r in v) / len(v),
                    "all_converged": all(r[2] == 0 for r in v)} for k, v in forms.items()}
     n = len(forms["plain_mc"])
@@ -625,8 +628,9 @@ CG_LAUNCHES = 7
 CIRC_LAUNCHES = 12
 
 
-# sources of the three A-application kernels: the traffic record holds for them only
-TRAFFIC_SOURCES = ("tod_fast.cu", "fft_reg.cuh", "fft.cuh", "tod_common.cuh", "common.cuh")
+# sources of the three A-application kernels of the two-detector path: the traffic
+# record holds for them only
+TRAFFIC_SOURCES = ("tod_pair.cu", "tod_fast.cuh", "fft_reg.cuh", "fft.cuh", "tod_common.cuh", "common.cuh")
 
 
 def kernel_sources_digest():

@@ -227,7 +227,8 @@ int cmm_op_set_pixel_cache(cmm_op* op, int32_t enable);
  * a, b = (w_1 +- w_2) / 2.  enable == 0 selects the one-detector packing (even
  * and odd samples as one complex sequence of n_samp / 2 points), which also serves
  * correlated noise, the right-hand side and operators above the FP32 hit limit.
- * Results agree to FP32 rounding either way; waits for the operator's stream. */
+ * Results agree to the rounding of the spectrum storage (FP32 or BF16) either way;
+ * waits for the operator's stream. */
 int cmm_op_set_pair_packing(cmm_op* op, int32_t enable);
 /* m_out = A m_in (Eq. 2).  device double [ncomp][ny][nx] each; must not alias. */
 int cmm_apply_A(cmm_op* op, const double* m_in, double* m_out);
@@ -403,7 +404,7 @@ int cmm_spectra(cmm_ctx* ctx, int32_t ny, int32_t nx, double pix_rad, int32_t nm
  * assigned largest first to the least loaded lane, one after another within a
  * lane), each solve on the stream of its own context (give each operator its own
  * context for the lanes to overlap).  Automatic width: 1 when the solves average
- * 10^7 samples or more (each alone fills the GPU, and concurrent ones only share
+ * 10^8 samples or more (each alone fills the GPU, and concurrent ones only share
  * the L2 their maps live in), else up to 8.  A solve that has converged keeps
  * returning early inside the graph.  opts as in
  * cmm_solve (resid_replace must be 0); infos[i] receives each solve's result, its

@@ -37,6 +37,29 @@
 
 namespace cmm {
 
+// Tuning knobs of this path (compile-time; the defaults are the measured best).
+#ifndef CMM_PAIR_SPL
+#define CMM_PAIR_SPL 8     // consecutive samples per lane in the binning
+#endif
+#ifndef CMM_PAIR_ROT
+#define CMM_PAIR_ROT 1     // forward pass: 0 = (cos 2phi, sin 2phi) from the FP32 table, 1 = from the boresight record
+#endif
+#ifndef CMM_PAIR_ROT_INV
+#define CMM_PAIR_ROT_INV 0   // binning: 0 = from the FP32 table, 1 = from the boresight record, staged beside the pixels
+#endif
+#ifndef CMM_PAIR_FILTER_THREADS_PER_SM
+#define CMM_PAIR_FILTER_THREADS_PER_SM 1024
+#endif
+
+// (cos 2phi, sin 2phi) of the fixed-point pair (c, s) of a boresight record, in FP32:
+// (c^2 - s^2, 2 c s) / (c^2 + s^2), the integers converted exactly on the FP32 pipe
+__device__ __forceinline__ float2 rot2_of_bore(const int4 b) {
+  const float cf = small_int_to_float(b.z + 32768) - 32768.0f;
+  const float sf = small_int_to_float(b.w + 32768) - 32768.0f;
+  const float inv = __fdividef(1.0f, fmaf(cf, cf, sf * sf));
+  return make_float2((cf - sf) * (cf + sf) * inv, 2.0f * cf * sf * inv);
+}
+
 // w_d at frequency index kf (0 <= kf <= n_t / 2): the detector's table, else the law
 __device__ __forceinline__ float pair_weight(const TodArgs& a, int d, const float4 cf, int kf) {
   if (a.wtab) return __ldg(reinterpret_cast<const float*>(a.wtab) + (size_t)d * (a.n_t / 2 + 1) + kf);
@@ -77,15 +100,17 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB) k_pai
   for (int e = 0; e < kE; ++e) {
     const int t = c + (i + e * TPC) * a.C;
     int p1, p2;
+    float2 r2 = make_float2(0.f, 0.f);
     if constexpr (CACHED) {
       p1 = __ldcs(a.pix + (size_t)d1 * a.n_t + t);
       p2 = __ldcs(a.pix + (size_t)d2 * a.n_t + t);
+      if (NC == 3) r2 = __ldg(a.rot2 + t);
     } else {
       const int4 b = __ldg(a.bore + t);
       p1 = pixel_fast<PERIODIC>(b, off1, a.ny, a.nx, npix);
       p2 = pixel_fast<PERIODIC>(b, off2, a.ny, a.nx, npix);
+      if (NC == 3) r2 = CMM_PAIR_ROT ? rot2_of_bore(b) : __ldg(a.rot2 + t);
     }
-    const float2 r2 = NC == 3 ? __ldg(a.rot2 + t) : make_float2(0.f, 0.f);
     const float v1 = pair_project<NC>(a, p1, pol1, r2);
     const float v2 = pair_project<NC>(a, p2, pol2, r2);
     x[e] = make_float2(v1, two ? v2 : 0.f);
@@ -107,7 +132,7 @@ template <int C, int E> struct PairFilterShape {
   static constexpr int TPR = C / E;
   static constexpr int THREADS = 2 * TPR > 256 ? 2 * TPR : 256;
   static constexpr int ROWS = THREADS / TPR;
-  static constexpr int MINB = THREADS >= 1024 ? 1 : 1024 / THREADS;   // 64 registers
+  static constexpr int MINB = THREADS >= CMM_PAIR_FILTER_THREADS_PER_SM ? 1 : CMM_PAIR_FILTER_THREADS_PER_SM / THREADS;
 };
 
 template <typename S, int E, int... RC>
@@ -207,9 +232,16 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   constexpr int J = ColShape<R>::J;
   constexpr int NT = ColShape<R>::THREADS;
   constexpr int BS = J + 2;    // row stride of the binning tile (the pad spreads rows over the banks)
-  constexpr int LPR = J / 8;   // lanes per row: 8 consecutive samples each
-  constexpr int RPP = NT / LPR;   // rows per binning pass
-  static_assert(LPR >= 1 && (RPP * J) % NT == 0, "binning layout");
+  constexpr int SPL = CMM_PAIR_SPL;   // consecutive samples per lane
+  constexpr int LPR = J / SPL;        // lanes per row
+  constexpr int RPP = NT / LPR;       // rows per binning pass
+  // Pixel staging: row stride PS ints; a lane's 8 pixels are two 16-byte chunks
+  // interleaved with its row neighbour's (chunk h of lane bq at word 8h + 4bq of a
+  // 16-sample group), so that the eight lanes of a quarter-warp load hit eight
+  // distinct 4-bank groups (PS = 24 words = 8 mod 32 shifts consecutive rows).
+  constexpr int PS = J + 8;
+  constexpr int RS = J + 2;   // row stride (complex) of the staged rotations
+  static_assert(SPL == 8 && LPR >= 1 && RPP <= R && R % RPP == 0 && (RPP * J) % NT == 0, "binning layout");
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
   const int cl = threadIdx.x % J;
@@ -238,10 +270,13 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   const float2* pol = reinterpret_cast<const float2*>(a.pol);
   const float2 pol1 = pol[d1], pol2 = pol[d2];
   const int2 off1 = a.det_off[d1], off2 = a.det_off[d2];
-  int* pst = reinterpret_cast<int*>(smf + R * BS);   // pixels of one pass: [detector][RPP][J]
+  int* pst = reinterpret_cast<int*>(smf + R * BS);   // pixels of one pass: [detector][RPP][PS]
+  float2* rst = reinterpret_cast<float2*>(pst + 2 * RPP * PS);   // rotations of one pass: [RPP][RS]
+  const float4* smf4 = reinterpret_cast<const float4*>(smf);
+  constexpr bool ROT_STAGED = CMM_PAIR_ROT_INV && !CACHED && NC == 3;
   for (int kr0 = 0; kr0 < R; kr0 += RPP) {
     const int kr = kr0 + br;
-    const int tq = c0 + 8 * bq + kr * a.C;   // the lane's first sample
+    const int tq = c0 + SPL * bq + kr * a.C;   // the lane's first sample
     if constexpr (!CACHED) {
       // pixels of both detectors for the pass's RPP x J samples, lanes on
       // consecutive samples (coalesced boresight reads)
@@ -250,43 +285,51 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
         const int sidx = threadIdx.x + k * NT;
         const int rr = sidx / J, col = sidx % J;
         const int4 b = __ldg(a.bore + c0 + col + (kr0 + rr) * a.C);
-        pst[sidx] = pixel_fast<PERIODIC>(b, off1, a.ny, a.nx, npix);
-        pst[RPP * J + sidx] = pixel_fast<PERIODIC>(b, off2, a.ny, a.nx, npix);
+        // column col = 16 g + 8 bq + 4 h + w of the row goes to word 16 g + 8 h + 4 bq + w
+        const int sw = (col & ~15) | ((col & 4) << 1) | ((col & 8) >> 1) | (col & 3);
+        pst[rr * PS + sw] = pixel_fast<PERIODIC>(b, off1, a.ny, a.nx, npix);
+        pst[(RPP + rr) * PS + sw] = pixel_fast<PERIODIC>(b, off2, a.ny, a.nx, npix);
+        if constexpr (ROT_STAGED) rst[rr * RS + col] = rot2_of_bore(b);
       }
       __syncthreads();
     }
+    const int t8 = tq;
     float2 r2[8];
     if (NC == 3) {
 #pragma unroll
       for (int k = 0; k < 8; k += 2) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
+        const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
+                                    : __ldg(reinterpret_cast<const float4*>(a.rot2 + t8 + k));
         r2[k] = make_float2(v.x, v.y);
         r2[k + 1] = make_float2(v.z, v.w);
       }
     }
-    const float4* tile = reinterpret_cast<const float4*>(smf + kr * BS + 8 * bq);
+    // the lane's 8 filtered samples of both detectors (real part: d1, imaginary: d2)
+    float4 yv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) yv[j] = smf4[(kr * BS + 8 * bq) / 2 + j];
 #pragma unroll
     for (int dd = 0; dd < 2; ++dd) {
       if (dd == 1 && !two) break;
       int p[8];
       int4 P0, P1;
       if constexpr (CACHED) {
-        const int* pixd = a.pix + (size_t)(dd ? d2 : d1) * a.n_t + tq;
+        const int* pixd = a.pix + (size_t)(dd ? d2 : d1) * a.n_t + t8;
         P0 = __ldcs(reinterpret_cast<const int4*>(pixd));
         P1 = __ldcs(reinterpret_cast<const int4*>(pixd + 4));
       } else {
-        const int* ps = pst + dd * RPP * J + br * J + 8 * bq;
-        P0 = *reinterpret_cast<const int4*>(ps);
-        P1 = *reinterpret_cast<const int4*>(ps + 4);
+        // chunks h = 0, 1 of the lane's 8 pixels at words 16 (bq / 2) + 4 (bq % 2) + 8 h
+        const int4* ps = reinterpret_cast<const int4*>(pst + (dd * RPP + br) * PS + ((bq >> 1) << 4) + ((bq & 1) << 2));
+        P0 = ps[0];
+        P1 = ps[2];
       }
       p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
       p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
       float u[8], cc[8], ss[8];
 #pragma unroll
-      for (int k = 0; k < 8; k += 2) {
-        const float4 v = tile[k / 2];
-        u[k] = (dd ? v.y : v.x) * scale;
-        u[k + 1] = (dd ? v.w : v.z) * scale;
+      for (int j = 0; j < 4; ++j) {
+        u[2 * j] = (dd ? yv[j].y : yv[j].x) * scale;
+        u[2 * j + 1] = (dd ? yv[j].w : yv[j].z) * scale;
       }
       if (NC == 3) {
         const float2 pl = dd ? pol2 : pol1;
@@ -335,10 +378,13 @@ template <int NC, typename S, int R, bool PERIODIC, bool CACHED>
 static int run_pair_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, bool attr_only) {
   constexpr int J = ColShape<R>::J;
   constexpr int NT = ColShape<R>::THREADS;
-  // forward: FFT tile R x J complex.  inverse: binning tile R x (J + 2) complex, then
-  // the pixel staging of one pass, 2 x (threads / (J / 8)) x J ints
+  // forward: FFT tile R x J complex.  inverse: binning tile R x (J + 2) complex, the
+  // pixel staging of one pass (2 detectors x RPP rows x (J + 8) ints) and, when the
+  // rotation is staged, RPP rows x (J + 2) complex
+  constexpr int RPP = NT / (J / 8);   // rows per binning pass
   const int smem_f = (int)(sizeof(float2) * R * J);
-  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * (NT / (J / 8)) * J);
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * RPP * (J + 8) +
+                           (CMM_PAIR_ROT_INV ? sizeof(float2) * RPP * (J + 2) : 0));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_f));

@@ -67,6 +67,8 @@ def host(t):
 
 
 TOL = {0: 1e-10, 1: 1e-5, 2: 2e-2}
+# the same operator through two kernel paths (cached against on-the-fly pointing)
+SAME = {1: 1e-6, 2: 1e-4}
 
 
 def small(ncomp=3, periodic=False, cfg=201):
@@ -142,10 +144,12 @@ def test_handles_destroyed_out_of_order(cmm):
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("ncomp", [1, 3])
 def test_pixel_cache_same_result(cmm, ctx, prec, ncomp):
-    """A with the cached pixel indices equals A with on-the-fly pointing (same pixels,
-    same arithmetic; only the order of the FP32 atomic additions into the partial
-    map differs between runs, so agreement is to FP32 rounding), including samples
-    outside the map."""
+    """A with the cached pixel indices equals A with on-the-fly pointing (same pixels;
+    the forward pass on the fly forms (cos 2phi, sin 2phi) from the boresight record
+    in FP32 where the cached one reads the FP32 table, and the FP32 atomic additions
+    into the partial map come in another order), including samples outside the map:
+    agreement to FP32 rounding, or to BF16 rounding with BF16 spectrum storage (a
+    last-bit FP32 difference can move a value to the neighbouring BF16 number)."""
     scan = gen.small_scan(cfg=211, ny=20, nx=18, n_t=1 << 13, ncols=4, nrows=2, throw_px=40.0, ncomp=ncomp)
     noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=211)
     op = cmm.Operator(ctx, scan, noise, precision=prec, det_chunk=3)
@@ -153,9 +157,9 @@ def test_pixel_cache_same_result(cmm, ctx, prec, ncomp):
     y0 = host(op.apply(m))
     op.set_pixel_cache(True)
     y1 = host(op.apply(m))
-    assert rel(y1, y0) < 1e-6
+    assert rel(y1, y0) < SAME[prec]
     op.set_pixel_cache(False)
-    assert rel(host(op.apply(m)), y0) < 1e-6
+    assert rel(host(op.apply(m)), y0) < SAME[prec]
     oop = om.make_operator(scan, noise)
     assert rel(y1, om.apply_A(oop, gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=212)[0])) < TOL[prec]
 
@@ -246,7 +250,11 @@ def test_circulant_precon(cmm, ctx, prec, ncomp, taper):
     pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=taper if math.isfinite(taper) else 0.0)
     ref = om.CirculantPrecon(oop, taper_sigma=taper)
     r = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=208)[0]
-    assert rel(host(pc.apply(dev(r))), ref(r)) < (1e-9 if prec == 0 else 1e-4)
+    err = rel(host(pc.apply(dev(r))), ref(r))
+    print(f"circulant apply, precision {prec}, ncomp {ncomp}, taper {taper}: error {err:.2e}")
+    # FP32 operator: the map FFTs of the apply run in FP32 (perf mode) and the
+    # per-mode 3x3 inverse amplifies their rounding in the weakest modes
+    assert err < (1e-9 if prec == 0 else 1e-4)
     if prec == 0:
         assert pc.clamped() == ref.n_clamped
 
@@ -353,7 +361,7 @@ def test_apply_A_fast_path_sizes(cmm, ctx, log_nt, prec, pair):
     y = host(op.apply(dev(m)))
     assert rel(y, om.apply_A(oop, m)) < TOL[prec]
     op.set_pixel_cache(True)
-    assert rel(host(op.apply(dev(m))), y) < 1e-6
+    assert rel(host(op.apply(dev(m))), y) < SAME[prec]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
