@@ -252,9 +252,8 @@ def test_circulant_precon(cmm, ctx, prec, ncomp, taper):
     r = gen.random_maps(ncomp, scan.ny, scan.nx, 1, cfg=208)[0]
     err = rel(host(pc.apply(dev(r))), ref(r))
     print(f"circulant apply, precision {prec}, ncomp {ncomp}, taper {taper}: error {err:.2e}")
-    # FP32 operator: the map FFTs of the apply run in FP32 (perf mode) and the
-    # per-mode 3x3 inverse amplifies their rounding in the weakest modes
-    assert err < (1e-9 if prec == 0 else 1e-4)
+    # FP32 operator: the map FFTs of the apply run in FP32 (measured 1.7e-7 to 1.9e-7)
+    assert err < (1e-9 if prec == 0 else 1e-5)
     if prec == 0:
         assert pc.clamped() == ref.n_clamped
 
