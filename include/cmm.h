@@ -412,13 +412,18 @@ int cmm_spectra(cmm_ctx* ctx, int32_t ny, int32_t nx, double pix_rad, int32_t nm
  */
 int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const double* const* b,
                     double* const* x, const cmm_solve_opts* opts, cmm_solve_info* infos);
-/* Chooses the split N = R C of the time-ordered FFTs for this operator by timing
- * `reps` applications of A for every split the kernels support, keeps the fastest,
- * and remembers it for operators of the same (n_samp, n_det, precision, ncomp) in
- * this process and, if cache_path is not NULL, in that text file (read first,
- * appended to).  *chosen_logR (may be NULL) receives log2 R; *best_ms (may be NULL)
- * the time of one application, or -1 when the decision came from a cache. */
-int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, double* best_ms);
+/* Chooses how the time-ordered FFTs of this operator run, by timing `reps`
+ * applications of A for every candidate: the two-detector packing (where it
+ * applies; its split of n_samp is fixed) and every split N = R C of the
+ * one-detector packing that the kernels support.  Keeps the fastest and remembers
+ * it for operators of the same (n_samp, n_det, precision, ncomp) in this process
+ * and, if cache_path is not NULL, in that text file (read first, appended to; the
+ * last field is 0 for the two-detector packing, else log2 R).  *chosen_logR (may
+ * be NULL) receives log2 R of the chosen split, *chosen_pair (may be NULL) 1 for
+ * the two-detector packing, else 0; *best_ms (may be NULL) the time of one
+ * application, or -1 when the decision came from a cache. */
+int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, int32_t* chosen_pair,
+                 double* best_ms);
 
 #ifdef __cplusplus
 }

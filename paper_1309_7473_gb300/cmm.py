@@ -106,7 +106,7 @@ _SIGS = {
     "cmm_unet_loss_grad": [_vp, _i32, _vp, _vp, _vp, C.POINTER(_d)],
     "cmm_unet_train_step": [_vp, _i32, _vp, _vp, C.c_float, C.POINTER(_d)],
     "cmm_batch_solve": [_i32, _vp, _vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)],
-    "cmm_autotune": [_vp, _i32, C.c_char_p, C.POINTER(_i32), C.POINTER(_d)],
+    "cmm_autotune": [_vp, _i32, C.c_char_p, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_d)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -453,10 +453,13 @@ def cmm_batch_solve(ops, pcs, bs, xs, tol=1e-6, maxit=500, check_every=10, cg_f3
 
 
 def cmm_autotune(op, reps=3, cache_path=None):
+    """Returns (log2 R, two-detector packing chosen, ms per application or -1 from a cache)."""
     lr = C.c_int32()
+    pair = C.c_int32()
     ms = C.c_double()
-    _check(_lib.cmm_autotune(op, int(reps), cache_path.encode() if cache_path else None, C.byref(lr), C.byref(ms)))
-    return int(lr.value), float(ms.value)
+    _check(_lib.cmm_autotune(op, int(reps), cache_path.encode() if cache_path else None, C.byref(lr),
+                             C.byref(pair), C.byref(ms)))
+    return int(lr.value), bool(pair.value), float(ms.value)
 
 
 # ---------------------------------------------------------------- handle owners

@@ -1426,37 +1426,58 @@ struct TuneKey {
 std::vector<std::pair<TuneKey, int>> g_tune_cache;
 }  // namespace
 
-int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, double* best_ms) {
+// Decision values of the tuner (process cache and file): 0 = two-detector packing
+// (its split is fixed by n_samp), lr > 0 = one-detector packing with R = 2^lr.
+static int apply_decision(cmm_op* op, int v) {
+  if (v == 0) {
+    op->pair = 1;
+    return CMM_OK;
+  }
+  op->pair = 0;
+  return v != op->logR ? op_set_split(op, v) : CMM_OK;
+}
+
+static void report_decision(const cmm_op* op, int v, int32_t* chosen_logR, int32_t* chosen_pair) {
+  if (chosen_pair) *chosen_pair = v == 0 ? 1 : 0;
+  if (chosen_logR) *chosen_logR = v == 0 ? op->plogR : v;
+}
+
+int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chosen_logR, int32_t* chosen_pair,
+                 double* best_ms) {
   if (!op || reps <= 0) return fail(CMM_ERR_ARG, "bad argument");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   const TuneKey key{op->pt->n_t, op->pt->n_det, op->prec, op->pt->ncomp};
   const int logN = op->logR + op->logC;
+  const bool pair_ok = op->pR > 0 && op->tw_pair && op->nz->corr_r == 0 && op->pt->max_hits <= kF32HitLimit;
+  auto valid = [&](int v) { return (v == 0 && pair_ok) || (v > 0 && v < logN); };
   // cached decision (process-wide, then the optional file)
   for (auto& e : g_tune_cache)
-    if (e.first == key) {
-      if (e.second != op->logR) CMM_TRY(op_set_split(op, e.second));
-      if (chosen_logR) *chosen_logR = e.second;
+    if (e.first == key && valid(e.second)) {
+      CMM_TRY(apply_decision(op, e.second));
+      report_decision(op, e.second, chosen_logR, chosen_pair);
       if (best_ms) *best_ms = -1.0;
       return CMM_OK;
     }
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
       long long nt;
-      int nd, pr, nc, lr;
-      while (std::fscanf(f, "%lld %d %d %d %d", &nt, &nd, &pr, &nc, &lr) == 5)
-        if (TuneKey{nt, nd, pr, nc} == key && lr > 0 && lr < logN) {
+      int nd, pr, nc, v;
+      while (std::fscanf(f, "%lld %d %d %d %d", &nt, &nd, &pr, &nc, &v) == 5)
+        if (TuneKey{nt, nd, pr, nc} == key && valid(v)) {
           std::fclose(f);
-          g_tune_cache.push_back({key, lr});
-          if (lr != op->logR) CMM_TRY(op_set_split(op, lr));
-          if (chosen_logR) *chosen_logR = lr;
+          g_tune_cache.push_back({key, v});
+          CMM_TRY(apply_decision(op, v));
+          report_decision(op, v, chosen_logR, chosen_pair);
           if (best_ms) *best_ms = -1.0;
           return CMM_OK;
         }
       std::fclose(f);
     }
   }
-  // candidates: every split the fast kernels support, else the current one
+  // candidates: the two-detector packing where it applies, and every split of the
+  // one-detector packing that the fast kernels support (else the current one)
   std::vector<int> cand;
+  if (pair_ok) cand.push_back(0);
   for (int lr = 6; lr <= 8; ++lr)
     if (logN - lr >= 6 && logN - lr <= 12 && op->prec != CMM_PREC_F64) cand.push_back(lr);
   if (cand.empty()) cand.push_back(op->logR);
@@ -1468,8 +1489,8 @@ int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chos
   int best = cand[0];
   double best_t = 1e300;
   int s = CMM_OK;
-  for (int lr : cand) {
-    s = op_set_split(op, lr);
+  for (int v : cand) {
+    s = apply_decision(op, v);
     if (s != CMM_OK) break;
     s = apply_A_dev(op, op->tmp_a, op->tmp_b);   // warm-up
     if (s != CMM_OK) break;
@@ -1482,13 +1503,13 @@ int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chos
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms / reps < best_t) {
       best_t = ms / reps;
-      best = lr;
+      best = v;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != CMM_OK) return s;
-  if (best != op->logR) CMM_TRY(op_set_split(op, best));
+  CMM_TRY(apply_decision(op, best));
   g_tune_cache.push_back({key, best});
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
@@ -1496,7 +1517,7 @@ int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chos
       std::fclose(f);
     }
   }
-  if (chosen_logR) *chosen_logR = best;
+  report_decision(op, best, chosen_logR, chosen_pair);
   if (best_ms) *best_ms = best_t;
   return CMM_OK;
 }

@@ -651,20 +651,22 @@ def test_batch_solve_matches_individual_solves(cmm):
 
 
 def test_autotune_keeps_parity(cmm, ctx, tmp_path):
+    """The tuner times the two-detector packing and the one-detector splits, keeps the
+    fastest (parity holds either way) and remembers it in its file cache."""
     scan, noise = gen.tiny_patch()
     op = cmm.Operator(ctx, scan, noise, precision=1)
     oop = om.make_operator(scan, noise)
     m = gen.sky_map(scan.ny, scan.nx, cfg=1)
     ref = om.apply_A(oop, m)
     cache = str(tmp_path / "tune.txt")
-    lr, ms = cmm.cmm_autotune(op.h, 3, cache)
+    lr, pair, ms = cmm.cmm_autotune(op.h, 3, cache)
     assert 6 <= lr <= 8 and ms > 0
     assert rel(host(op.apply(dev(m))), ref) < TOL[1]
     op2 = cmm.Operator(ctx, scan, noise, precision=1)
-    lr2, ms2 = cmm.cmm_autotune(op2.h, 3, cache)
-    assert lr2 == lr and ms2 == -1.0
+    lr2, pair2, ms2 = cmm.cmm_autotune(op2.h, 3, cache)
+    assert (lr2, pair2) == (lr, pair) and ms2 == -1.0
     assert rel(host(op2.apply(dev(m))), ref) < TOL[1]
-    assert open(cache).read().split()[-1] == str(lr)
+    assert open(cache).read().split()[-1] == ("0" if pair else str(lr))
 
 
 # ---------------------------------------------------------------- tiled circulant (next row 3)
