@@ -326,6 +326,88 @@ __global__ void __launch_bounds__(128) k_conv3_wgrad_mma(const bf16* __restrict_
   if (threadIdx.x < 16 && blockIdx.y == 0 && o0 + (int)threadIdx.x < Cout) atomicAdd(gb + o0 + threadIdx.x, accb);
 }
 
+// Per-pixel channel GEMMs on the tensor cores: the 2x2 stride-2 transposed
+// convolution (TAPS = 4: out[b][o][2y+dy][2x+dx] = sum_i in[b][i][y][x] W[i][o][dy][dx]
+// + bias[o], BF16 out) and the 1x1 output convolution (TAPS = 1: out[b][o][p] =
+// sum_i W[o][i] in[b][i][p] + bias[o], FP32 out).  GEMM per tap: M = output
+// channels (MT x 16 per CTA), N = 128 pixels (four warps x four n8 tiles), K = input
+// channels, 16 per chunk; the pixel tile is staged once per chunk as [pixel][channel]
+// and reused by every tap.
+template <int TAPS, typename TOUT, int MT>
+__global__ void __launch_bounds__(128) k_pointwise_mma(const bf16* __restrict__ in, const bf16* __restrict__ w,
+                                                       const float* __restrict__ bias, TOUT* __restrict__ out,
+                                                       int Cin, int Cout, int H, int W, const int* done) {
+  if (stopped(done)) return;
+  constexpr int NP = 128;       // pixels per CTA
+  constexpr int MO = MT * 16;
+  __shared__ __align__(16) bf16 s_in[NP * kCP];
+  __shared__ __align__(16) bf16 s_w[TAPS * MO * kCP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int HW = H * W;
+  const int p0 = blockIdx.x * NP;
+  const int o0 = blockIdx.y * MO;
+  const int b = blockIdx.z;
+  float acc[TAPS][MT][4][4];
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t)
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[t][m][n][c] = 0.f;
+  for (int i0 = 0; i0 < Cin; i0 += 16) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * NP; e += 128) {
+      const int px = e % NP, ci = e / NP;
+      const int gi = i0 + ci, gp = p0 + px;
+      s_in[px * kCP + ci] = (gi < Cin && gp < HW) ? in[((long long)b * Cin + gi) * HW + gp] : __float2bfloat16_rn(0.f);
+    }
+    for (int e = threadIdx.x; e < TAPS * MO * 16; e += 128) {
+      const int ii = e % 16, r = e / 16, oo = r % MO, t = r / MO;
+      const int go = o0 + oo, gi = i0 + ii;
+      bf16 v = __float2bfloat16_rn(0.f);
+      if (go < Cout && gi < Cin) v = TAPS == 4 ? w[((long long)gi * Cout + go) * 4 + t] : w[(long long)go * Cin + gi];
+      s_w[(t * MO + oo) * kCP + ii] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const bf16* pb = s_in + (warp * 32 + n * 8 + g) * kCP + 2 * q;
+      const uint32_t b0 = lds32(pb), b1 = lds32(pb + 8);
+#pragma unroll
+      for (int t = 0; t < TAPS; ++t)
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          const bf16* pa = s_w + (t * MO + m * 16 + g) * kCP + 2 * q;
+          uint32_t a[4] = {lds32(pa), lds32(pa + 8 * kCP), lds32(pa + 8), lds32(pa + 8 * kCP + 8)};
+          mma_bf16_16816(acc[t][m][n], a, b0, b1);
+        }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t)
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int o = o0 + m * 16 + g + 8 * (c >> 1);
+          const int p = p0 + warp * 32 + n * 8 + 2 * q + (c & 1);
+          if (o >= Cout || p >= HW) continue;
+          const float v = acc[t][m][n][c] + bias[o];
+          if (TAPS == 4) {
+            const int y = p / W, x = p - (p / W) * W;
+            const int Y = 2 * y + (t >> 1), X = 2 * x + (t & 1);
+            stf(out + (((long long)b * Cout + o) * 2 * H + Y) * 2 * W + X, v);
+          } else {
+            stf(out + ((long long)b * Cout + o) * HW + p, v);
+          }
+        }
+}
+
 // Weight and bias gradients of a 3x3 convolution: gw[o][i][dy][dx] +=
 // sum_{b,y,x} g[b][o][y][x] in[b][i][y+dy-1][x+dx-1], gb[o] += sum g[b][o].
 // CTA: 16 output x 16 input channels, one image row at a time over its slice of the
@@ -825,8 +907,14 @@ int unet_forward(cmm_unet* u, int B, const int* done) {
     const Layer& t = u->layers[li++];
     const Layer& a = u->layers[li++];
     const Layer& b = u->layers[li++];
-    k_tconv_fwd<<<grid_n((long long)B * w * H * W), 256, 0, u->ctx->stream>>>(h, u->wbf + t.woff, u->master + t.boff,
-                                                                              u->up[l], c, w, H / 2, W / 2, B, done);
+    if (u->tensor_cores) {
+      const dim3 gp((unsigned)(((H / 2) * (W / 2) + 127) / 128), (unsigned)((w + 31) / 32), (unsigned)B);
+      k_pointwise_mma<4, bf16, 2><<<gp, 128, 0, u->ctx->stream>>>(h, u->wbf + t.woff, u->master + t.boff, u->up[l],
+                                                                    c, w, H / 2, W / 2, done);
+    } else {
+      k_tconv_fwd<<<grid_n((long long)B * w * H * W), 256, 0, u->ctx->stream>>>(h, u->wbf + t.woff, u->master + t.boff,
+                                                                                u->up[l], c, w, H / 2, W / 2, B, done);
+    }
     CMM_LAUNCH_CHECK();
     k_cat<<<grid_n((long long)B * 2 * w * H * W), 256, 0, u->ctx->stream>>>(u->up[l], u->enc_b[l], u->cat[l], w, w,
                                                                             (long long)H * W, B, done);
@@ -838,8 +926,14 @@ int unet_forward(cmm_unet* u, int B, const int* done) {
   }
   const Layer& o = u->layers[li++];
   const long long HW = (long long)u->ny * u->nx;
-  k_conv1_fwd<<<grid_n((long long)B * 3 * HW), 256, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff,
-                                                                        u->y_out, c, 3, HW, B, done);
+  if (u->tensor_cores) {
+    const dim3 gp((unsigned)((HW + 127) / 128), 1, (unsigned)B);
+    k_pointwise_mma<1, float, 1><<<gp, 128, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff, u->y_out, c,
+                                                                   3, u->ny, u->nx, done);
+  } else {
+    k_conv1_fwd<<<grid_n((long long)B * 3 * HW), 256, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff,
+                                                                          u->y_out, c, 3, HW, B, done);
+  }
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
