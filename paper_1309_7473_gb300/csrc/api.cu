@@ -630,6 +630,7 @@ int op_sync_corr(cmm_op* op) {
 extern "C" {
 
 static int apply_A_dev(cmm_op* op, const double* m_in, double* m_out) {
+  TraceRange tr("cmm: A = P^T N^-1 P");
   CMM_TRY(launch_map_to_gather(op, m_in));
   for (int d0 = 0; d0 < op->pt->n_det; d0 += op->chunk) {
     const int nd = std::min(op->chunk, op->pt->n_det - d0);
@@ -723,6 +724,7 @@ int cmm_project(cmm_op* op, const double* m, void* tod, int32_t tod_is_f64) {
 }
 
 int cmm_rhs(cmm_op* op, const void* tod, int32_t tod_is_f64, double* b) {
+  TraceRange tr("cmm: rhs P^T N^-1 d");
   if (!op || !tod || !b) return fail(CMM_ERR_ARG, "null argument");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   CMM_TRY(op_sync_corr(op));
@@ -938,6 +940,7 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
 extern "C" {
 
 int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm_precon** out) {
+  TraceRange tr("cmm: preconditioner build");
   if (!op || !out) return fail(CMM_ERR_ARG, "null argument");
   *out = nullptr;
   CMM_CUDA(cudaSetDevice(op->ctx->device));
@@ -1041,6 +1044,7 @@ static int precon_apply_dev(cmm_precon* pc, const double* r, double* z, double* 
 }
 
 int cmm_precon_apply(cmm_precon* pc, const double* r, double* z) {
+  TraceRange tr("cmm: preconditioner apply");
   if (!pc || !r || !z) return fail(CMM_ERR_ARG, "null argument");
   if (r == z) return fail(CMM_ERR_ARG, "r and z must not alias");
   CMM_CUDA(cudaSetDevice(pc->op->ctx->device));
@@ -1216,6 +1220,7 @@ int cmm_solve_state_load(cmm_op* op, const double* state) {
 
 int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_solve_opts* opts,
               double* resid_hist, double* anorm_terms, double* snapshots, cmm_solve_info* info) {
+  TraceRange tr("cmm: solve");
   if (!op || !pc || !b || !x || !opts || !info) return fail(CMM_ERR_ARG, "null argument");
   CMM_CUDA(cudaSetDevice(op->ctx->device));
   CMM_TRY(op_sync_corr(op));
@@ -1525,6 +1530,7 @@ int cmm_autotune(cmm_op* op, int32_t reps, const char* cache_path, int32_t* chos
 // ------------------------------------------------------------------ batched solves
 int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const double* const* b,
                     double* const* x, const cmm_solve_opts* opts, cmm_solve_info* infos) {
+  TraceRange tr("cmm: batch solve");
   if (n <= 0 || !ops || !pcs || !b || !x || !opts || !infos) return fail(CMM_ERR_ARG, "null argument");
   for (int i = 0; i < n; ++i) {
     if (!ops[i] || !pcs[i] || !b[i] || !x[i]) return fail(CMM_ERR_ARG, "null entry in batch");

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -30,6 +31,16 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
     int s_ = (call);             \
     if (s_ != CMM_OK) return s_; \
   } while (0)
+
+// ------------------------------------------------------------------ tracing
+// NVTX range for the lifetime of the object (a name per A-application pass and
+// per solver phase, seen by Nsight tools; free when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // ------------------------------------------------------------------ vector types
 template <typename T> struct V2t;

@@ -461,11 +461,16 @@ static int apply_pair_s(cmm_op* op, int d0, int nd, int pass) {
   cudaStream_t st = op->ctx->stream;
   const int nc = op->pt->ncomp;
   if (pass < 0 || pass == 0) {
+    TraceRange tr("A: P m + column FFTs (two detectors per sequence)");
     if (nc == 1) CMM_TRY((dispatch_pair_T<1, S>(a, nd, 0, st, false)));
     else CMM_TRY((dispatch_pair_T<3, S>(a, nd, 0, st, false)));
   }
-  if (pass < 0 || pass == 1) CMM_TRY((dispatch_pair_F<S>(a, nd, st, false)));
+  if (pass < 0 || pass == 1) {
+    TraceRange tr("A: row FFTs + N^-1");
+    CMM_TRY((dispatch_pair_F<S>(a, nd, st, false)));
+  }
   if (pass < 0 || pass == 2) {
+    TraceRange tr("A: inverse column FFTs + P^T");
     for (int g0 = 0; g0 < nd; g0 += kFlushDets) {
       TodArgs b = a;
       const int gn = std::min(kFlushDets, nd - g0);   // even g0: whole pairs per group
