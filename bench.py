@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--learned-reals", type=int, default=220,
                     help="realisations of the learned workload (90 percent train: about 20k pairs)")
     ap.add_argument("--learned-epochs", type=int, default=15)
+    ap.add_argument("--learned-rounds", type=int, default=2,
+                    help="on-policy rounds: pairs from the corrected solves themselves, then more training")
     return ap.parse_args()
 
 
@@ -479,6 +481,25 @@ def run_learned(args):
     pcl = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=8.0)
     cmm.cmm_precon_set_correction(pcl.h, net.h)
     pcb = cmm.Precon(op, cmm.PRECON_BINNED)
+    held_out = list(range(10_000, 10_020))
+
+    def fcg8_mean():
+        its = [cmm.solve(op, pcl, rhs(r), tol=1e-6, maxit=1000, flexible=True, window=8)[1].iterations
+               for r in held_out[:10]]
+        return sum(its) / len(its)
+
+    # on-policy rounds: pairs harvested along the corrected FCG(8) solves of the
+    # training realisations themselves, added to the set, a few more epochs
+    rounds = [{"round": 0, "fcg8_iterations_mean_10": fcg8_mean(), "pairs": int(ti.shape[0]) // 2}]
+    for rd in range(args.learned_rounds):
+        new = [learned.harvest_pairs(op, pc, rhs(r), max_iter=200, tol=1e-12, solve_pc=pcl, window=8)[:2]
+               for r in range(n_train)]
+        ni = torch.cat([p[0] for p in new])
+        nt = torch.cat([p[1] for p in new])
+        ti, tt = torch.cat([ti, ni, -ni]), torch.cat([tt, nt, -nt])
+        learned.train(net, ti, tt, epochs=max(1, args.learned_epochs // 3), batch=32, lr=3e-4, val=(vi, vt),
+                      seed=rd + 1)
+        rounds.append({"round": rd + 1, "fcg8_iterations_mean_10": fcg8_mean(), "pairs": int(ti.shape[0]) // 2})
     # on 20 held-out realisations: binned PCG, PCG(M_C), the corrected preconditioner
     # in flexible CG (Polak-Ribiere form and FCG(8)), and PCG(M_C) started from the
     # corrected preconditioner applied to b
@@ -492,7 +513,7 @@ def run_learned(args):
         torch.cuda.synchronize()
         return info.iterations, time.perf_counter() - t, info.status
 
-    for real in range(10_000, 10_020):
+    for real in held_out:
         b = rhs(real)
         forms["binned"].append(timed(lambda: cmm.solve(op, pcb, b, tol=1e-6, maxit=2000)[1]))
         forms["plain_mc"].append(timed(lambda: cmm.solve(op, pc, b, tol=1e-6, maxit=1000)[1]))
@@ -518,6 +539,7 @@ def run_learned(args):
                    "pairs_train": int(ti.shape[0]) // 2, "pairs_train_with_sign_flips": int(ti.shape[0]),
                    "epochs": args.learned_epochs},
         "solves": summary,
+        "on_policy_rounds": rounds,
         "val_loss": {"zero_output": float(0.5 * (vt.double() ** 2).mean()), "trained": hist[-1][2]},
         "harvest_seconds": round(harvest_s, 2), "train_seconds": round(train_s, 2),
     }

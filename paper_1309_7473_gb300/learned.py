@@ -18,19 +18,19 @@ import torch
 from . import cmm
 
 
-def harvest_pairs(op, pc, b, max_iter=200, tol=1e-10, every=1, solve_pc=None):
+def harvest_pairs(op, pc, b, max_iter=200, tol=1e-10, every=1, solve_pc=None, window=1):
     """Runs FP64 PCG with the (circulant) preconditioner pc on A x = b and returns
     (inputs, targets, info): FP32 tensors [K, 3, ny, nx] of normalised pairs from the
     snapshots k = 0, every, ... of the solve.  With solve_pc (e.g. M_C followed by
-    the current network) the iterates come from that flexible solve instead, while
-    the pairs are still formed with z = M_C r, so a network can be retrained on the
-    residuals it meets itself."""
+    the current network) the iterates come from that flexible solve instead (FCG(m)
+    with window m > 1), while the pairs are still formed with z = M_C r, so a network
+    can be retrained on the residuals it meets itself."""
     slots = max_iter // every + 1
     snaps = torch.zeros((slots, 2) + tuple(op.shape), dtype=torch.float64, device=b.device)
     x = op.new_map()
     run_pc = solve_pc if solve_pc is not None else pc
     info = cmm.cmm_solve(op.h, run_pc.h, b, x, tol, 20 * max_iter + 200, 10, True, False, None, None,
-                         snapshots=snaps, snapshot_every=every)
+                         snapshots=snaps, snapshot_every=every, flexible=window > 1, window=window)
     taken = min(slots, info.iterations // every + 1)
     ins = torch.empty((taken,) + tuple(op.shape), dtype=torch.float32, device=b.device)
     tgts = torch.empty_like(ins)
