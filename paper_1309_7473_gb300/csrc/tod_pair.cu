@@ -38,9 +38,6 @@
 namespace cmm {
 
 // Tuning knobs of this path (compile-time; the defaults are the measured best).
-#ifndef CMM_PAIR_SPL
-#define CMM_PAIR_SPL 8     // consecutive samples per lane in the binning
-#endif
 #ifndef CMM_PAIR_ROT
 #define CMM_PAIR_ROT 1     // forward pass: 0 = (cos 2phi, sin 2phi) from the FP32 table, 1 = from the boresight record
 #endif
@@ -232,7 +229,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   constexpr int J = ColShape<R>::J;
   constexpr int NT = ColShape<R>::THREADS;
   constexpr int BS = J + 2;    // row stride of the binning tile (the pad spreads rows over the banks)
-  constexpr int SPL = CMM_PAIR_SPL;   // consecutive samples per lane
+  constexpr int SPL = 8;              // consecutive samples per lane
   constexpr int LPR = J / SPL;        // lanes per row
   constexpr int RPP = NT / LPR;       // rows per binning pass
   // Pixel staging: row stride PS ints; a lane's 8 pixels are two 16-byte chunks
@@ -241,7 +238,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   // distinct 4-bank groups (PS = 24 words = 8 mod 32 shifts consecutive rows).
   constexpr int PS = J + 8;
   constexpr int RS = J + 2;   // row stride (complex) of the staged rotations
-  static_assert(SPL == 8 && LPR >= 1 && RPP <= R && R % RPP == 0 && (RPP * J) % NT == 0, "binning layout");
+  static_assert(LPR >= 1 && RPP <= R && R % RPP == 0 && (RPP * J) % NT == 0, "binning layout");
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
   const int cl = threadIdx.x % J;

@@ -182,6 +182,20 @@ def test_apply_A_periodic(cmm, ctx, prec):
     assert rel(host(op.apply(dev(m))), om.apply_A(oop, m)) < TOL[prec]
 
 
+@pytest.mark.parametrize("pair", [True, False])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_apply_A_periodic_fast_path(cmm, ctx, prec, pair):
+    """The periodic-boundary instances of the register-FFT kernels (2^13 samples on
+    the wrapping scan), in both FFT packings, element-wise against the oracle."""
+    scan = gen.bccb_scan(8, 16, 1 << 13, diagonal=True, ncomp=3)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=215)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    op.set_pair_packing(pair)
+    oop = om.make_operator(scan, noise)
+    m = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=216)[0]
+    assert rel(host(op.apply(dev(m))), om.apply_A(oop, m)) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_apply_A_tiny_patch(cmm, ctx, prec):
     scan, noise = gen.tiny_patch()
