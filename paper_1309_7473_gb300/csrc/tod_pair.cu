@@ -1,5 +1,7 @@
-// Pair-packed fast path of A = P^T N^-1 P for FP32 compute (FP32 or BF16 spectrum
-// storage), detectors with independent noise.
+// Pair-packed fast path of A = P^T N^-1 P (Eq. 2; pointing of Eq. 1 with the response
+// of Sec. Test setup; N^-1 the per-detector Fourier-diagonal noise filter of the
+// Introduction and Sec. Test setup) for FP32 compute (FP32 or BF16 spectrum storage),
+// detectors with independent noise.
 //
 // Two detectors d1, d2 share one complex sequence of n_t points, z(t) = s1(t) +
 // i s2(t): each complex element is one time sample of both detectors, so the
