@@ -46,6 +46,12 @@ namespace cmm {
 #ifndef CMM_PAIR_ROT_INV
 #define CMM_PAIR_ROT_INV 0   // binning: 0 = from the FP32 table, 1 = from the boresight record, staged beside the pixels
 #endif
+#ifndef CMM_PAIR_XOR
+#define CMM_PAIR_XOR 0     // pixel staging: 0 = rows padded to J + 8 ints, 1 = XOR-swizzled 16-byte chunks (no pad)
+#endif
+#ifndef CMM_PAIR_EARLY_ROT
+#define CMM_PAIR_EARLY_ROT 0   // binning: 1 = the lane's rotation loads issued before the staging barrier
+#endif
 #ifndef CMM_PAIR_FILTER_THREADS_PER_SM
 #define CMM_PAIR_FILTER_THREADS_PER_SM 1024
 #endif
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   // interleaved with its row neighbour's (chunk h of lane bq at word 8h + 4bq of a
   // 16-sample group), so that the eight lanes of a quarter-warp load hit eight
   // distinct 4-bank groups (PS = 24 words = 8 mod 32 shifts consecutive rows).
-  constexpr int PS = J + 8;
+  constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
   constexpr int RS = J + 2;   // row stride (complex) of the staged rotations
   static_assert(LPR >= 1 && RPP <= R && R % RPP == 0 && (RPP * J) % NT == 0, "binning layout");
   if (a.done && *a.done) return;
@@ -276,6 +282,17 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   for (int kr0 = 0; kr0 < R; kr0 += RPP) {
     const int kr = kr0 + br;
     const int tq = c0 + SPL * bq + kr * a.C;   // the lane's first sample
+    float2 r2[8];
+    auto load_rot = [&]() {
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
+                                    : __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
+        r2[k] = make_float2(v.x, v.y);
+        r2[k + 1] = make_float2(v.z, v.w);
+      }
+    };
+    if (NC == 3 && CMM_PAIR_EARLY_ROT && !ROT_STAGED) load_rot();
     if constexpr (!CACHED) {
       // pixels of both detectors for the pass's RPP x J samples, lanes on
       // consecutive samples (coalesced boresight reads)
@@ -285,7 +302,9 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
         const int rr = sidx / J, col = sidx % J;
         const int4 b = __ldg(a.bore + c0 + col + (kr0 + rr) * a.C);
         // column col = 16 g + 8 bq + 4 h + w of the row goes to word 16 g + 8 h + 4 bq + w
-        const int sw = (col & ~15) | ((col & 4) << 1) | ((col & 8) >> 1) | (col & 3);
+        // (padded rows), or to chunk (2 h + bq) ^ (row & 3) of its 16-word group
+        const int sw = CMM_PAIR_XOR ? (col & ~15) | (((((col >> 1) & 2) | ((col >> 3) & 1)) ^ (rr & 3)) << 2) | (col & 3)
+                                    : (col & ~15) | ((col & 4) << 1) | ((col & 8) >> 1) | (col & 3);
         pst[rr * PS + sw] = pixel_fast<PERIODIC>(b, off1, a.ny, a.nx, npix);
         pst[(RPP + rr) * PS + sw] = pixel_fast<PERIODIC>(b, off2, a.ny, a.nx, npix);
         if constexpr (ROT_STAGED) rst[rr * RS + col] = rot2_of_bore(b);
@@ -293,16 +312,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
       __syncthreads();
     }
     const int t8 = tq;
-    float2 r2[8];
-    if (NC == 3) {
-#pragma unroll
-      for (int k = 0; k < 8; k += 2) {
-        const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
-                                    : __ldg(reinterpret_cast<const float4*>(a.rot2 + t8 + k));
-        r2[k] = make_float2(v.x, v.y);
-        r2[k + 1] = make_float2(v.z, v.w);
-      }
-    }
+    if (NC == 3 && !(CMM_PAIR_EARLY_ROT && !ROT_STAGED)) load_rot();
     // the lane's 8 filtered samples of both detectors (real part: d1, imaginary: d2)
     float4 yv[4];
 #pragma unroll
@@ -317,10 +327,17 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
         P0 = __ldcs(reinterpret_cast<const int4*>(pixd));
         P1 = __ldcs(reinterpret_cast<const int4*>(pixd + 4));
       } else {
-        // chunks h = 0, 1 of the lane's 8 pixels at words 16 (bq / 2) + 4 (bq % 2) + 8 h
-        const int4* ps = reinterpret_cast<const int4*>(pst + (dd * RPP + br) * PS + ((bq >> 1) << 4) + ((bq & 1) << 2));
-        P0 = ps[0];
-        P1 = ps[2];
+        const int* prow = pst + (dd * RPP + br) * PS + ((bq >> 1) << 4);
+        if (CMM_PAIR_XOR) {
+          // chunks (2 h + bq % 2) ^ (row & 3) of the 16-word group
+          P0 = *reinterpret_cast<const int4*>(prow + (((bq & 1) ^ (br & 3)) << 2));
+          P1 = *reinterpret_cast<const int4*>(prow + (((2 | (bq & 1)) ^ (br & 3)) << 2));
+        } else {
+          // chunks h = 0, 1 of the lane's 8 pixels at words 16 (bq / 2) + 4 (bq % 2) + 8 h
+          const int4* ps = reinterpret_cast<const int4*>(prow + ((bq & 1) << 2));
+          P0 = ps[0];
+          P1 = ps[2];
+        }
       }
       p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
       p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
@@ -382,7 +399,8 @@ static int run_pair_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, boo
   // rotation is staged, RPP rows x (J + 2) complex
   constexpr int RPP = NT / (J / 8);   // rows per binning pass
   const int smem_f = (int)(sizeof(float2) * R * J);
-  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * RPP * (J + 8) +
+  constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * RPP * PS +
                            (CMM_PAIR_ROT_INV ? sizeof(float2) * RPP * (J + 2) : 0));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
