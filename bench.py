@@ -634,13 +634,13 @@ def cufft_filter_ms(scan, noise, dev, stream):
 
 def launches_per_iteration(n_det, chunk):
     """Kernels of one circulant-PCG iteration: the A-application (map copy in, per
-    chunk one forward and one filter launch and per 128 detectors one inverse +
+    chunk one forward and one filter launch and per 256 detectors one inverse +
     binning launch and one flush, map copy out), the CG update kernels and the
     circulant preconditioner (Sigma^-1, 2-D FFTs, per-mode solve)."""
     a = 2
     for d0 in range(0, n_det, chunk):
         nd = min(chunk, n_det - d0)
-        a += 2 + 2 * math.ceil(nd / 128)
+        a += 2 + 2 * math.ceil(nd / 256)
     return a + CG_LAUNCHES + CIRC_LAUNCHES
 
 

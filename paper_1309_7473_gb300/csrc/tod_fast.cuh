@@ -41,7 +41,10 @@ constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
 constexpr int kGenUnroll = CMM_GEN_UNROLL;
 constexpr int kBinUnroll = CMM_BIN_UNROLL;
 constexpr int kBinHalves = CMM_BIN_HALVES;
-constexpr int kFlushDets = 128;
+#ifndef CMM_FLUSH_DETS
+#define CMM_FLUSH_DETS 256
+#endif
+constexpr int kFlushDets = CMM_FLUSH_DETS;   // detectors between flushes of the FP32 partial map
 constexpr int kE = 16;     // elements per thread in the column FFT
 
 // Columns per CTA: 32 (one per lane) for R <= 128, 16 (one per half-warp lane)

@@ -24,7 +24,7 @@
 //                   with a run accumulator (one vector FP32 reduction per run into
 //                   the L2-resident partial map).
 //   k_fast_flush (tod_fast.cu) adds the FP32 partial map into the FP64 map after
-//   every 64 pairs (128 detectors), as on the one-detector path.
+//   every kFlushDets detectors (256), as on the one-detector path.
 //
 // A chunk with an odd number of detectors pairs its last detector with nothing
 // (the imaginary part stays zero and is not binned).
@@ -47,7 +47,7 @@ namespace cmm {
 #define CMM_PAIR_ROT_INV 0   // binning: 0 = from the FP32 table, 1 = from the boresight record, staged beside the pixels
 #endif
 #ifndef CMM_PAIR_XOR
-#define CMM_PAIR_XOR 0     // pixel staging: 0 = rows padded to J + 8 ints, 1 = XOR-swizzled 16-byte chunks (no pad)
+#define CMM_PAIR_XOR 1     // pixel staging: 0 = rows padded to J + 8 ints, 1 = XOR-swizzled 16-byte chunks (no pad)
 #endif
 #ifndef CMM_PAIR_EARLY_ROT
 #define CMM_PAIR_EARLY_ROT 0   // binning: 1 = the lane's rotation loads issued before the staging barrier

@@ -418,7 +418,7 @@ def _flush_case(log_nt):
 @pytest.mark.parametrize("prec", [1, 2])
 def test_apply_A_flush_groups(cmm, ctx, log_nt, prec, pair):
     """320 ACT-like detectors in one chunk (det_chunk = 0), as the 1024-detector
-    launch: the binning pass runs as three groups of at most 128 detectors, each
+    launch: the binning pass runs as two groups (256 + 64 detectors), each
     followed by the flush of the FP32 partial map into the FP64 accumulator.
     Element-wise against the oracle, on-the-fly and cached pointing; 2^18 samples
     use the 256-point column FFTs of the bench's size."""
