@@ -306,6 +306,23 @@ def bin_tod(op, tod, dets=None):
     return out.reshape(op.shape)
 
 
+def binning_magnitude(op, m):
+    """Scale of the rounding error of the binning sums of A m = P^T N^-1 P m (Eq. 2),
+    for error bounds in tests: S[c, p] = sum over the samples hitting p of
+    |P_{dt,c} (N^-1 P m)_{dt}| (no cancellation), and h[p], the number of those
+    samples.  Not a step of the method."""
+    dets = np.arange(op.scan.n_det)
+    y = _ninv(op, project(op, m, dets), dets)
+    pix = _pix(op, dets)
+    wts = sample_weights(op.scan, dets)
+    ok = pix >= 0
+    s = np.empty((op.scan.ncomp, op.scan.npix))
+    for c in range(op.scan.ncomp):
+        s[c] = np.bincount(pix[ok], weights=np.abs(wts[c] * y)[ok], minlength=op.scan.npix)
+    h = np.bincount(pix[ok], minlength=op.scan.npix)
+    return s.reshape(op.shape), h.reshape(op.shape[1:])
+
+
 def _chunks(op):
     # correlated noise couples the detectors: one chunk holding all of them
     step = DET_CHUNK if op.corr is None else op.scan.n_det

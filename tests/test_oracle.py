@@ -251,6 +251,31 @@ def test_white_noise_T_only_is_hit_count():
     np.testing.assert_allclose(x.ravel()[op.mask], m.ravel()[op.mask], rtol=1e-12)
 
 
+def test_binning_magnitude_bounds_A(tiny):
+    """The binning-error scale S = P^T |N^-1 P m| with its hit counts: equal to A m
+    and to the brute-force hit count where no term can cancel (white noise, T only,
+    a positive map), above |A m| everywhere on a TQU scan with 1/f noise, and
+    homogeneous of degree one in m."""
+    scan = gen.small_scan(cfg=103, ny=6, nx=7, n_t=512, ncomp=1, throw_px=10.0)
+    noise = gen.Noise(np.full(scan.n_det, 2.0), np.zeros(scan.n_det), np.full(scan.n_det, 3.5))
+    op = om.make_operator(scan, noise)
+    hits = np.zeros(scan.npix)
+    for p in om.sample_pixels(scan, np.arange(scan.n_det)).ravel():
+        if p >= 0:
+            hits[p] += 1
+    m = 1.0 + np.random.default_rng(2).random((1, 6, 7))
+    s, h = om.binning_magnitude(op, m)
+    np.testing.assert_array_equal(h.ravel(), hits)
+    np.testing.assert_allclose(s, om.apply_A(op, m), rtol=1e-12)
+    m3 = gen.random_maps(3, 8, 8, 1, cfg=5)[0]
+    s3, h3 = om.binning_magnitude(tiny, m3)
+    a3 = om.apply_A(tiny, m3)
+    assert np.all(s3 >= np.abs(a3) * (1 - 1e-12))
+    assert np.any(s3 > 2 * np.abs(a3))
+    np.testing.assert_allclose(om.binning_magnitude(tiny, -2.0 * m3)[0], 2.0 * s3, rtol=1e-12)
+    assert h3.sum() == (om._pix(tiny, np.arange(tiny.scan.n_det)) >= 0).sum()
+
+
 def test_mask_removes_degenerate_pixels():
     # one detector at one angle hits pixels once: the TQU block is rank one
     scan = gen.small_scan(cfg=104, ny=6, nx=6, n_t=64, ncols=1, nrows=1, throw_px=30.0)
