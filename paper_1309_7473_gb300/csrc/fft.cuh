@@ -18,20 +18,25 @@
 
 namespace cmm {
 
-// cos(2 pi k / 32) for integer k (exact constants of the 32nd roots of unity)
+// cos(2 pi k / 32) for integer k (exact constants of the 32nd roots of unity).
+// Written without recursion: a recursive constexpr function is a real call when its
+// argument is not a constant expression (rot32's m is a function parameter), so
+// the compiler kept it out of line, with a stack frame and double-precision
+// conversions, inside every register FFT.
 __host__ __device__ constexpr double cos32(int k) {
   k &= 31;
-  if (k > 16) k = 32 - k;           // cos is even
-  if (k > 8) return -cos32(16 - k);  // cos(pi - x) = -cos x
+  if (k > 16) k = 32 - k;            // cos is even
+  const double sg = k > 8 ? -1.0 : 1.0;
+  if (k > 8) k = 16 - k;             // cos(pi - x) = -cos x
   switch (k) {
-    case 0: return 1.0;
-    case 1: return 0.98078528040323044913;
-    case 2: return 0.92387953251128675613;
-    case 3: return 0.83146961230254523708;
-    case 4: return 0.70710678118654752440;
-    case 5: return 0.55557023301960222474;
-    case 6: return 0.38268343236508977173;
-    case 7: return 0.19509032201612826785;
+    case 0: return sg;
+    case 1: return sg * 0.98078528040323044913;
+    case 2: return sg * 0.92387953251128675613;
+    case 3: return sg * 0.83146961230254523708;
+    case 4: return sg * 0.70710678118654752440;
+    case 5: return sg * 0.55557023301960222474;
+    case 6: return sg * 0.38268343236508977173;
+    case 7: return sg * 0.19509032201612826785;
     default: return 0.0;
   }
 }

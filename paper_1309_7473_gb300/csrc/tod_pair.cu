@@ -55,6 +55,32 @@ namespace cmm {
 #ifndef CMM_PAIR_FILTER_THREADS_PER_SM
 #define CMM_PAIR_FILTER_THREADS_PER_SM 1024
 #endif
+#ifndef CMM_PAIR_DD_UNROLL
+#define CMM_PAIR_DD_UNROLL 2   // binning: the two detectors' runs unrolled (2) or in a loop (1)
+#endif
+#ifndef CMM_PAIR_ROTACC
+#define CMM_PAIR_ROTACC 1   // binning runs: 1 = sums of u cos 2phi, u sin 2phi, rotated by psi_d at the run's end; 0 = per sample
+#endif
+
+constexpr int kDdUnroll = CMM_PAIR_DD_UNROLL;
+
+// A binning run in the frame of the scan rotation: for samples of one detector on
+// one pixel, sums of u, u cos 2phi_t and u sin 2phi_t; the detector angle psi_d
+// enters once, when the run is reduced: sum u cos 2(psi + phi) = cos 2psi * sum u
+// cos 2phi - sin 2psi * sum u sin 2phi (and the sine likewise), with the inverse
+// FFT's 1/N folded into (sx, sy) = (cos 2psi, sin 2psi) / N and st = 1/N.
+struct PairRun {
+  int cur = -1;
+  float t = 0.f, c = 0.f, s = 0.f;
+};
+
+template <int NC>
+__device__ __forceinline__ void pair_run_close(float* acc32, const PairRun& r, int skip, float st, float sx, float sy) {
+  if (r.cur >= 0 && r.cur != skip) {
+    if (NC == 1) red_add(acc32 + r.cur, st * r.t);
+    else red_add4(acc32 + 4 * r.cur, st * r.t, fmaf(sx, r.c, -sy * r.s), fmaf(sy, r.c, sx * r.s));
+  }
+}
 
 // (cos 2phi, sin 2phi) of the fixed-point pair (c, s) of a boresight record, in FP32:
 // (c^2 - s^2, 2 c s) / (c^2 + s^2), the integers converted exactly on the FP32 pipe
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
     float4 yv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) yv[j] = smf4[(kr * BS + 8 * bq) / 2 + j];
-#pragma unroll
+#pragma unroll kDdUnroll
     for (int dd = 0; dd < 2; ++dd) {
       if (dd == 1 && !two) break;
       int p[8];
@@ -341,23 +367,47 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
       }
       p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
       p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
-      float u[8], cc[8], ss[8];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        u[2 * j] = (dd ? yv[j].y : yv[j].x) * scale;
-        u[2 * j + 1] = (dd ? yv[j].w : yv[j].z) * scale;
-      }
-      if (NC == 3) {
+      if constexpr (CMM_PAIR_ROTACC) {
         const float2 pl = dd ? pol2 : pol1;
+        const float sx = scale * pl.x, sy = scale * pl.y;
+        PairRun run;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          cc[k] = pl.x * r2[k].x - pl.y * r2[k].y;
-          ss[k] = pl.y * r2[k].x + pl.x * r2[k].y;
+          const float4 v = yv[k >> 1];
+          const float u = dd ? ((k & 1) ? v.w : v.y) : ((k & 1) ? v.z : v.x);
+          if (p[k] != run.cur) {
+            pair_run_close<NC>(a.acc32, run, npix, scale, sx, sy);
+            run.cur = p[k];
+            run.t = 0.f;
+            run.c = 0.f;
+            run.s = 0.f;
+          }
+          run.t += u;
+          if (NC == 3) {
+            run.c = fmaf(r2[k].x, u, run.c);
+            run.s = fmaf(r2[k].y, u, run.s);
+          }
         }
+        pair_run_close<NC>(a.acc32, run, npix, scale, sx, sy);
+      } else {
+        float u[8], cc[8], ss[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          u[2 * j] = (dd ? yv[j].y : yv[j].x) * scale;
+          u[2 * j + 1] = (dd ? yv[j].w : yv[j].z) * scale;
+        }
+        if (NC == 3) {
+          const float2 pl = dd ? pol2 : pol1;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            cc[k] = pl.x * r2[k].x - pl.y * r2[k].y;
+            ss[k] = pl.y * r2[k].x + pl.x * r2[k].y;
+          }
+        }
+        BinRun run;
+        bin_push8<NC>(a.acc32, run, p, u, cc, ss, npix);
+        bin_close<NC>(a.acc32, run, npix);
       }
-      BinRun run;
-      bin_push8<NC>(a.acc32, run, p, u, cc, ss, npix);
-      bin_close<NC>(a.acc32, run, npix);
     }
     if constexpr (!CACHED) __syncthreads();   // the staging is rewritten by the next pass
   }
