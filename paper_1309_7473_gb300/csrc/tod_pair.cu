@@ -50,7 +50,7 @@ namespace cmm {
 #define CMM_PAIR_XOR 1     // pixel staging: 0 = rows padded to J + 8 ints, 1 = XOR-swizzled 16-byte chunks (no pad)
 #endif
 #ifndef CMM_PAIR_EARLY_ROT
-#define CMM_PAIR_EARLY_ROT 0   // binning: 1 = the lane's rotation loads issued before the staging barrier
+#define CMM_PAIR_EARLY_ROT 1   // binning: 1 = the lane's rotation loads issued before the staging barrier
 #endif
 #ifndef CMM_PAIR_FILTER_THREADS_PER_SM
 #define CMM_PAIR_FILTER_THREADS_PER_SM 1024
