@@ -464,12 +464,16 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
         if constexpr (!CACHED) {
           P0 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * H * bq + 8 * h);
           P1 = *reinterpret_cast<const int4*>(pst + br * PSTR + 8 * H * bq + 8 * h + 4);
+        } else if constexpr (CMM_V8) {
+          ld_cs_v8(pixd + t, p);   // 32-byte aligned: t and n_t are multiples of 8
         } else {
           P0 = __ldcs(reinterpret_cast<const int4*>(pixd + t));
           P1 = __ldcs(reinterpret_cast<const int4*>(pixd + t + 4));
         }
-        p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
-        p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
+        if constexpr (!CACHED || !CMM_V8) {
+          p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
+          p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
+        }
         const float4 A = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * H * bq + 4 * h);
         const float4 B = *reinterpret_cast<const float4*>(smf + kr * BS + 4 * H * bq + 4 * h + 2);
         float u[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
@@ -478,12 +482,25 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
         for (int k = 0; k < 8; ++k) u[k] *= scale;
         if (NC == 3) {
 #pragma unroll
-          for (int k = 0; k < 8; k += 2) {
-            const float4 r2 = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k));
-            cc[k] = pol.x * r2.x - pol.y * r2.y;
-            ss[k] = pol.y * r2.x + pol.x * r2.y;
-            cc[k + 1] = pol.x * r2.z - pol.y * r2.w;
-            ss[k + 1] = pol.y * r2.z + pol.x * r2.w;
+          for (int k = 0; k < 8; k += 4) {
+            float4 r2[2];
+            if constexpr (CMM_V8) {
+              float v[8];
+              ld_nc_v8(a.rot2 + t + k, v);
+              r2[0] = make_float4(v[0], v[1], v[2], v[3]);
+              r2[1] = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+              r2[0] = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k));
+              r2[1] = __ldg(reinterpret_cast<const float4*>(a.rot2 + t + k + 2));
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const int kk = k + 2 * j;
+              cc[kk] = pol.x * r2[j].x - pol.y * r2[j].y;
+              ss[kk] = pol.y * r2[j].x + pol.x * r2[j].y;
+              cc[kk + 1] = pol.x * r2[j].z - pol.y * r2[j].w;
+              ss[kk + 1] = pol.y * r2[j].z + pol.x * r2[j].w;
+            }
           }
         }
         bin_push8<NC>(a.acc32, run, p, u, cc, ss, npix);

@@ -41,6 +41,9 @@ constexpr int kDetsPerCta = CMM_DETS_PER_CTA;
 constexpr int kGenUnroll = CMM_GEN_UNROLL;
 constexpr int kBinUnroll = CMM_BIN_UNROLL;
 constexpr int kBinHalves = CMM_BIN_HALVES;
+#ifndef CMM_V8
+#define CMM_V8 1   // binning: a lane's 8 rotations / cached pixels by 32-byte loads (1) or 16-byte loads (0)
+#endif
 #ifndef CMM_FLUSH_DETS
 #define CMM_FLUSH_DETS 256
 #endif
@@ -136,6 +139,21 @@ template <> struct ColPlan<256> {
 
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+// One 32-byte read-only load of eight floats (the 256-bit vector load of sm_100 and
+// later); p must be 32-byte aligned.  A lane that needs 32 contiguous bytes gets them
+// in one request touching one sector, where two 16-byte loads of lanes 32 bytes
+// apart would each touch every sector twice.
+__device__ __forceinline__ void ld_nc_v8(const void* p, float (&v)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+// The same for eight ints read once (evict-first: streamed pixel indices).
+__device__ __forceinline__ void ld_cs_v8(const int* p, int (&v)[8]) {
+  asm volatile("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "l"(p));
 }
 __device__ __forceinline__ void red_add4(float* p, float a, float b, float c) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(0.0f)

@@ -310,12 +310,23 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
     const int tq = c0 + SPL * bq + kr * a.C;   // the lane's first sample
     float2 r2[8];
     auto load_rot = [&]() {
+      if constexpr (CMM_V8 && !ROT_STAGED) {
+        // the lane's 8 rotations (64 bytes, 64-byte aligned: tq is a multiple of 8)
 #pragma unroll
-      for (int k = 0; k < 8; k += 2) {
-        const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
-                                    : __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
-        r2[k] = make_float2(v.x, v.y);
-        r2[k + 1] = make_float2(v.z, v.w);
+        for (int h = 0; h < 2; ++h) {
+          float v[8];
+          ld_nc_v8(a.rot2 + tq + 4 * h, v);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) r2[4 * h + k] = make_float2(v[2 * k], v[2 * k + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
+                                      : __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
+          r2[k] = make_float2(v.x, v.y);
+          r2[k + 1] = make_float2(v.z, v.w);
+        }
       }
     };
     if (NC == 3 && CMM_PAIR_EARLY_ROT && !ROT_STAGED) load_rot();
@@ -348,7 +359,12 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
       if (dd == 1 && !two) break;
       int p[8];
       int4 P0, P1;
-      if constexpr (CACHED) {
+      if constexpr (CACHED && CMM_V8) {
+        // 32 bytes, 32-byte aligned (t8 and n_t are multiples of 8)
+        ld_cs_v8(a.pix + (size_t)(dd ? d2 : d1) * a.n_t + t8, p);
+        P0 = make_int4(p[0], p[1], p[2], p[3]);
+        P1 = make_int4(p[4], p[5], p[6], p[7]);
+      } else if constexpr (CACHED) {
         const int* pixd = a.pix + (size_t)(dd ? d2 : d1) * a.n_t + t8;
         P0 = __ldcs(reinterpret_cast<const int4*>(pixd));
         P1 = __ldcs(reinterpret_cast<const int4*>(pixd + 4));
