@@ -97,6 +97,19 @@ __device__ __forceinline__ float pair_weight(const TodArgs& a, int d, const floa
   return filter_weight_law(cf, kf);
 }
 
+// w_d1 and w_d2 at frequency index kf: the tables, else the law with log2(kf) shared
+__device__ __forceinline__ void pair_weights(const TodArgs& a, int d1, int d2, const float4 cf1, const float4 cf2,
+                                             bool two, int kf, float& w1, float& w2) {
+  if (a.wtab) {
+    w1 = pair_weight(a, d1, cf1, kf);
+    w2 = two ? pair_weight(a, d2, cf2, kf) : 0.f;
+    return;
+  }
+  const float lk = __log2f(small_int_to_float(kf == 0 ? 1 : kf));
+  w1 = cf1.w != 0.0f ? cf1.x : __fdividef(cf1.x, 1.0f + exp2f(fmaf(-cf1.y, lk, cf1.z)));
+  w2 = !two ? 0.f : cf2.w != 0.0f ? cf2.x : __fdividef(cf2.x, 1.0f + exp2f(fmaf(-cf2.y, lk, cf2.z)));
+}
+
 // (P m)(t) of one detector from its pixel, the response table entry and the gather copy
 template <int NC>
 __device__ __forceinline__ float pair_project(const TodArgs& a, int p, const float2 pol, const float2 r2) {
@@ -205,43 +218,31 @@ __global__ void __launch_bounds__(PairFilterShape<RadProd<RC...>::value, E>::THR
 #pragma unroll
   for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
   __syncthreads();
-  if (pair_ok) {
+  // Each thread filters its own elements in registers.  Position pos of row `row`
+  // holds Z(k), k = row + R pos; Z(n - k) sits at position C - 1 - pos of row
+  // R - row (for row 0: (C - pos) mod C of row 0), held by one partner thread;
+  // both threads form a Z + b conj(partner) with the same (a, b), since
+  // min(k, n - k) is the same for the two.  The inverse FFT's first stage starts
+  // with a barrier, so the partner reads below finish before the buffer is reused.
+  if (active) {
     const float4 cf1 = reinterpret_cast<const float4*>(a.coef)[d1];
     const float4 cf2 = reinterpret_cast<const float4*>(a.coef)[d2];
-    float2* r0 = smf + (2 * ps) * ROWLEN;
-    float2* r1 = single ? r0 : r0 + ROWLEN;
-    int kc0, step, npairs;
-    if (!single) {
-      kc0 = side * TPR + i;
-      step = 2 * TPR;
-      npairs = C;
-    } else {
-      kc0 = side ? C : i;   // only side 0 works on a single row
-      step = TPR;
-      npairs = ra == 0 ? C / 2 + 1 : C / 2;
-    }
+    const bool wrap = row == 0;
+    const RowAddr<PS> pa{smf + (single ? rs : (rs ^ 1)) * ROWLEN};
     const int n = (int)a.N;
-    for (int kc = kc0; kc < npairs; kc += step) {
-      // Z(k) at r0[kc] and Z(n - k) at r1[j2]
-      int j2;
-      if (!single) j2 = C - 1 - kc;
-      else if (ra == 0) j2 = (C - kc) & (C - 1);
-      else j2 = C - 1 - kc;
-      const int i1 = kc + (kc >> PS), i2 = j2 + (j2 >> PS);
-      const int k = ra + a.R * kc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int pos = i + e * TPR;
+      const int pp = wrap ? ((C - pos) & (C - 1)) : (C - 1 - pos);
+      const float2 B = pa.ld(pp);
+      const int k = row + a.R * pos;
       const int kf = min(k, n - k);
-      const float w1 = pair_weight(a, d1, cf1, kf);
-      const float w2 = two ? pair_weight(a, d2, cf2, kf) : 0.f;
+      float w1, w2;
+      pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
       const float ha = 0.5f * (w1 + w2), hb = 0.5f * (w1 - w2);
-      const float2 A = r0[i1], B = r1[i2];
-      // a Z(k) + b conj Z(n - k), and the same at n - k
-      r0[i1] = make_float2(fmaf(ha, A.x, hb * B.x), fmaf(ha, A.y, -hb * B.y));
-      if (!(single && i2 == i1)) r1[i2] = make_float2(fmaf(ha, B.x, hb * A.x), fmaf(ha, B.y, -hb * A.y));
+      x[e] = make_float2(fmaf(ha, x[e].x, hb * B.x), fmaf(ha, x[e].y, -hb * B.y));
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int e = 0; e < E; ++e) x[e] = ad.ld_at(bi, e * TPR);
   rfft<1, E, RC...>(x, i, tw + a.twl.C_off, ad);
   if (active) {
     // w_N^(row c), c = i + e TPR, by recurrence over e
