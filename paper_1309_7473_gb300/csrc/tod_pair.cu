@@ -55,6 +55,9 @@ namespace cmm {
 #ifndef CMM_PAIR_FILTER_THREADS_PER_SM
 #define CMM_PAIR_FILTER_THREADS_PER_SM 1024
 #endif
+#ifndef CMM_INV_CARVEOUT
+#define CMM_INV_CARVEOUT -1   // inverse pass: shared-memory carveout in percent (-1: the driver's choice)
+#endif
 #ifndef CMM_PAIR_DD_UNROLL
 #define CMM_PAIR_DD_UNROLL 2   // binning: the two detectors' runs unrolled (2) or in a loop (1)
 #endif
@@ -468,12 +471,15 @@ static int run_pair_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, boo
   const int smem_f = (int)(sizeof(float2) * R * J);
   constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
   const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * RPP * PS +
-                           (CMM_PAIR_ROT_INV ? sizeof(float2) * RPP * (J + 2) : 0));
+                           (CMM_PAIR_ROT_INV && !CACHED && NC == 3 ? sizeof(float2) * RPP * (J + 2) : 0));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_f));
     CMM_CUDA(cudaFuncSetAttribute(k_pair_inv_bin<NC, S, R, PERIODIC, CACHED>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_i));
+    if (CMM_INV_CARVEOUT >= 0)
+      CMM_CUDA(cudaFuncSetAttribute(k_pair_inv_bin<NC, S, R, PERIODIC, CACHED>,
+                                    cudaFuncAttributePreferredSharedMemoryCarveout, CMM_INV_CARVEOUT));
     return CMM_OK;
   }
   const dim3 g(a.C / J, (nd + 1) / 2);
