@@ -143,7 +143,8 @@ template <> __device__ __forceinline__ void st2(bf16* p, float a, float b) {
 template <typename TIN, typename TOUT, bool RELU, bool FLIP, int MT, int TW>
 __global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, const bf16* __restrict__ w,
                                                    const float* __restrict__ bias, TOUT* __restrict__ out, int Cin,
-                                                   int Cout, int H, int W, const int* done) {
+                                                   int Cout, int H, int W, const int* done, int ks = 1,
+                                                   float* __restrict__ part = nullptr) {
   if (stopped(done)) return;
   constexpr int TH = 256 / TW;   // tile rows
   constexpr int RPW = TH / 4;    // rows per warp
@@ -158,7 +159,10 @@ __global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, c
   const int tiles_x = (W + TW - 1) / TW;
   const int x0 = (blockIdx.x % tiles_x) * TW, y0 = (blockIdx.x / tiles_x) * TH;
   const int o0 = blockIdx.y * MO;
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / ks;
+  // split K: slice blockIdx.z % ks of the input channels, in whole 16-channel chunks
+  const int cps = ((Cin + 15) / 16 + ks - 1) / ks;
+  const int c_lo = (blockIdx.z % ks) * cps * 16, c_hi = min(Cin, c_lo + cps * 16);
   const int Wi = FLIP ? Cout : Cin;   // input channels of the forward layer's weight tensor
   float acc[MT][NT][4];
 #pragma unroll
@@ -167,8 +171,11 @@ __global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, c
     for (int n = 0; n < NT; ++n)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[m][n][c] = 0.f;
-  for (int i0 = 0; i0 < Cin; i0 += 16) {
+  for (int i0 = c_lo; i0 < c_hi; i0 += 16) {
     __syncthreads();
+    // unrolled so that a thread has several loads in flight: with few CTAs (one map)
+    // the staging is latency-bound
+#pragma unroll 8
     for (int t = threadIdx.x; t < 16 * (TH + 2) * SX; t += 128) {
       const int xx = t % SX, r = t / SX, yy = r % (TH + 2), ci = r / (TH + 2);
       const int gi = i0 + ci, gy = y0 + yy - 1, gx = x0 + xx - 1;
@@ -176,6 +183,7 @@ __global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, c
       if (gi < Cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = ldf(in + (((long long)b * Cin + gi) * H + gy) * W + gx);
       s_in[(yy * SX + xx) * kCP + ci] = __float2bfloat16_rn(v);
     }
+#pragma unroll 8
     for (int t = threadIdx.x; t < 9 * MO * 16; t += 128) {
       const int k = t % 9, r = t / 9, ii = r % 16, oo = r / 16;
       const int go = o0 + oo, gi = i0 + ii;
@@ -218,6 +226,13 @@ __global__ void __launch_bounds__(128) k_conv3_mma(const TIN* __restrict__ in, c
       for (int h = 0; h < 2; ++h) {
         const int o = o0 + m * 16 + g + 8 * h;
         if (o >= Cout) continue;
+        if (part) {
+          // partial sum of this K slice; bias and activation follow in k_bias_act
+          float* dst = part + (((long long)b * Cout + o) * H + y) * W + x;
+          atomicAdd(dst, acc[m][n][2 * h]);
+          if (x + 1 < W) atomicAdd(dst + 1, acc[m][n][2 * h + 1]);
+          continue;
+        }
         const float bo = bias ? bias[o] : 0.f;
         float v0 = acc[m][n][2 * h] + bo, v1 = acc[m][n][2 * h + 1] + bo;
         if (RELU) {
@@ -336,7 +351,8 @@ __global__ void __launch_bounds__(128) k_conv3_wgrad_mma(const bf16* __restrict_
 template <int TAPS, typename TOUT, int MT>
 __global__ void __launch_bounds__(128) k_pointwise_mma(const bf16* __restrict__ in, const bf16* __restrict__ w,
                                                        const float* __restrict__ bias, TOUT* __restrict__ out,
-                                                       int Cin, int Cout, int H, int W, const int* done) {
+                                                       int Cin, int Cout, int H, int W, const int* done, int ks = 1,
+                                                       float* __restrict__ part = nullptr) {
   if (stopped(done)) return;
   constexpr int NP = 128;       // pixels per CTA
   constexpr int MO = MT * 16;
@@ -347,7 +363,9 @@ __global__ void __launch_bounds__(128) k_pointwise_mma(const bf16* __restrict__ 
   const int HW = H * W;
   const int p0 = blockIdx.x * NP;
   const int o0 = blockIdx.y * MO;
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / ks;
+  const int cps = ((Cin + 15) / 16 + ks - 1) / ks;
+  const int c_lo = (blockIdx.z % ks) * cps * 16, c_hi = min(Cin, c_lo + cps * 16);
   float acc[TAPS][MT][4][4];
 #pragma unroll
   for (int t = 0; t < TAPS; ++t)
@@ -357,13 +375,15 @@ __global__ void __launch_bounds__(128) k_pointwise_mma(const bf16* __restrict__ 
       for (int n = 0; n < 4; ++n)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[t][m][n][c] = 0.f;
-  for (int i0 = 0; i0 < Cin; i0 += 16) {
+  for (int i0 = c_lo; i0 < c_hi; i0 += 16) {
     __syncthreads();
+#pragma unroll 8
     for (int e = threadIdx.x; e < 16 * NP; e += 128) {
       const int px = e % NP, ci = e / NP;
       const int gi = i0 + ci, gp = p0 + px;
       s_in[px * kCP + ci] = (gi < Cin && gp < HW) ? in[((long long)b * Cin + gi) * HW + gp] : __float2bfloat16_rn(0.f);
     }
+#pragma unroll 8
     for (int e = threadIdx.x; e < TAPS * MO * 16; e += 128) {
       const int ii = e % 16, r = e / 16, oo = r % MO, t = r / MO;
       const int go = o0 + oo, gi = i0 + ii;
@@ -397,15 +417,32 @@ __global__ void __launch_bounds__(128) k_pointwise_mma(const bf16* __restrict__ 
           const int o = o0 + m * 16 + g + 8 * (c >> 1);
           const int p = p0 + warp * 32 + n * 8 + 2 * q + (c & 1);
           if (o >= Cout || p >= HW) continue;
-          const float v = acc[t][m][n][c] + bias[o];
+          long long idx;
           if (TAPS == 4) {
             const int y = p / W, x = p - (p / W) * W;
             const int Y = 2 * y + (t >> 1), X = 2 * x + (t & 1);
-            stf(out + (((long long)b * Cout + o) * 2 * H + Y) * 2 * W + X, v);
+            idx = (((long long)b * Cout + o) * 2 * H + Y) * 2 * W + X;
           } else {
-            stf(out + ((long long)b * Cout + o) * HW + p, v);
+            idx = ((long long)b * Cout + o) * HW + p;
           }
+          if (part) atomicAdd(part + idx, acc[t][m][n][c]);
+          else stf(out + idx, acc[t][m][n][c] + bias[o]);
         }
+}
+
+// out = act(part + bias[o]) over [B][Cout][hw] and part reset to zero: the end of a
+// split-K convolution, whose K slices added their partial sums into part.
+template <typename TOUT, bool RELU>
+__global__ void k_bias_act(float* __restrict__ part, const float* __restrict__ bias, TOUT* __restrict__ out,
+                           int Cout, long long hw, long long n, const int* done) {
+  if (stopped(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)((i / hw) % Cout);
+    float v = part[i] + (bias ? bias[o] : 0.f);
+    if (RELU) v = fmaxf(v, 0.f);
+    stf(out + i, v);
+    part[i] = 0.f;
+  }
 }
 
 // Weight and bias gradients of a 3x3 convolution: gw[o][i][dy][dx] +=
@@ -781,6 +818,7 @@ struct cmm_unet {
   float *g0 = nullptr, *g1 = nullptr, *g2 = nullptr;
   std::vector<float*> gskip;
   double* partial = nullptr;
+  float* part = nullptr;       // zeroed FP32 partial sums of the split-K forward convolutions
 };
 
 namespace {
@@ -790,13 +828,52 @@ int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>
 int level_h(const cmm_unet* u, int l) { return u->ny >> l; }
 int level_w(const cmm_unet* u, int l) { return u->nx >> l; }
 
+// K slices for a forward launch of `ctas` CTAs over Cin input channels: enough to
+// put about two CTAs on every SM when the output alone gives too few (a single map,
+// the deep levels), in whole 16-channel chunks and without empty slices.
+int k_slices(int ctas, int Cin) {
+  const int chunks = (Cin + 15) / 16;
+  if (ctas >= 152 || chunks < 2) return 1;
+  const int want = std::min(chunks, (2 * 152 + ctas - 1) / ctas);
+  const int cps = (chunks + want - 1) / want;
+  return (chunks + cps - 1) / cps;
+}
+
+template <typename TOUT, bool RELU>
+int bias_act(const cmm_unet* u, const float* bias, TOUT* out, int Cout, long long hw, int B, const int* done) {
+  const long long n = (long long)B * Cout * hw;
+  k_bias_act<TOUT, RELU><<<grid_n(n), 256, 0, u->ctx->stream>>>(u->part, bias, out, Cout, hw, n, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
 template <typename TIN, typename TOUT, bool RELU, bool FLIP, int MT, int TW>
 int conv3_tc(const cmm_unet* u, const TIN* in, const bf16* w, const float* bias, TOUT* out, int Cin, int Cout, int H,
              int W, int B, const int* done) {
   constexpr int TH = 256 / TW;
-  const dim3 g(((W + TW - 1) / TW) * ((H + TH - 1) / TH), (Cout + MT * 16 - 1) / (MT * 16), B);
-  k_conv3_mma<TIN, TOUT, RELU, FLIP, MT, TW><<<g, 128, 0, u->ctx->stream>>>(in, w, bias, out, Cin, Cout, H, W, done);
+  const int gx = ((W + TW - 1) / TW) * ((H + TH - 1) / TH), gy = (Cout + MT * 16 - 1) / (MT * 16);
+  // split K only in the forward layers (FLIP is the input gradient of the backward pass)
+  const int ks = (!FLIP && u->part) ? k_slices(gx * gy * B, Cin) : 1;
+  const dim3 g(gx, gy, B * ks);
+  k_conv3_mma<TIN, TOUT, RELU, FLIP, MT, TW><<<g, 128, 0, u->ctx->stream>>>(in, w, bias, out, Cin, Cout, H, W, done,
+                                                                           ks, ks > 1 ? u->part : nullptr);
   CMM_LAUNCH_CHECK();
+  if (ks > 1) return bias_act<TOUT, RELU>(u, bias, out, Cout, (long long)H * W, B, done);
+  return CMM_OK;
+}
+
+// k_pointwise_mma over Cin -> Cout at H x W inputs (TAPS = 4: the 2x2 transposed
+// convolution to 2H x 2W; TAPS = 1: a 1x1 convolution), split K as conv3_tc.
+template <int TAPS, typename TOUT, int MT>
+int pointwise_tc(const cmm_unet* u, const bf16* in, const bf16* w, const float* bias, TOUT* out, int Cin, int Cout,
+                 int H, int W, int B, const int* done) {
+  const int gx = (H * W + 127) / 128, gy = (Cout + MT * 16 - 1) / (MT * 16);
+  const int ks = u->part ? k_slices(gx * gy * B, Cin) : 1;
+  const dim3 g(gx, gy, B * ks);
+  k_pointwise_mma<TAPS, TOUT, MT><<<g, 128, 0, u->ctx->stream>>>(in, w, bias, out, Cin, Cout, H, W, done, ks,
+                                                                 ks > 1 ? u->part : nullptr);
+  CMM_LAUNCH_CHECK();
+  if (ks > 1) return bias_act<TOUT, false>(u, bias, out, Cout, (long long)H * W * TAPS, B, done);
   return CMM_OK;
 }
 
@@ -908,14 +985,13 @@ int unet_forward(cmm_unet* u, int B, const int* done) {
     const Layer& a = u->layers[li++];
     const Layer& b = u->layers[li++];
     if (u->tensor_cores) {
-      const dim3 gp((unsigned)(((H / 2) * (W / 2) + 127) / 128), (unsigned)((w + 31) / 32), (unsigned)B);
-      k_pointwise_mma<4, bf16, 2><<<gp, 128, 0, u->ctx->stream>>>(h, u->wbf + t.woff, u->master + t.boff, u->up[l],
-                                                                    c, w, H / 2, W / 2, done);
+      CMM_TRY((pointwise_tc<4, bf16, 2>(u, h, u->wbf + t.woff, u->master + t.boff, u->up[l], c, w, H / 2, W / 2, B,
+                                         done)));
     } else {
       k_tconv_fwd<<<grid_n((long long)B * w * H * W), 256, 0, u->ctx->stream>>>(h, u->wbf + t.woff, u->master + t.boff,
                                                                                 u->up[l], c, w, H / 2, W / 2, B, done);
+      CMM_LAUNCH_CHECK();
     }
-    CMM_LAUNCH_CHECK();
     k_cat<<<grid_n((long long)B * 2 * w * H * W), 256, 0, u->ctx->stream>>>(u->up[l], u->enc_b[l], u->cat[l], w, w,
                                                                             (long long)H * W, B, done);
     CMM_LAUNCH_CHECK();
@@ -926,14 +1002,10 @@ int unet_forward(cmm_unet* u, int B, const int* done) {
   }
   const Layer& o = u->layers[li++];
   const long long HW = (long long)u->ny * u->nx;
-  if (u->tensor_cores) {
-    const dim3 gp((unsigned)((HW + 127) / 128), 1, (unsigned)B);
-    k_pointwise_mma<1, float, 1><<<gp, 128, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff, u->y_out, c,
-                                                                   3, u->ny, u->nx, done);
-  } else {
-    k_conv1_fwd<<<grid_n((long long)B * 3 * HW), 256, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff,
-                                                                          u->y_out, c, 3, HW, B, done);
-  }
+  if (u->tensor_cores)
+    return pointwise_tc<1, float, 1>(u, h, u->wbf + o.woff, u->master + o.boff, u->y_out, c, 3, u->ny, u->nx, B, done);
+  k_conv1_fwd<<<grid_n((long long)B * 3 * HW), 256, 0, u->ctx->stream>>>(h, u->wbf + o.woff, u->master + o.boff,
+                                                                        u->y_out, c, 3, HW, B, done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
@@ -1020,7 +1092,7 @@ static void free_unet(cmm_unet* u) {
   cudaSetDevice(u->ctx->device);
   cudaStreamSynchronize(u->ctx->stream);
   for (void* p : {(void*)u->master, (void*)u->wbf, (void*)u->grad, (void*)u->m, (void*)u->v, (void*)u->x_in,
-                  (void*)u->y_out, (void*)u->g0, (void*)u->g1, (void*)u->g2, (void*)u->partial})
+                  (void*)u->y_out, (void*)u->g0, (void*)u->g1, (void*)u->g2, (void*)u->partial, (void*)u->part})
     if (p) cudaFree(p);
   for (auto* vec : {&u->enc_a, &u->enc_b, &u->pooled, &u->up, &u->cat, &u->dec_a, &u->dec_b})
     for (auto* p : *vec)
@@ -1107,6 +1179,14 @@ int cmm_unet_create(cmm_ctx* ctx, int32_t ny, int32_t nx, int32_t levels, const 
   A(&u->g0, sizeof(float) * B * gmax);
   A(&u->g1, sizeof(float) * B * gmax);
   A(&u->g2, sizeof(float) * B * gmax);
+  // split-K partial sums: the largest forward output, [B][w_l][ny >> l][nx >> l] or the 3-channel output
+  long long pmax = 3LL * ny * nx;
+  for (int l = 0; l < levels; ++l) pmax = std::max(pmax, (long long)widths[l] * (ny >> l) * (nx >> l));
+  A(&u->part, sizeof(float) * B * pmax);
+  if (s == CMM_OK && cudaMemset(u->part, 0, sizeof(float) * B * pmax) != cudaSuccess) {
+    cudaGetLastError();
+    s = fail(CMM_ERR_CUDA, "cudaMemset of the U-Net partial sums failed");
+  }
   if (s != CMM_OK) {
     cmm_unet_destroy(u);
     return s;
