@@ -462,8 +462,12 @@ int cmm_op_create(cmm_ctx* ctx, cmm_pointing* pt, cmm_noise* nz, int32_t precisi
   // samples outside the map there (zero in the gather copy, never read back)
   if (s == CMM_OK) s = dalloc(&op->gather, gel * (nc == 1 ? 1 : 4) * (npix + 1));
   if (s == CMM_OK) s = dalloc(&op->acc, sizeof(double) * op->acc_stride * (npix + 1));
-  if (s == CMM_OK) s = dalloc(&op->acc32, sizeof(float) * op->acc_stride * (npix + 1));
-  if (s == CMM_OK) s = (cudaMemset(op->acc32, 0, sizeof(float) * op->acc_stride * (npix + 1)) == cudaSuccess) ? CMM_OK : fail(CMM_ERR_CUDA, "memset");
+  // one FP32 partial map per group of kFlushDets detectors of a chunk (at most
+  // kMaxPartialMaps): the two-detector path bins a whole chunk in one launch
+  op->acc32_maps = precision == CMM_PREC_F64 ? 1 : std::max(1, std::min(kMaxPartialMaps, (chunk + kFlushDets - 1) / kFlushDets));
+  const size_t acc32_elems = (size_t)op->acc32_maps * op->acc_stride * (npix + 1);
+  if (s == CMM_OK) s = dalloc(&op->acc32, sizeof(float) * acc32_elems);
+  if (s == CMM_OK) s = (cudaMemset(op->acc32, 0, sizeof(float) * acc32_elems) == cudaSuccess) ? CMM_OK : fail(CMM_ERR_CUDA, "memset");
   if (s == CMM_OK) s = dalloc(&op->tmp_a, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = dalloc(&op->tmp_b, sizeof(double) * nc * npix);
   if (s == CMM_OK) s = op_init_twiddles(op);

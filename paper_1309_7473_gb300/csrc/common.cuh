@@ -123,6 +123,14 @@ struct cmm_pointing {
 // biased.  The binning pass of such operators runs the generic kernel, which
 // reduces every sample straight into the FP64 map.
 constexpr int64_t kF32HitLimit = 8192;
+// Detectors whose samples share one FP32 partial sum before it is added into the
+// FP64 map, and the most partial maps an operator keeps (one per such group of a
+// chunk, so that a chunk's binning is one launch).
+#ifndef CMM_FLUSH_DETS
+#define CMM_FLUSH_DETS 256
+#endif
+constexpr int kFlushDets = CMM_FLUSH_DETS;
+constexpr int kMaxPartialMaps = 8;
 
 struct cmm_noise {
   int refs = 1;                // owner reference + one per dependent handle
@@ -157,7 +165,8 @@ struct cmm_op {
   void* spec = nullptr;        // [chunk][N] complex intermediate
   void* gather = nullptr;      // [npix] map copy for the projection gather
   double* acc = nullptr;       // [npix][acc_stride] FP64 accumulator of P^T
-  float* acc32 = nullptr;      // [npix][acc_stride] FP32 partial accumulator (fast path)
+  float* acc32 = nullptr;      // [maps][npix + 1][acc_stride] FP32 partial accumulators (fast path)
+  int acc32_maps = 1;          // partial maps in acc32: one per group of detectors between flushes
   int acc_stride = 0;
   void* tw = nullptr;          // twiddle tables in the op's compute type
   int32_t* pix = nullptr;      // optional [n_det][n_samp] pixel index per sample (npix: outside)

@@ -72,6 +72,7 @@ int cmm_apply_A_noalloc(cmm_op* op, const double* m_in, double* m_out) {
   cmm_op v = *op;
   v.acc = reinterpret_cast<double*>(base);
   v.acc32 = reinterpret_cast<float*>(base + acc_bytes);
+  v.acc32_maps = 1;
   v.gather = base + acc_bytes + acc32_bytes;
   v.spec = base + fixed;
   v.chunk = (int)std::min<size_t>((kNoAllocScratchBytes - fixed) / per_det, (size_t)op->pt->n_det);

@@ -90,6 +90,8 @@ struct TodArgs {
   const void* gather;   // V4<T> / T [npix]
   double* acc;          // [npix][acc_stride]
   float* acc32;         // [npix][acc_stride] FP32 partials (fast path)
+  long long acc32_map;  // elements of one partial map in acc32 (pair path: one map per flush group)
+  int flush_dets;       // detectors per partial map (the pair path's binning picks map (d - d0) / flush_dets)
   long long npix;
   const void* tod;      // float / double [n_det][n_t]
   const int* pix;       // cached pixel indices [n_det][n_t] or nullptr
@@ -182,6 +184,8 @@ static inline TodArgs make_args(const cmm_op* op, int d0) {
   a.gather = op->gather;
   a.acc = op->acc;
   a.acc32 = op->acc32;
+  a.acc32_map = 0;
+  a.flush_dets = 1 << 30;
   a.npix = pt->npix;
   a.tod = nullptr;
   a.pix = op->pix;

@@ -654,6 +654,62 @@ static int dispatch_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
   }
 }
 
+// Flush of `maps` FP32 partial maps (map_elems elements apart) into the FP64 map:
+// per pixel the partials are summed in FP64, added once, and cleared.
+template <int NC>
+__global__ void k_fast_flush_maps(float* __restrict__ acc32, int maps, long long map_elems, double* __restrict__ acc,
+                                  long long npix, const int* done) {
+  if (done && *done) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (NC == 1) {
+      double s = 0.0;
+      bool any = false;
+      for (int g = 0; g < maps; ++g) {
+        float* q = acc32 + g * map_elems + p;
+        const float v = *q;
+        if (v != 0.0f) {
+          s += (double)v;
+          *q = 0.0f;
+          any = true;
+        }
+      }
+      if (any) acc[p] += s;
+    } else {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      bool any = false;
+      for (int g = 0; g < maps; ++g) {
+        float4* q = reinterpret_cast<float4*>(acc32 + g * map_elems) + p;
+        const float4 v = *q;
+        if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f) {
+          s0 += (double)v.x;
+          s1 += (double)v.y;
+          s2 += (double)v.z;
+          *q = make_float4(0.f, 0.f, 0.f, 0.f);
+          any = true;
+        }
+      }
+      if (any) {
+        double* d = acc + 4 * p;
+        d[0] += s0;
+        d[1] += s1;
+        d[2] += s2;
+      }
+    }
+  }
+}
+
+int launch_flush(const TodArgs& a, int nc, cudaStream_t st);
+
+int launch_flush_maps(const TodArgs& a, int nc, int maps, cudaStream_t st) {
+  if (maps <= 1) return launch_flush(a, nc, st);
+  const int blocks = (int)std::min<long long>((a.npix + 256) / 256, 4096);
+  if (nc == 1) k_fast_flush_maps<1><<<blocks, 256, 0, st>>>(a.acc32, maps, a.acc32_map, a.acc, a.npix + 1, a.done);
+  else k_fast_flush_maps<3><<<blocks, 256, 0, st>>>(a.acc32, maps, a.acc32_map, a.acc, a.npix + 1, a.done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+
 int launch_flush(const TodArgs& a, int nc, cudaStream_t st) {
   // npix + 1 entries: the extra pixel is cleared too, so its FP32 sum stays bounded
   const int blocks = (int)std::min<long long>((a.npix + 256) / 256, 4096);

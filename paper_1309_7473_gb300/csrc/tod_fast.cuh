@@ -44,10 +44,6 @@ constexpr int kBinHalves = CMM_BIN_HALVES;
 #ifndef CMM_V8
 #define CMM_V8 1   // binning: a lane's 8 rotations / cached pixels by 32-byte loads (1) or 16-byte loads (0)
 #endif
-#ifndef CMM_FLUSH_DETS
-#define CMM_FLUSH_DETS 256
-#endif
-constexpr int kFlushDets = CMM_FLUSH_DETS;   // detectors between flushes of the FP32 partial map
 constexpr int kE = 16;     // elements per thread in the column FFT
 
 // Columns per CTA: 32 (one per lane) for R <= 128, 16 (one per half-warp lane)

@@ -288,6 +288,8 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   const int q = blockIdx.y;
   const bool two = 2 * q + 1 < nd;
   const int d1 = a.d0 + 2 * q, d2 = two ? d1 + 1 : d1;
+  // the FP32 partial map of this pair's group of detectors (whole pairs per group)
+  float* const acc32 = a.acc32 + (long long)((2 * q) / a.flush_dets) * a.acc32_map;
   const float scale = 1.0f / (float)a.N;
   const int npix = (int)a.npix;
   const S* Y = reinterpret_cast<const S*>(a.spec) + (size_t)q * a.N + c + i * a.C;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
           const float4 v = yv[k >> 1];
           const float u = dd ? ((k & 1) ? v.w : v.y) : ((k & 1) ? v.z : v.x);
           if (p[k] != run.cur) {
-            pair_run_close<NC>(a.acc32, run, npix, scale, sx, sy);
+            pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
             run.cur = p[k];
             run.t = 0.f;
             run.c = 0.f;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
             run.s = fmaf(r2[k].y, u, run.s);
           }
         }
-        pair_run_close<NC>(a.acc32, run, npix, scale, sx, sy);
+        pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
       } else {
         float u[8], cc[8], ss[8];
 #pragma unroll
@@ -425,8 +427,8 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
           }
         }
         BinRun run;
-        bin_push8<NC>(a.acc32, run, p, u, cc, ss, npix);
-        bin_close<NC>(a.acc32, run, npix);
+        bin_push8<NC>(acc32, run, p, u, cc, ss, npix);
+        bin_close<NC>(acc32, run, npix);
       }
     }
     if constexpr (!CACHED) __syncthreads();   // the staging is rewritten by the next pass
@@ -470,7 +472,8 @@ static int run_pair_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, boo
   constexpr int RPP = NT / (J / 8);   // rows per binning pass
   const int smem_f = (int)(sizeof(float2) * R * J);
   constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
-  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + sizeof(int) * 2 * RPP * PS +
+  // (the pixel-cache instances stage no pixels: less shared memory leaves more L1)
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + (CACHED ? 0 : sizeof(int) * 2 * RPP * PS) +
                            (CMM_PAIR_ROT_INV && !CACHED && NC == 3 ? sizeof(float2) * RPP * (J + 2) : 0));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -544,6 +547,7 @@ static int dispatch_pair_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_
 }
 
 int launch_flush(const TodArgs& a, int nc, cudaStream_t st);
+int launch_flush_maps(const TodArgs& a, int nc, int maps, cudaStream_t st);
 
 template <typename S>
 static int apply_pair_s(cmm_op* op, int d0, int nd, int pass) {
@@ -561,14 +565,19 @@ static int apply_pair_s(cmm_op* op, int d0, int nd, int pass) {
   }
   if (pass < 0 || pass == 2) {
     TraceRange tr("A: inverse column FFTs + P^T");
-    for (int g0 = 0; g0 < nd; g0 += kFlushDets) {
+    // one launch bins up to acc32_maps groups of kFlushDets detectors, each group
+    // into its own FP32 partial map; one flush then adds them all into FP64
+    const int per_launch = op->acc32_maps * kFlushDets;   // even: whole pairs per group
+    for (int g0 = 0; g0 < nd; g0 += per_launch) {
       TodArgs b = a;
-      const int gn = std::min(kFlushDets, nd - g0);   // even g0: whole pairs per group
+      const int gn = std::min(per_launch, nd - g0);
       b.d0 = a.d0 + g0;
       b.spec = reinterpret_cast<S*>(a.spec) + (long long)(g0 / 2) * a.N;
+      b.flush_dets = kFlushDets;
+      b.acc32_map = (long long)op->acc_stride * (a.npix + 1);
       if (nc == 1) CMM_TRY((dispatch_pair_T<1, S>(b, gn, 2, st, false)));
       else CMM_TRY((dispatch_pair_T<3, S>(b, gn, 2, st, false)));
-      CMM_TRY(launch_flush(b, nc, st));
+      CMM_TRY(launch_flush_maps(b, nc, (gn + kFlushDets - 1) / kFlushDets, st));
     }
   }
   return CMM_OK;
