@@ -634,13 +634,15 @@ def cufft_filter_ms(scan, noise, dev, stream):
 
 def launches_per_iteration(n_det, chunk):
     """Kernels of one circulant-PCG iteration: the A-application (map copy in, per
-    chunk one forward and one filter launch and per 256 detectors one inverse +
-    binning launch and one flush, map copy out), the CG update kernels and the
-    circulant preconditioner (Sigma^-1, 2-D FFTs, per-mode solve)."""
+    chunk one forward and one filter launch and, per 2048 detectors (eight FP32
+    partial maps of 256 detectors), one inverse + binning launch and one flush; map
+    copy out), the CG update kernels and the circulant preconditioner (Sigma^-1,
+    2-D FFTs, per-mode solve)."""
     a = 2
+    maps = min(8, max(1, math.ceil(chunk / 256)))
     for d0 in range(0, n_det, chunk):
         nd = min(chunk, n_det - d0)
-        a += 2 + 2 * math.ceil(nd / 256)
+        a += 2 + 2 * math.ceil(nd / (256 * maps))
     return a + CG_LAUNCHES + CIRC_LAUNCHES
 
 

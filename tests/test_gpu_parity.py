@@ -442,8 +442,9 @@ def _flush_case(log_nt):
 @pytest.mark.parametrize("prec", [1, 2])
 def test_apply_A_flush_groups(cmm, ctx, log_nt, prec, pair):
     """320 ACT-like detectors in one chunk (det_chunk = 0), as the 1024-detector
-    launch: the binning pass runs as two groups (256 + 64 detectors), each
-    followed by the flush of the FP32 partial map into the FP64 accumulator.
+    launch: the binning pass bins two groups (256 + 64 detectors) in one launch,
+    each into its own FP32 partial map, and one flush adds both into the FP64
+    accumulator.
     Element-wise against the oracle, on-the-fly and cached pointing; 2^18 samples
     use the 256-point column FFTs of the bench's size."""
     scan, noise, oop, m, ref = _flush_case(log_nt)
