@@ -649,7 +649,7 @@ def launches_per_iteration(n_det, chunk):
 # kernels per iteration outside the A-application, from the launch list of this
 # bench (profiles/apply_kernels_1024x2p20.md)
 CG_LAUNCHES = 7
-CIRC_LAUNCHES = 12
+CIRC_LAUNCHES = 10
 
 
 # sources of the three A-application kernels of the two-detector path: the traffic

@@ -127,6 +127,7 @@ struct cmm_precon {
   double* sig = nullptr;       // circulant: Sigma
   double* sig_inv = nullptr;   // circulant: Sigma^-1
   double* hinv = nullptr;      // circulant: per-mode packed inverse
+  float* hinv32 = nullptr;     // its FP32 copy, applied with the FP32 map FFTs of FP32/BF16 operators
   void* planes = nullptr;      // complex workspace [ncomp][npix]
   double* tmp = nullptr;       // [ncomp * npix]
   Fft2Plan plan;
@@ -761,6 +762,7 @@ int cmm_precon_destroy(cmm_precon* pc) {
   dfree(pc->sig);
   dfree(pc->sig_inv);
   dfree(pc->hinv);
+  dfree(pc->hinv32);
   dfree(pc->planes);
   dfree(pc->tmp);
   dfree(pc->plan.tw);
@@ -930,6 +932,13 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
     CMM_TRY(fft2<double>(plan64, qplanes, nc * nc, -1, nullptr, st));
     const double eps = (o && o->pd_eps > 0) ? o->pd_eps : 1e-6;
     CMM_TRY(launch_mode_inverse<double>(nc, qplanes, npix, eps, pc->hinv, scratch, st));
+    if (op->prec != CMM_PREC_F64) {
+      // the apply of an FP32 operator multiplies FP32 spectra: FP32 blocks (GB300's
+      // FP64 pipe would otherwise bound the per-mode products)
+      const int64_t nh = (int64_t)(nc == 1 ? 1 : 9) * npix;
+      CMM_TRY(dalloc(&pc->hinv32, sizeof(float) * nh));
+      CMM_TRY(launch_to_f32(pc->hinv, pc->hinv32, nh, st));
+    }
     unsigned long long h[2];
     CMM_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
     CMM_CUDA(cudaStreamSynchronize(st));
@@ -998,13 +1007,21 @@ static int circulant_apply(cmm_precon* pc, const double* r, double* z, double* p
   const int nc = op->pt->ncomp;
   const int64_t npix = op->pt->npix;
   cudaStream_t st = op->ctx->stream;
-  CMM_TRY(launch_block_apply_dot(nc, npix, pc->sig_inv, r, pc->tmp, nullptr, nullptr, done, st));
-  CMM_TRY(launch_real_to_planes<T>(pc->tmp, (V2<T>*)pc->planes, nc * npix, done, st));
+  // z = Sigma^-1 F^-1 H^-1 F Sigma^-1 r (Eq. 12), the block applies fused with the
+  // moves into and out of the complex planes
+  CMM_TRY(launch_block_to_planes<T>(nc, npix, pc->sig_inv, r, (V2<T>*)pc->planes, done, st));
   CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, -1, done, st));
-  CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv, npix, done, st));
+  bool applied32 = false;
+  if constexpr (sizeof(T) == 4) {
+    if (pc->hinv32) {
+      CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv32, npix, done, st));
+      applied32 = true;
+    }
+  }
+  if (!applied32) CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv, npix, done, st));
   CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, 1, done, st));
-  CMM_TRY(launch_planes_to_real<T>((const V2<T>*)pc->planes, pc->tmp, nc * npix, 1.0 / (double)npix, done, st));
-  return launch_block_apply_dot(nc, npix, pc->sig_inv, pc->tmp, z, r, partial, done, st);
+  return launch_planes_block_dot<T>(nc, npix, (const V2<T>*)pc->planes, 1.0 / (double)npix, pc->sig_inv, z, r,
+                                    partial, done, st);
 }
 
 extern "C" {

@@ -712,34 +712,84 @@ __global__ void k_planes_to_real(const V2<T>* __restrict__ planes, double* __res
     x[i] = (double)planes[i].x * scale;
 }
 
-// y_f = H_f^-1 x_f per mode (Hermitian packed)
+// planes = (Sigma^-1 x, 0): the first step of the circulant apply (the 3x3 block
+// apply of k_block_apply) written straight into the complex FFT planes.
 template <typename T, int NC>
-__global__ void k_mode_apply(V2<T>* __restrict__ planes, const double* __restrict__ hinv, long long npix,
+__global__ void k_block_to_planes(const double* __restrict__ blk, const double* __restrict__ x,
+                                  V2<T>* __restrict__ planes, long long npix, const int* done) {
+  if (done && *done) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (NC == 1) {
+      planes[p] = V2<T>{(T)(blk[p] * x[p]), (T)0};
+    } else {
+      const double* b = blk + 6 * p;
+      const double x0 = x[p], x1 = x[npix + p], x2 = x[2 * npix + p];
+      planes[p] = V2<T>{(T)(b[0] * x0 + b[1] * x1 + b[2] * x2), (T)0};
+      planes[npix + p] = V2<T>{(T)(b[1] * x0 + b[3] * x1 + b[4] * x2), (T)0};
+      planes[2 * npix + p] = V2<T>{(T)(b[2] * x0 + b[4] * x1 + b[5] * x2), (T)0};
+    }
+  }
+}
+
+// y = Sigma^-1 (scale Re planes) and the partial sums of w^T y: the last step of the
+// circulant apply (k_planes_to_real followed by k_block_apply) in one pass.
+template <typename T, int NC>
+__global__ void k_planes_block_dot(const V2<T>* __restrict__ planes, double scale, const double* __restrict__ blk,
+                                   double* __restrict__ y, long long npix, const double* __restrict__ w,
+                                   double* __restrict__ partial, const int* done) {
+  if (done && *done) return;
+  double acc = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (NC == 1) {
+      const double v = blk[p] * ((double)planes[p].x * scale);
+      y[p] = v;
+      if (w) acc += w[p] * v;
+    } else {
+      const double* b = blk + 6 * p;
+      const double x0 = (double)planes[p].x * scale, x1 = (double)planes[npix + p].x * scale,
+                   x2 = (double)planes[2 * npix + p].x * scale;
+      const double y0 = b[0] * x0 + b[1] * x1 + b[2] * x2;
+      const double y1 = b[1] * x0 + b[3] * x1 + b[4] * x2;
+      const double y2 = b[2] * x0 + b[4] * x1 + b[5] * x2;
+      y[p] = y0;
+      y[npix + p] = y1;
+      y[2 * npix + p] = y2;
+      if (w) acc += w[p] * y0 + w[npix + p] * y1 + w[2 * npix + p] * y2;
+    }
+  }
+  if (partial) block_sum_store(acc, partial);
+}
+
+// y_f = H_f^-1 x_f per mode (Hermitian packed)
+template <typename T, int NC, typename H>
+__global__ void k_mode_apply(V2<T>* __restrict__ planes, const H* __restrict__ hinv, long long npix,
                              const int* done) {
   if (done && *done) return;
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < npix;
        f += (long long)gridDim.x * blockDim.x) {
     if (NC == 1) {
-      const double h = hinv[f];
+      const H h = hinv[f];
       V2<T> v = planes[f];
       planes[f] = V2<T>{(T)(h * v.x), (T)(h * v.y)};
       continue;
     }
-    const double* o = hinv + 9 * f;
-    double xr[3], xi[3];
+    const H* o = hinv + 9 * f;
+    H xr[3], xi[3];
     for (int a = 0; a < 3; ++a) {
       const V2<T> v = planes[a * npix + f];
       xr[a] = v.x;
       xi[a] = v.y;
     }
     // H = [[d0, h01, h02], [conj h01, d1, h12], [conj h02, conj h12, d2]]
-    const double h01r = o[3], h01i = o[4], h02r = o[5], h02i = o[6], h12r = o[7], h12i = o[8];
-    const double y0r = o[0] * xr[0] + (h01r * xr[1] - h01i * xi[1]) + (h02r * xr[2] - h02i * xi[2]);
-    const double y0i = o[0] * xi[0] + (h01r * xi[1] + h01i * xr[1]) + (h02r * xi[2] + h02i * xr[2]);
-    const double y1r = (h01r * xr[0] + h01i * xi[0]) + o[1] * xr[1] + (h12r * xr[2] - h12i * xi[2]);
-    const double y1i = (h01r * xi[0] - h01i * xr[0]) + o[1] * xi[1] + (h12r * xi[2] + h12i * xr[2]);
-    const double y2r = (h02r * xr[0] + h02i * xi[0]) + (h12r * xr[1] + h12i * xi[1]) + o[2] * xr[2];
-    const double y2i = (h02r * xi[0] - h02i * xr[0]) + (h12r * xi[1] - h12i * xr[1]) + o[2] * xi[2];
+    const H h01r = o[3], h01i = o[4], h02r = o[5], h02i = o[6], h12r = o[7], h12i = o[8];
+    const H y0r = o[0] * xr[0] + (h01r * xr[1] - h01i * xi[1]) + (h02r * xr[2] - h02i * xi[2]);
+    const H y0i = o[0] * xi[0] + (h01r * xi[1] + h01i * xr[1]) + (h02r * xi[2] + h02i * xr[2]);
+    const H y1r = (h01r * xr[0] + h01i * xi[0]) + o[1] * xr[1] + (h12r * xr[2] - h12i * xi[2]);
+    const H y1i = (h01r * xi[0] - h01i * xr[0]) + o[1] * xi[1] + (h12r * xi[2] + h12i * xr[2]);
+    const H y2r = (h02r * xr[0] + h02i * xi[0]) + (h12r * xr[1] + h12i * xi[1]) + o[2] * xr[2];
+    const H y2i = (h02r * xi[0] - h02i * xr[0]) + (h12r * xi[1] - h12i * xr[1]) + o[2] * xi[2];
     planes[f] = V2<T>{(T)y0r, (T)y0i};
     planes[npix + f] = V2<T>{(T)y1r, (T)y1i};
     planes[2 * npix + f] = V2<T>{(T)y2r, (T)y2i};
@@ -1089,15 +1139,54 @@ template int launch_planes_to_real<float>(const float2*, double*, long long, dou
 template int launch_planes_to_real<double>(const double2*, double*, long long, double, const int*, cudaStream_t);
 
 template <typename T>
-int launch_mode_apply(int ncomp, V2<T>* planes, const double* hinv, long long npix, const int* done,
-                      cudaStream_t s) {
-  if (ncomp == 1) k_mode_apply<T, 1><<<grid_for(npix), 256, 0, s>>>(planes, hinv, npix, done);
-  else k_mode_apply<T, 3><<<grid_for(npix), 256, 0, s>>>(planes, hinv, npix, done);
+int launch_block_to_planes(int ncomp, int64_t npix, const double* blk, const double* x, V2<T>* planes,
+                           const int* done, cudaStream_t s) {
+  if (ncomp == 1) k_block_to_planes<T, 1><<<grid_for(npix), 256, 0, s>>>(blk, x, planes, npix, done);
+  else k_block_to_planes<T, 3><<<grid_for(npix), 256, 0, s>>>(blk, x, planes, npix, done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
-template int launch_mode_apply<float>(int, float2*, const double*, long long, const int*, cudaStream_t);
-template int launch_mode_apply<double>(int, double2*, const double*, long long, const int*, cudaStream_t);
+template int launch_block_to_planes<float>(int, int64_t, const double*, const double*, float2*, const int*,
+                                           cudaStream_t);
+template int launch_block_to_planes<double>(int, int64_t, const double*, const double*, double2*, const int*,
+                                            cudaStream_t);
+
+template <typename T>
+int launch_planes_block_dot(int ncomp, int64_t npix, const V2<T>* planes, double scale, const double* blk, double* y,
+                            const double* w, double* partial, const int* done, cudaStream_t s) {
+  const int g = partial ? kRedBlocks : grid_for(npix);
+  if (ncomp == 1) k_planes_block_dot<T, 1><<<g, 256, 0, s>>>(planes, scale, blk, y, npix, w, partial, done);
+  else k_planes_block_dot<T, 3><<<g, 256, 0, s>>>(planes, scale, blk, y, npix, w, partial, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+template int launch_planes_block_dot<float>(int, int64_t, const float2*, double, const double*, double*,
+                                            const double*, double*, const int*, cudaStream_t);
+template int launch_planes_block_dot<double>(int, int64_t, const double2*, double, const double*, double*,
+                                             const double*, double*, const int*, cudaStream_t);
+
+template <typename T, typename H>
+int launch_mode_apply(int ncomp, V2<T>* planes, const H* hinv, long long npix, const int* done,
+                      cudaStream_t s) {
+  if (ncomp == 1) k_mode_apply<T, 1, H><<<grid_for(npix), 256, 0, s>>>(planes, hinv, npix, done);
+  else k_mode_apply<T, 3, H><<<grid_for(npix), 256, 0, s>>>(planes, hinv, npix, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+template int launch_mode_apply<float, double>(int, float2*, const double*, long long, const int*, cudaStream_t);
+template int launch_mode_apply<float, float>(int, float2*, const float*, long long, const int*, cudaStream_t);
+template int launch_mode_apply<double, double>(int, double2*, const double*, long long, const int*, cudaStream_t);
+
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+int launch_to_f32(const double* x, float* y, long long n, cudaStream_t s) {
+  k_to_f32<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
 
 __global__ void k_window(const double* __restrict__ d, const double* __restrict__ x, double* __restrict__ y,
                          long long npix, int ncomp, int mode, const int* done) {

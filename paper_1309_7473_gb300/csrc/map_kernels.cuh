@@ -103,10 +103,17 @@ int launch_mode_inverse(int ncomp, const V2<T>* planes, long long npix, double e
 template <typename T>
 int launch_real_to_planes(const double* x, V2<T>* planes, long long n, const int* done, cudaStream_t s);
 template <typename T>
+int launch_block_to_planes(int ncomp, int64_t npix, const double* blk, const double* x, V2<T>* planes,
+                           const int* done, cudaStream_t s);
+template <typename T>
+int launch_planes_block_dot(int ncomp, int64_t npix, const V2<T>* planes, double scale, const double* blk, double* y,
+                            const double* w, double* partial, const int* done, cudaStream_t s);
+template <typename T>
 int launch_planes_to_real(const V2<T>* planes, double* x, long long n, double scale, const int* done,
                           cudaStream_t s);
-template <typename T>
-int launch_mode_apply(int ncomp, V2<T>* planes, const double* hinv, long long npix, const int* done,
+template <typename T, typename H>
+int launch_mode_apply(int ncomp, V2<T>* planes, const H* hinv, long long npix, const int* done,
                       cudaStream_t s);
+int launch_to_f32(const double* x, float* y, long long n, cudaStream_t s);
 
 }  // namespace cmm
