@@ -203,7 +203,62 @@ struct MixedPlan {
   int L;
   int nrad;
   int rad[kMaxFactors];
+  // per stage: magic multipliers of the divisions by L / rad and by p (the product
+  // of the earlier radices; 0 where p = 1), see fast_div
+  unsigned mnbf[kMaxFactors];
+  unsigned mp[kMaxFactors];
 };
+
+// t / d for 0 <= t < 2^16 and 2 <= d < 2^16 as __umulhi(t, m), m = floor((2^32 - 1) / d) + 1:
+// t m / 2^32 exceeds t / d by less than t / 2^32 < 2^-16 < 1 / d, so its floor is
+// floor(t / d).  A magic of 0 stands for d = 1.
+__host__ __device__ constexpr unsigned fast_div_magic(unsigned d) { return d > 1 ? 0xFFFFFFFFu / d + 1u : 0u; }
+__device__ __forceinline__ int fast_div(int t, unsigned m) { return m ? (int)__umulhi((unsigned)t, m) : t; }
+
+// R-point DFTs for R = 2, 3, 4, 5, y_q = sum_m x_m w^(m q), w = exp(sign 2 pi i / R):
+// sums and differences of conjugate pairs, then the real cosines and the sines
+// times sign i (the standard short transforms).
+template <typename T>
+__device__ __forceinline__ V2<T> times_i(V2<T> v, T sg) { return V2<T>{-sg * v.y, sg * v.x}; }
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(V2<T> (&x)[R], T sg) {
+  if constexpr (R == 2) {
+    const V2<T> a = x[0], b = x[1];
+    x[0] = V2<T>{a.x + b.x, a.y + b.y};
+    x[1] = V2<T>{a.x - b.x, a.y - b.y};
+  } else if constexpr (R == 3) {
+    const T h = (T)0.86602540378443864676;   // sin(2 pi / 3)
+    const V2<T> t1{x[1].x + x[2].x, x[1].y + x[2].y};
+    const V2<T> t2{x[0].x - (T)0.5 * t1.x, x[0].y - (T)0.5 * t1.y};
+    const V2<T> u = times_i(V2<T>{h * (x[1].x - x[2].x), h * (x[1].y - x[2].y)}, sg);
+    x[0] = V2<T>{x[0].x + t1.x, x[0].y + t1.y};
+    x[1] = V2<T>{t2.x + u.x, t2.y + u.y};
+    x[2] = V2<T>{t2.x - u.x, t2.y - u.y};
+  } else if constexpr (R == 4) {
+    const V2<T> a{x[0].x + x[2].x, x[0].y + x[2].y}, b{x[1].x + x[3].x, x[1].y + x[3].y};
+    const V2<T> c{x[0].x - x[2].x, x[0].y - x[2].y};
+    const V2<T> d = times_i(V2<T>{x[1].x - x[3].x, x[1].y - x[3].y}, sg);
+    x[0] = V2<T>{a.x + b.x, a.y + b.y};
+    x[1] = V2<T>{c.x + d.x, c.y + d.y};
+    x[2] = V2<T>{a.x - b.x, a.y - b.y};
+    x[3] = V2<T>{c.x - d.x, c.y - d.y};
+  } else {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;   // cos(2 pi / 5), cos(4 pi / 5)
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;    // sin(2 pi / 5), sin(4 pi / 5)
+    const V2<T> a1{x[1].x + x[4].x, x[1].y + x[4].y}, a2{x[2].x + x[3].x, x[2].y + x[3].y};
+    const V2<T> b1{x[1].x - x[4].x, x[1].y - x[4].y}, b2{x[2].x - x[3].x, x[2].y - x[3].y};
+    const V2<T> t1{x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y};
+    const V2<T> t2{x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y};
+    const V2<T> u1 = times_i(V2<T>{s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y}, sg);
+    const V2<T> u2 = times_i(V2<T>{s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y}, sg);
+    x[0] = V2<T>{x[0].x + a1.x + a2.x, x[0].y + a1.y + a2.y};
+    x[1] = V2<T>{t1.x + u1.x, t1.y + u1.y};
+    x[4] = V2<T>{t1.x - u1.x, t1.y - u1.y};
+    x[2] = V2<T>{t2.x + u2.x, t2.y + u2.y};
+    x[3] = V2<T>{t2.x - u2.x, t2.y - u2.y};
+  }
+}
 
 // cos and sin of 2 pi j / R for the radices of the map FFT (R in {2, 3, 4, 5})
 template <int R> struct RootsR;
@@ -233,25 +288,27 @@ template <> struct RootsR<5> {
 };
 
 // One mixed-radix Stockham pass of compile-time radix R; tw holds w_L^e, e < L.
-// The R-point DFT uses constant roots (unrolled), only the inter-stage twiddles
-// come from the table.
+// The R-point DFT is dft_small, only the inter-stage twiddles come from the table;
+// the butterfly and sequence indices come from multiplicative divisions (mnbf, mp:
+// the plan's magics of this stage; ns: of nseq).
 template <typename T, int R>
 __device__ __forceinline__ void mixed_pass_r(const V2<T>* __restrict__ in, V2<T>* __restrict__ out, int L, int p,
                                              int nseq, int sstride, int estride, const V2<T>* __restrict__ tw,
-                                             int sign) {
+                                             int sign, unsigned mnbf, unsigned mp, unsigned ns) {
   const int nbf = L / R;
   const int total = nbf * nseq;
   const int step = L / (p * R);
+  const T sg = (T)sign;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int s, i;
     if (sstride == 1) {
-      s = t % nseq;
-      i = t / nseq;
+      s = t - fast_div(t, ns) * nseq;
+      i = fast_div(t, ns);
     } else {
-      i = t % nbf;
-      s = t / nbf;
+      s = fast_div(t, mnbf);
+      i = t - s * nbf;
     }
-    const int k = i % p;
+    const int k = i - fast_div(i, mp) * p;
     const V2<T>* src = in + s * sstride;
     V2<T> x[R];
 #pragma unroll
@@ -265,21 +322,11 @@ __device__ __forceinline__ void mixed_pass_r(const V2<T>* __restrict__ in, V2<T>
         x[m] = cmul(v, w);
       }
     }
+    dft_small<T, R>(x, sg);
     const int base = (i - k) * R + k;
     V2<T>* dst = out + s * sstride;
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      V2<T> acc = x[0];
-#pragma unroll
-      for (int m = 1; m < R; ++m) {
-        const int j = (m * q) % R;
-        const T c = (T)RootsR<R>::c(j);
-        const T sn = (T)(sign > 0 ? RootsR<R>::s(j) : -RootsR<R>::s(j));
-        acc.x += x[m].x * c - x[m].y * sn;
-        acc.y += x[m].x * sn + x[m].y * c;
-      }
-      dst[(base + q * p) * estride] = acc;
-    }
+    for (int q = 0; q < R; ++q) dst[(base + q * p) * estride] = x[q];
   }
 }
 
@@ -287,12 +334,13 @@ __device__ __forceinline__ void mixed_pass_r(const V2<T>* __restrict__ in, V2<T>
 template <typename T>
 __device__ __forceinline__ void mixed_pass(const V2<T>* __restrict__ in, V2<T>* __restrict__ out,
                                            int L, int R, int p, int nseq, int sstride, int estride,
-                                           const V2<T>* __restrict__ tw, int sign) {
+                                           const V2<T>* __restrict__ tw, int sign, unsigned mnbf, unsigned mp,
+                                           unsigned ns) {
   switch (R) {
-    case 2: mixed_pass_r<T, 2>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
-    case 3: mixed_pass_r<T, 3>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
-    case 4: mixed_pass_r<T, 4>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
-    default: mixed_pass_r<T, 5>(in, out, L, p, nseq, sstride, estride, tw, sign); break;
+    case 2: mixed_pass_r<T, 2>(in, out, L, p, nseq, sstride, estride, tw, sign, mnbf, mp, ns); break;
+    case 3: mixed_pass_r<T, 3>(in, out, L, p, nseq, sstride, estride, tw, sign, mnbf, mp, ns); break;
+    case 4: mixed_pass_r<T, 4>(in, out, L, p, nseq, sstride, estride, tw, sign, mnbf, mp, ns); break;
+    default: mixed_pass_r<T, 5>(in, out, L, p, nseq, sstride, estride, tw, sign, mnbf, mp, ns); break;
   }
 }
 
@@ -300,9 +348,10 @@ template <typename T>
 __device__ V2<T>* block_fft_mixed(V2<T>* a, V2<T>* b, const MixedPlan& plan, int nseq, int sstride,
                                   int estride, const V2<T>* __restrict__ tw, int sign) {
   int p = 1;
+  const unsigned ns = fast_div_magic((unsigned)nseq);
   for (int st = 0; st < plan.nrad; ++st) {
     const int R = plan.rad[st];
-    mixed_pass<T>(a, b, plan.L, R, p, nseq, sstride, estride, tw, sign);
+    mixed_pass<T>(a, b, plan.L, R, p, nseq, sstride, estride, tw, sign, plan.mnbf[st], plan.mp[st], ns);
     __syncthreads();
     V2<T>* t = a;
     a = b;

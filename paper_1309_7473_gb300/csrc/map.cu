@@ -1034,6 +1034,12 @@ static bool factor_smooth(int L, MixedPlan& plan) {
   while (n % 2 == 0 && plan.nrad < kMaxFactors) { plan.rad[plan.nrad++] = 2; n /= 2; }
   while (n % 3 == 0 && plan.nrad < kMaxFactors) { plan.rad[plan.nrad++] = 3; n /= 3; }
   while (n % 5 == 0 && plan.nrad < kMaxFactors) { plan.rad[plan.nrad++] = 5; n /= 5; }
+  int p = 1;
+  for (int st = 0; st < plan.nrad; ++st) {
+    plan.mnbf[st] = fast_div_magic((unsigned)(L / plan.rad[st]));
+    plan.mp[st] = fast_div_magic((unsigned)p);
+    p *= plan.rad[st];
+  }
   return n == 1;
 }
 
@@ -1044,6 +1050,8 @@ int fft2_plan_init(Fft2Plan& p, int ny, int nx) {
   p.f64 = sizeof(T) == 8;
   if (!factor_smooth(ny, p.py) || !factor_smooth(nx, p.px))
     return fail(CMM_ERR_UNSUPPORTED, "map dimensions must factor into 2, 3 and 5");
+  if (ny >= 65536 || nx >= 65536)   // the index divisions of the line FFTs (fast_div)
+    return fail(CMM_ERR_UNSUPPORTED, "map sides must be below 65536 pixels");
   std::vector<V2<T>> h(ny + nx);
   for (int e = 0; e < nx; ++e) {
     const double a = -2.0 * M_PI * e / nx;
