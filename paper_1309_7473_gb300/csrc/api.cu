@@ -1007,21 +1007,29 @@ static int circulant_apply(cmm_precon* pc, const double* r, double* z, double* p
   const int nc = op->pt->ncomp;
   const int64_t npix = op->pt->npix;
   cudaStream_t st = op->ctx->stream;
+  V2<T>* planes = (V2<T>*)pc->planes;
   // z = Sigma^-1 F^-1 H^-1 F Sigma^-1 r (Eq. 12), the block applies fused with the
-  // moves into and out of the complex planes
-  CMM_TRY(launch_block_to_planes<T>(nc, npix, pc->sig_inv, r, (V2<T>*)pc->planes, done, st));
-  CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, -1, done, st));
-  bool applied32 = false;
-  if constexpr (sizeof(T) == 4) {
-    if (pc->hinv32) {
-      CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv32, npix, done, st));
-      applied32 = true;
+  // moves into and out of the complex planes; TQU maps travel as two complex planes
+  // (T + i Q and U), so three real transforms take two complex ones
+  if (nc == 3) {
+    CMM_TRY(launch_block_to_planes_packed<T>(npix, pc->sig_inv, r, planes, done, st));
+    CMM_TRY(fft2<T>(pc->plan, planes, 2, -1, done, st));
+    bool applied32 = false;
+    if constexpr (sizeof(T) == 4) {
+      if (pc->hinv32) {
+        CMM_TRY((launch_mode_apply_packed<T, float>(planes, pc->hinv32, op->pt->ny, op->pt->nx, done, st)));
+        applied32 = true;
+      }
     }
+    if (!applied32) CMM_TRY((launch_mode_apply_packed<T, double>(planes, pc->hinv, op->pt->ny, op->pt->nx, done, st)));
+    CMM_TRY(fft2<T>(pc->plan, planes, 2, 1, done, st));
+    return launch_planes_block_dot_packed<T>(npix, planes, 1.0 / (double)npix, pc->sig_inv, z, r, partial, done, st);
   }
-  if (!applied32) CMM_TRY(launch_mode_apply<T>(nc, (V2<T>*)pc->planes, pc->hinv, npix, done, st));
-  CMM_TRY(fft2<T>(pc->plan, (V2<T>*)pc->planes, nc, 1, done, st));
-  return launch_planes_block_dot<T>(nc, npix, (const V2<T>*)pc->planes, 1.0 / (double)npix, pc->sig_inv, z, r,
-                                    partial, done, st);
+  CMM_TRY(launch_block_to_planes<T>(nc, npix, pc->sig_inv, r, planes, done, st));
+  CMM_TRY(fft2<T>(pc->plan, planes, nc, -1, done, st));
+  CMM_TRY(launch_mode_apply<T>(nc, planes, pc->hinv, npix, done, st));
+  CMM_TRY(fft2<T>(pc->plan, planes, nc, 1, done, st));
+  return launch_planes_block_dot<T>(nc, npix, planes, 1.0 / (double)npix, pc->sig_inv, z, r, partial, done, st);
 }
 
 extern "C" {

@@ -762,6 +762,102 @@ __global__ void k_planes_block_dot(const V2<T>* __restrict__ planes, double scal
   if (partial) block_sum_store(acc, partial);
 }
 
+// The three real planes of a TQU map packed into two complex ones: plane 0 holds
+// T + i Q, plane 1 U (a real plane's spectrum is Hermitian, so the FFT of T + i Q
+// carries both, X_T(f) = (Z(f) + conj Z(-f)) / 2 and X_Q(f) = (Z(f) - conj Z(-f)) / 2i).
+// First step of the circulant apply: plane 0 = (Sigma^-1 x)_T + i (Sigma^-1 x)_Q,
+// plane 1 = (Sigma^-1 x)_U.
+template <typename T>
+__global__ void k_block_to_planes_packed(const double* __restrict__ blk, const double* __restrict__ x,
+                                         V2<T>* __restrict__ planes, long long npix, const int* done) {
+  if (done && *done) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double* b = blk + 6 * p;
+    const double x0 = x[p], x1 = x[npix + p], x2 = x[2 * npix + p];
+    planes[p] = V2<T>{(T)(b[0] * x0 + b[1] * x1 + b[2] * x2), (T)(b[1] * x0 + b[3] * x1 + b[4] * x2)};
+    planes[npix + p] = V2<T>{(T)(b[2] * x0 + b[4] * x1 + b[5] * x2), (T)0};
+  }
+}
+
+// Last step, from the packed planes: t = scale (Re P0, Im P0, Re P1), y = Sigma^-1 t,
+// and the partial sums of w^T y.
+template <typename T>
+__global__ void k_planes_block_dot_packed(const V2<T>* __restrict__ planes, double scale,
+                                          const double* __restrict__ blk, double* __restrict__ y, long long npix,
+                                          const double* __restrict__ w, double* __restrict__ partial,
+                                          const int* done) {
+  if (done && *done) return;
+  double acc = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double* b = blk + 6 * p;
+    const V2<T> z0 = planes[p];
+    const double x0 = (double)z0.x * scale, x1 = (double)z0.y * scale, x2 = (double)planes[npix + p].x * scale;
+    const double y0 = b[0] * x0 + b[1] * x1 + b[2] * x2;
+    const double y1 = b[1] * x0 + b[3] * x1 + b[4] * x2;
+    const double y2 = b[2] * x0 + b[4] * x1 + b[5] * x2;
+    y[p] = y0;
+    y[npix + p] = y1;
+    y[2 * npix + p] = y2;
+    if (w) acc += w[p] * y0 + w[npix + p] * y1 + w[2 * npix + p] * y2;
+  }
+  if (partial) block_sum_store(acc, partial);
+}
+
+// Y = H^-1 X for one mode from its packed Hermitian block (d0 d1 d2, h01 h02 h12)
+template <typename H>
+__device__ __forceinline__ void mode_mul3(const H* __restrict__ o, const H (&xr)[3], const H (&xi)[3], H (&yr)[3],
+                                          H (&yi)[3]) {
+  const H h01r = o[3], h01i = o[4], h02r = o[5], h02i = o[6], h12r = o[7], h12i = o[8];
+  yr[0] = o[0] * xr[0] + (h01r * xr[1] - h01i * xi[1]) + (h02r * xr[2] - h02i * xi[2]);
+  yi[0] = o[0] * xi[0] + (h01r * xi[1] + h01i * xr[1]) + (h02r * xi[2] + h02i * xr[2]);
+  yr[1] = (h01r * xr[0] + h01i * xi[0]) + o[1] * xr[1] + (h12r * xr[2] - h12i * xi[2]);
+  yi[1] = (h01r * xi[0] - h01i * xr[0]) + o[1] * xi[1] + (h12r * xi[2] + h12i * xr[2]);
+  yr[2] = (h02r * xr[0] + h02i * xi[0]) + (h12r * xr[1] + h12i * xi[1]) + o[2] * xr[2];
+  yi[2] = (h02r * xi[0] - h02i * xr[0]) + (h12r * xi[1] - h12i * xr[1]) + o[2] * xi[2];
+}
+
+// The per-mode products on the packed spectra: each thread takes a mode f and its
+// mirror g = -f (when f <= g in index order), unpacks X_T, X_Q from plane 0 at f and
+// g and X_U from plane 1, multiplies X(f) and X(g) = conj X(f) by their own blocks,
+// and packs Y_T + i Y_Q and Y_U back at f and g.
+template <typename T, typename H>
+__global__ void k_mode_apply_packed(V2<T>* __restrict__ planes, const H* __restrict__ hinv, int ny, int nx,
+                                    const int* done) {
+  if (done && *done) return;
+  const long long npix = (long long)ny * nx;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < npix;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int ky = (int)(f / nx), kx = (int)(f - (long long)ky * nx);
+    const long long g = (long long)(ky ? ny - ky : 0) * nx + (kx ? nx - kx : 0);
+    if (g < f) continue;
+    const V2<T> z0f = planes[f], z0g = planes[g], z1f = planes[npix + f], z1g = planes[npix + g];
+    H xr[3], xi[3];
+    xr[0] = (H)0.5 * ((H)z0f.x + (H)z0g.x);
+    xi[0] = (H)0.5 * ((H)z0f.y - (H)z0g.y);
+    xr[1] = (H)0.5 * ((H)z0f.y + (H)z0g.y);
+    xi[1] = (H)0.5 * ((H)z0g.x - (H)z0f.x);
+    xr[2] = (H)z1f.x;
+    xi[2] = (H)z1f.y;
+    H yr[3], yi[3];
+    mode_mul3<H>(hinv + 9 * f, xr, xi, yr, yi);
+    planes[f] = V2<T>{(T)(yr[0] - yi[1]), (T)(yi[0] + yr[1])};
+    planes[npix + f] = V2<T>{(T)yr[2], (T)yi[2]};
+    if (g == f) continue;
+    H gr[3], gi[3], vr[3], vi[3];
+    gr[0] = xr[0];
+    gi[0] = -xi[0];
+    gr[1] = xr[1];
+    gi[1] = -xi[1];
+    gr[2] = (H)z1g.x;
+    gi[2] = (H)z1g.y;
+    mode_mul3<H>(hinv + 9 * g, gr, gi, vr, vi);
+    planes[g] = V2<T>{(T)(vr[0] - vi[1]), (T)(vi[0] + vr[1])};
+    planes[npix + g] = V2<T>{(T)vr[2], (T)vi[2]};
+  }
+}
+
 // y_f = H_f^-1 x_f per mode (Hermitian packed)
 template <typename T, int NC, typename H>
 __global__ void k_mode_apply(V2<T>* __restrict__ planes, const H* __restrict__ hinv, long long npix,
@@ -1172,6 +1268,41 @@ template int launch_planes_block_dot<float>(int, int64_t, const float2*, double,
                                             const double*, double*, const int*, cudaStream_t);
 template int launch_planes_block_dot<double>(int, int64_t, const double2*, double, const double*, double*,
                                              const double*, double*, const int*, cudaStream_t);
+
+template <typename T>
+int launch_block_to_planes_packed(int64_t npix, const double* blk, const double* x, V2<T>* planes, const int* done,
+                                  cudaStream_t s) {
+  k_block_to_planes_packed<T><<<grid_for(npix), 256, 0, s>>>(blk, x, planes, npix, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+template int launch_block_to_planes_packed<float>(int64_t, const double*, const double*, float2*, const int*,
+                                                  cudaStream_t);
+template int launch_block_to_planes_packed<double>(int64_t, const double*, const double*, double2*, const int*,
+                                                   cudaStream_t);
+
+template <typename T>
+int launch_planes_block_dot_packed(int64_t npix, const V2<T>* planes, double scale, const double* blk, double* y,
+                                   const double* w, double* partial, const int* done, cudaStream_t s) {
+  const int g = partial ? kRedBlocks : grid_for(npix);
+  k_planes_block_dot_packed<T><<<g, 256, 0, s>>>(planes, scale, blk, y, npix, w, partial, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+template int launch_planes_block_dot_packed<float>(int64_t, const float2*, double, const double*, double*,
+                                                   const double*, double*, const int*, cudaStream_t);
+template int launch_planes_block_dot_packed<double>(int64_t, const double2*, double, const double*, double*,
+                                                    const double*, double*, const int*, cudaStream_t);
+
+template <typename T, typename H>
+int launch_mode_apply_packed(V2<T>* planes, const H* hinv, int ny, int nx, const int* done, cudaStream_t s) {
+  k_mode_apply_packed<T, H><<<grid_for((long long)ny * nx), 256, 0, s>>>(planes, hinv, ny, nx, done);
+  CMM_LAUNCH_CHECK();
+  return CMM_OK;
+}
+template int launch_mode_apply_packed<float, float>(float2*, const float*, int, int, const int*, cudaStream_t);
+template int launch_mode_apply_packed<float, double>(float2*, const double*, int, int, const int*, cudaStream_t);
+template int launch_mode_apply_packed<double, double>(double2*, const double*, int, int, const int*, cudaStream_t);
 
 template <typename T, typename H>
 int launch_mode_apply(int ncomp, V2<T>* planes, const H* hinv, long long npix, const int* done,

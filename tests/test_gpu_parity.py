@@ -296,6 +296,25 @@ def test_circulant_precon(cmm, ctx, prec, ncomp, taper):
         assert pc.clamped() == ref.n_clamped
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(27, 25), (30, 45)])
+def test_circulant_precon_odd_and_mixed_sides(cmm, ctx, prec, shape):
+    """Maps whose sides are odd (27 x 25: radices 3 and 5 only, every Fourier mode but
+    the zero one paired with a distinct mirror) or mixed (30 x 45): the line FFTs'
+    radix passes and the TQU packing of the apply into two complex planes."""
+    ny, nx = shape
+    scan = gen.small_scan(cfg=231, ny=ny, nx=nx, n_t=1 << 12, ncols=4, nrows=2, throw_px=1.2 * nx, ncomp=3)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=231)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    oop = om.make_operator(scan, noise)
+    pc = cmm.Precon(op, cmm.PRECON_CIRCULANT, taper_sigma_px=3.0)
+    ref = om.CirculantPrecon(oop, taper_sigma=3.0)
+    r = gen.random_maps(3, ny, nx, 1, cfg=232)[0]
+    err = rel(host(pc.apply(dev(r))), ref(r))
+    print(f"circulant apply {ny}x{nx}, precision {prec}: error {err:.2e}")
+    assert err < (1e-9 if prec == 0 else 1e-5)
+
+
 @pytest.mark.parametrize("ncomp", [1, 3])
 def test_white_level_weights(cmm, ctx, ncomp):
     """The alternative reading of diag(N^-1) in Eq. 3 and Eq. 7 (white level
