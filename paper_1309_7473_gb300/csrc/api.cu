@@ -1129,6 +1129,7 @@ int cmm_precon_clamped(cmm_precon* pc, int64_t* n_clamped) {
 // ------------------------------------------------------------------ solver
 struct SolveBufs {
   double *r, *z, *p, *q, *r_old, *p1, *p2, *p3;
+  bool cg_f32 = false;   // FP32 CG: z is rounded to FP32 before its dot products
 };
 
 // ||b - A x|| / ||b|| recomputed from x (one A-application), in the op's CG
@@ -1151,6 +1152,8 @@ static int true_residual(cmm_op* op, const double* b, const double* x, double bn
 static int precon_step(cmm_op* op, cmm_precon* pc, const SolveBufs& v, SolverDev* dst, bool flexible) {
   const int64_t n = (int64_t)op->pt->ncomp * op->pt->npix;
   cudaStream_t st = op->ctx->stream;
+  // FP64 PCG: the preconditioner's last kernel forms the partials of r^T z itself
+  if (!flexible && !v.cg_f32) return precon_apply_dev(pc, v.r, v.z, v.p1, &dst->done);
   CMM_TRY(precon_apply_dev(pc, v.r, v.z, nullptr, &dst->done));
   return launch_solver_z(v.z, v.r, flexible ? v.r_old : nullptr, n, dst, v.p1, flexible ? v.p3 : nullptr, st);
 }
@@ -1291,6 +1294,7 @@ int cmm_solve(cmm_op* op, cmm_precon* pc, const double* b, double* x, const cmm_
     fcg.wpart = op->fcg + 2 * (int64_t)fcg.win * n;
   }
   SolveBufs v;
+  v.cg_f32 = opts->cg_f32 != 0;
   v.r = op->sol;
   v.z = v.r + n;
   v.p = v.z + n;
@@ -1585,6 +1589,7 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
     if (!op->sol) CMM_TRY(dalloc(&op->sol, sizeof(double) * (5 * m + 3 * kRedBlocks)));
     if (!op->sol_state) CMM_TRY(dalloc(&op->sol_state, sizeof(SolverDev)));
     SolveBufs& v = vb[i];
+    v.cg_f32 = opts->cg_f32 != 0;
     v.r = op->sol;
     v.z = v.r + m;
     v.p = v.z + m;
