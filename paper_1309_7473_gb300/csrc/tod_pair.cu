@@ -58,6 +58,9 @@ namespace cmm {
 #ifndef CMM_INV_CARVEOUT
 #define CMM_INV_CARVEOUT -1   // inverse pass: shared-memory carveout in percent (-1: the driver's choice)
 #endif
+#ifndef CMM_PAIR_WSHARE
+#define CMM_PAIR_WSHARE 0   // filter: 1 = each of two partner threads computes the weights of half the bin pairs (slower: its 32 KB of shared memory cost L1)
+#endif
 #ifndef CMM_PAIR_DD_UNROLL
 #define CMM_PAIR_DD_UNROLL 2   // binning: the two detectors' runs unrolled (2) or in a loop (1)
 #endif
@@ -220,6 +223,24 @@ __global__ void __launch_bounds__(PairFilterShape<RadProd<RC...>::value, E>::THR
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
+  const bool wrap = row == 0;
+  const int n = (int)a.N;
+  // (a, b) of a bin pair, shared by the two partner threads: each computes those of
+  // its first E / 2 elements into wb[slot][thread][e] (the other half pairs with the
+  // partner's first half)
+  float2* const wb = smf + ROWS * ROWLEN;
+  if (CMM_PAIR_WSHARE && active) {
+    const float4 cf1 = reinterpret_cast<const float4*>(a.coef)[d1];
+    const float4 cf2 = reinterpret_cast<const float4*>(a.coef)[d2];
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+      const int k = row + a.R * (i + e * TPR);
+      const int kf = min(k, n - k);
+      float w1, w2;
+      pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
+      wb[(rs * TPR + i) * (E / 2) + e] = make_float2(0.5f * (w1 + w2), 0.5f * (w1 - w2));
+    }
+  }
   __syncthreads();
   // Each thread filters its own elements in registers.  Position pos of row `row`
   // holds Z(k), k = row + R pos; Z(n - k) sits at position C - 1 - pos of row
@@ -230,19 +251,32 @@ __global__ void __launch_bounds__(PairFilterShape<RadProd<RC...>::value, E>::THR
   if (active) {
     const float4 cf1 = reinterpret_cast<const float4*>(a.coef)[d1];
     const float4 cf2 = reinterpret_cast<const float4*>(a.coef)[d2];
-    const bool wrap = row == 0;
-    const RowAddr<PS> pa{smf + (single ? rs : (rs ^ 1)) * ROWLEN};
-    const int n = (int)a.N;
+    const int prs = single ? rs : (rs ^ 1);
+    const RowAddr<PS> pa{smf + prs * ROWLEN};
+    // the partner thread and, for its element pe, the element of ours it pairs with
+    const int pi = wrap ? ((TPR - i) & (TPR - 1)) : (TPR - 1 - i);
+    const float2* const wown = wb + (rs * TPR + i) * (E / 2);
+    const float2* const wpar = wb + (prs * TPR + pi) * (E / 2);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = i + e * TPR;
       const int pp = wrap ? ((C - pos) & (C - 1)) : (C - 1 - pos);
       const float2 B = pa.ld(pp);
-      const int k = row + a.R * pos;
-      const int kf = min(k, n - k);
-      float w1, w2;
-      pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
-      const float ha = 0.5f * (w1 + w2), hb = 0.5f * (w1 - w2);
+      float ha, hb;
+      if (!CMM_PAIR_WSHARE || (wrap && i == 0 && e == E / 2)) {
+        // computed here: the sharing is off, or the element pairs with itself
+        const int k = row + a.R * pos;
+        const int kf = min(k, n - k);
+        float w1, w2;
+        pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
+        ha = 0.5f * (w1 + w2);
+        hb = 0.5f * (w1 - w2);
+      } else {
+        // row 0's thread 0 pairs element e with (E - e) mod E of itself
+        const float2 h = e < E / 2 ? wown[e] : wpar[(wrap && i == 0) ? E - e : E - 1 - e];
+        ha = h.x;
+        hb = h.y;
+      }
       x[e] = make_float2(fmaf(ha, x[e].x, hb * B.x), fmaf(ha, x[e].y, -hb * B.y));
     }
   }
@@ -521,7 +555,8 @@ static int run_pair_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
   constexpr int ROWS = PairFilterShape<C, E>::ROWS;
   constexpr int PAIRS = ROWS / 2;
   constexpr int PS = clog2(E);
-  const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS));
+  constexpr int TPR = C / E;
+  const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS)) + (CMM_PAIR_WSHARE ? sizeof(float2) * ROWS * TPR * (E / 2) : 0);
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_filter<S, E, RC...>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return CMM_OK;
