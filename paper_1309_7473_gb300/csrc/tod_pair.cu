@@ -43,32 +43,12 @@ namespace cmm {
 #ifndef CMM_PAIR_ROT
 #define CMM_PAIR_ROT 1     // forward pass: 0 = (cos 2phi, sin 2phi) from the FP32 table, 1 = from the boresight record
 #endif
-#ifndef CMM_PAIR_ROT_INV
-#define CMM_PAIR_ROT_INV 0   // binning: 0 = from the FP32 table, 1 = from the boresight record, staged beside the pixels
-#endif
 #ifndef CMM_PAIR_XOR
 #define CMM_PAIR_XOR 1     // pixel staging: 0 = rows padded to J + 8 ints, 1 = XOR-swizzled 16-byte chunks (no pad)
-#endif
-#ifndef CMM_PAIR_EARLY_ROT
-#define CMM_PAIR_EARLY_ROT 1   // binning: 1 = the lane's rotation loads issued before the staging barrier
 #endif
 #ifndef CMM_PAIR_FILTER_THREADS_PER_SM
 #define CMM_PAIR_FILTER_THREADS_PER_SM 1024
 #endif
-#ifndef CMM_INV_CARVEOUT
-#define CMM_INV_CARVEOUT -1   // inverse pass: shared-memory carveout in percent (-1: the driver's choice)
-#endif
-#ifndef CMM_PAIR_WSHARE
-#define CMM_PAIR_WSHARE 0   // filter: 1 = each of two partner threads computes the weights of half the bin pairs (slower: its 32 KB of shared memory cost L1)
-#endif
-#ifndef CMM_PAIR_DD_UNROLL
-#define CMM_PAIR_DD_UNROLL 2   // binning: the two detectors' runs unrolled (2) or in a loop (1)
-#endif
-#ifndef CMM_PAIR_ROTACC
-#define CMM_PAIR_ROTACC 1   // binning runs: 1 = sums of u cos 2phi, u sin 2phi, rotated by psi_d at the run's end; 0 = per sample
-#endif
-
-constexpr int kDdUnroll = CMM_PAIR_DD_UNROLL;
 
 // A binning run in the frame of the scan rotation: for samples of one detector on
 // one pixel, sums of u, u cos 2phi_t and u sin 2phi_t; the detector angle psi_d
@@ -225,22 +205,6 @@ __global__ void __launch_bounds__(PairFilterShape<RadProd<RC...>::value, E>::THR
   for (int e = 0; e < E; ++e) ad.st_at(bi, e * TPR, x[e]);
   const bool wrap = row == 0;
   const int n = (int)a.N;
-  // (a, b) of a bin pair, shared by the two partner threads: each computes those of
-  // its first E / 2 elements into wb[slot][thread][e] (the other half pairs with the
-  // partner's first half)
-  float2* const wb = smf + ROWS * ROWLEN;
-  if (CMM_PAIR_WSHARE && active) {
-    const float4 cf1 = reinterpret_cast<const float4*>(a.coef)[d1];
-    const float4 cf2 = reinterpret_cast<const float4*>(a.coef)[d2];
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-      const int k = row + a.R * (i + e * TPR);
-      const int kf = min(k, n - k);
-      float w1, w2;
-      pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
-      wb[(rs * TPR + i) * (E / 2) + e] = make_float2(0.5f * (w1 + w2), 0.5f * (w1 - w2));
-    }
-  }
   __syncthreads();
   // Each thread filters its own elements in registers.  Position pos of row `row`
   // holds Z(k), k = row + R pos; Z(n - k) sits at position C - 1 - pos of row
@@ -251,32 +215,17 @@ __global__ void __launch_bounds__(PairFilterShape<RadProd<RC...>::value, E>::THR
   if (active) {
     const float4 cf1 = reinterpret_cast<const float4*>(a.coef)[d1];
     const float4 cf2 = reinterpret_cast<const float4*>(a.coef)[d2];
-    const int prs = single ? rs : (rs ^ 1);
-    const RowAddr<PS> pa{smf + prs * ROWLEN};
-    // the partner thread and, for its element pe, the element of ours it pairs with
-    const int pi = wrap ? ((TPR - i) & (TPR - 1)) : (TPR - 1 - i);
-    const float2* const wown = wb + (rs * TPR + i) * (E / 2);
-    const float2* const wpar = wb + (prs * TPR + pi) * (E / 2);
+    const RowAddr<PS> pa{smf + (single ? rs : (rs ^ 1)) * ROWLEN};
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int pos = i + e * TPR;
       const int pp = wrap ? ((C - pos) & (C - 1)) : (C - 1 - pos);
       const float2 B = pa.ld(pp);
-      float ha, hb;
-      if (!CMM_PAIR_WSHARE || (wrap && i == 0 && e == E / 2)) {
-        // computed here: the sharing is off, or the element pairs with itself
-        const int k = row + a.R * pos;
-        const int kf = min(k, n - k);
-        float w1, w2;
-        pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
-        ha = 0.5f * (w1 + w2);
-        hb = 0.5f * (w1 - w2);
-      } else {
-        // row 0's thread 0 pairs element e with (E - e) mod E of itself
-        const float2 h = e < E / 2 ? wown[e] : wpar[(wrap && i == 0) ? E - e : E - 1 - e];
-        ha = h.x;
-        hb = h.y;
-      }
+      const int k = row + a.R * pos;
+      const int kf = min(k, n - k);
+      float w1, w2;
+      pair_weights(a, d1, d2, cf1, cf2, two, kf, w1, w2);
+      const float ha = 0.5f * (w1 + w2), hb = 0.5f * (w1 - w2);
       x[e] = make_float2(fmaf(ha, x[e].x, hb * B.x), fmaf(ha, x[e].y, -hb * B.y));
     }
   }
@@ -309,7 +258,6 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   // 16-sample group), so that the eight lanes of a quarter-warp load hit eight
   // distinct 4-bank groups (PS = 24 words = 8 mod 32 shifts consecutive rows).
   constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
-  constexpr int RS = J + 2;   // row stride (complex) of the staged rotations
   static_assert(LPR >= 1 && RPP <= R && R % RPP == 0 && (RPP * J) % NT == 0, "binning layout");
   if (a.done && *a.done) return;
   extern __shared__ __align__(16) float2 smf[];
@@ -342,16 +290,15 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
   const float2 pol1 = pol[d1], pol2 = pol[d2];
   const int2 off1 = a.det_off[d1], off2 = a.det_off[d2];
   int* pst = reinterpret_cast<int*>(smf + R * BS);   // pixels of one pass: [detector][RPP][PS]
-  float2* rst = reinterpret_cast<float2*>(pst + 2 * RPP * PS);   // rotations of one pass: [RPP][RS]
   const float4* smf4 = reinterpret_cast<const float4*>(smf);
-  constexpr bool ROT_STAGED = CMM_PAIR_ROT_INV && !CACHED && NC == 3;
   for (int kr0 = 0; kr0 < R; kr0 += RPP) {
     const int kr = kr0 + br;
     const int tq = c0 + SPL * bq + kr * a.C;   // the lane's first sample
+    // the lane's 8 rotations (64 bytes, 64-byte aligned: tq is a multiple of 8),
+    // issued before the staging so that they are in flight across its barrier
     float2 r2[8];
-    auto load_rot = [&]() {
-      if constexpr (CMM_V8 && !ROT_STAGED) {
-        // the lane's 8 rotations (64 bytes, 64-byte aligned: tq is a multiple of 8)
+    if (NC == 3) {
+      if constexpr (CMM_V8) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float v[8];
@@ -362,14 +309,12 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
       } else {
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
-          const float4 v = ROT_STAGED ? reinterpret_cast<const float4*>(rst)[(br * RS + 8 * bq + k) / 2]
-                                      : __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
+          const float4 v = __ldg(reinterpret_cast<const float4*>(a.rot2 + tq + k));
           r2[k] = make_float2(v.x, v.y);
           r2[k + 1] = make_float2(v.z, v.w);
         }
       }
-    };
-    if (NC == 3 && CMM_PAIR_EARLY_ROT && !ROT_STAGED) load_rot();
+    }
     if constexpr (!CACHED) {
       // pixels of both detectors for the pass's RPP x J samples, lanes on
       // consecutive samples (coalesced boresight reads)
@@ -384,28 +329,25 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
                                     : (col & ~15) | ((col & 4) << 1) | ((col & 8) >> 1) | (col & 3);
         pst[rr * PS + sw] = pixel_fast<PERIODIC>(b, off1, a.ny, a.nx, npix);
         pst[(RPP + rr) * PS + sw] = pixel_fast<PERIODIC>(b, off2, a.ny, a.nx, npix);
-        if constexpr (ROT_STAGED) rst[rr * RS + col] = rot2_of_bore(b);
       }
       __syncthreads();
     }
-    const int t8 = tq;
-    if (NC == 3 && !(CMM_PAIR_EARLY_ROT && !ROT_STAGED)) load_rot();
     // the lane's 8 filtered samples of both detectors (real part: d1, imaginary: d2)
     float4 yv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) yv[j] = smf4[(kr * BS + 8 * bq) / 2 + j];
-#pragma unroll kDdUnroll
+#pragma unroll
     for (int dd = 0; dd < 2; ++dd) {
       if (dd == 1 && !two) break;
       int p[8];
       int4 P0, P1;
       if constexpr (CACHED && CMM_V8) {
-        // 32 bytes, 32-byte aligned (t8 and n_t are multiples of 8)
-        ld_cs_v8(a.pix + (size_t)(dd ? d2 : d1) * a.n_t + t8, p);
+        // 32 bytes, 32-byte aligned (tq and n_t are multiples of 8)
+        ld_cs_v8(a.pix + (size_t)(dd ? d2 : d1) * a.n_t + tq, p);
         P0 = make_int4(p[0], p[1], p[2], p[3]);
         P1 = make_int4(p[4], p[5], p[6], p[7]);
       } else if constexpr (CACHED) {
-        const int* pixd = a.pix + (size_t)(dd ? d2 : d1) * a.n_t + t8;
+        const int* pixd = a.pix + (size_t)(dd ? d2 : d1) * a.n_t + tq;
         P0 = __ldcs(reinterpret_cast<const int4*>(pixd));
         P1 = __ldcs(reinterpret_cast<const int4*>(pixd + 4));
       } else {
@@ -423,47 +365,27 @@ __global__ void __launch_bounds__(ColShape<R>::THREADS, ColShape<R>::MINB_INV) k
       }
       p[0] = P0.x; p[1] = P0.y; p[2] = P0.z; p[3] = P0.w;
       p[4] = P1.x; p[5] = P1.y; p[6] = P1.z; p[7] = P1.w;
-      if constexpr (CMM_PAIR_ROTACC) {
-        const float2 pl = dd ? pol2 : pol1;
-        const float sx = scale * pl.x, sy = scale * pl.y;
-        PairRun run;
+      const float2 pl = dd ? pol2 : pol1;
+      const float sx = scale * pl.x, sy = scale * pl.y;
+      PairRun run;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float4 v = yv[k >> 1];
-          const float u = dd ? ((k & 1) ? v.w : v.y) : ((k & 1) ? v.z : v.x);
-          if (p[k] != run.cur) {
-            pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
-            run.cur = p[k];
-            run.t = 0.f;
-            run.c = 0.f;
-            run.s = 0.f;
-          }
-          run.t += u;
-          if (NC == 3) {
-            run.c = fmaf(r2[k].x, u, run.c);
-            run.s = fmaf(r2[k].y, u, run.s);
-          }
+      for (int k = 0; k < 8; ++k) {
+        const float4 v = yv[k >> 1];
+        const float u = dd ? ((k & 1) ? v.w : v.y) : ((k & 1) ? v.z : v.x);
+        if (p[k] != run.cur) {
+          pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
+          run.cur = p[k];
+          run.t = 0.f;
+          run.c = 0.f;
+          run.s = 0.f;
         }
-        pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
-      } else {
-        float u[8], cc[8], ss[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          u[2 * j] = (dd ? yv[j].y : yv[j].x) * scale;
-          u[2 * j + 1] = (dd ? yv[j].w : yv[j].z) * scale;
-        }
+        run.t += u;
         if (NC == 3) {
-          const float2 pl = dd ? pol2 : pol1;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            cc[k] = pl.x * r2[k].x - pl.y * r2[k].y;
-            ss[k] = pl.y * r2[k].x + pl.x * r2[k].y;
-          }
+          run.c = fmaf(r2[k].x, u, run.c);
+          run.s = fmaf(r2[k].y, u, run.s);
         }
-        BinRun run;
-        bin_push8<NC>(acc32, run, p, u, cc, ss, npix);
-        bin_close<NC>(acc32, run, npix);
       }
+      pair_run_close<NC>(acc32, run, npix, scale, sx, sy);
     }
     if constexpr (!CACHED) __syncthreads();   // the staging is rewritten by the next pass
   }
@@ -507,16 +429,12 @@ static int run_pair_T_c(const TodArgs& a, int nd, int pass, cudaStream_t st, boo
   const int smem_f = (int)(sizeof(float2) * R * J);
   constexpr int PS = CMM_PAIR_XOR ? J + (J == 32 ? 8 : 0) : J + 8;
   // (the pixel-cache instances stage no pixels: less shared memory leaves more L1)
-  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + (CACHED ? 0 : sizeof(int) * 2 * RPP * PS) +
-                           (CMM_PAIR_ROT_INV && !CACHED && NC == 3 ? sizeof(float2) * RPP * (J + 2) : 0));
+  const int smem_i = (int)(sizeof(float2) * R * (J + 2) + (CACHED ? 0 : sizeof(int) * 2 * RPP * PS));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_fwd<NC, S, R, PERIODIC, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_f));
     CMM_CUDA(cudaFuncSetAttribute(k_pair_inv_bin<NC, S, R, PERIODIC, CACHED>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_i));
-    if (CMM_INV_CARVEOUT >= 0)
-      CMM_CUDA(cudaFuncSetAttribute(k_pair_inv_bin<NC, S, R, PERIODIC, CACHED>,
-                                    cudaFuncAttributePreferredSharedMemoryCarveout, CMM_INV_CARVEOUT));
     return CMM_OK;
   }
   const dim3 g(a.C / J, (nd + 1) / 2);
@@ -555,8 +473,7 @@ static int run_pair_F(const TodArgs& a, int nd, cudaStream_t st, bool attr_only)
   constexpr int ROWS = PairFilterShape<C, E>::ROWS;
   constexpr int PAIRS = ROWS / 2;
   constexpr int PS = clog2(E);
-  constexpr int TPR = C / E;
-  const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS)) + (CMM_PAIR_WSHARE ? sizeof(float2) * ROWS * TPR * (E / 2) : 0);
+  const size_t smem = sizeof(float2) * ROWS * (C + (C >> PS));
   if (attr_only) {
     CMM_CUDA(cudaFuncSetAttribute(k_pair_filter<S, E, RC...>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return CMM_OK;
