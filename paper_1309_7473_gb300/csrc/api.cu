@@ -126,6 +126,7 @@ struct cmm_precon {
   double* inv = nullptr;       // binned / Jacobi: inverse blocks
   double* sig = nullptr;       // circulant: Sigma
   double* sig_inv = nullptr;   // circulant: Sigma^-1
+  float* sig_inv32 = nullptr;  // its FP32 copy, for the apply of FP32/BF16 operators
   double* hinv = nullptr;      // circulant: per-mode packed inverse
   float* hinv32 = nullptr;     // its FP32 copy, applied with the FP32 map FFTs of FP32/BF16 operators
   void* planes = nullptr;      // complex workspace [ncomp][npix]
@@ -761,6 +762,7 @@ int cmm_precon_destroy(cmm_precon* pc) {
   dfree(pc->inv);
   dfree(pc->sig);
   dfree(pc->sig_inv);
+  dfree(pc->sig_inv32);
   dfree(pc->hinv);
   dfree(pc->hinv32);
   dfree(pc->planes);
@@ -938,6 +940,8 @@ static int circulant_build(cmm_precon* pc, const cmm_precon_opts* o) {
       const int64_t nh = (int64_t)(nc == 1 ? 1 : 9) * npix;
       CMM_TRY(dalloc(&pc->hinv32, sizeof(float) * nh));
       CMM_TRY(launch_to_f32(pc->hinv, pc->hinv32, nh, st));
+      CMM_TRY(dalloc(&pc->sig_inv32, sizeof(float) * nb * npix));
+      CMM_TRY(launch_to_f32(pc->sig_inv, pc->sig_inv32, nb * npix, st));
     }
     unsigned long long h[2];
     CMM_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -1012,18 +1016,23 @@ static int circulant_apply(cmm_precon* pc, const double* r, double* z, double* p
   // moves into and out of the complex planes; TQU maps travel as two complex planes
   // (T + i Q and U), so three real transforms take two complex ones
   if (nc == 3) {
-    CMM_TRY(launch_block_to_planes_packed<T>(npix, pc->sig_inv, r, planes, done, st));
-    CMM_TRY(fft2<T>(pc->plan, planes, 2, -1, done, st));
-    bool applied32 = false;
     if constexpr (sizeof(T) == 4) {
-      if (pc->hinv32) {
+      if (pc->hinv32 && pc->sig_inv32) {
+        // FP32 operator: Sigma^-1 and the mode blocks in FP32 (FP64 build, FP32 copies)
+        CMM_TRY((launch_block_to_planes_packed<T, float>(npix, pc->sig_inv32, r, planes, done, st)));
+        CMM_TRY(fft2<T>(pc->plan, planes, 2, -1, done, st));
         CMM_TRY((launch_mode_apply_packed<T, float>(planes, pc->hinv32, op->pt->ny, op->pt->nx, done, st)));
-        applied32 = true;
+        CMM_TRY(fft2<T>(pc->plan, planes, 2, 1, done, st));
+        return launch_planes_block_dot_packed<T, float>(npix, planes, 1.0 / (double)npix, pc->sig_inv32, z, r,
+                                                        partial, done, st);
       }
     }
-    if (!applied32) CMM_TRY((launch_mode_apply_packed<T, double>(planes, pc->hinv, op->pt->ny, op->pt->nx, done, st)));
+    CMM_TRY((launch_block_to_planes_packed<T, double>(npix, pc->sig_inv, r, planes, done, st)));
+    CMM_TRY(fft2<T>(pc->plan, planes, 2, -1, done, st));
+    CMM_TRY((launch_mode_apply_packed<T, double>(planes, pc->hinv, op->pt->ny, op->pt->nx, done, st)));
     CMM_TRY(fft2<T>(pc->plan, planes, 2, 1, done, st));
-    return launch_planes_block_dot_packed<T>(npix, planes, 1.0 / (double)npix, pc->sig_inv, z, r, partial, done, st);
+    return launch_planes_block_dot_packed<T, double>(npix, planes, 1.0 / (double)npix, pc->sig_inv, z, r, partial,
+                                                     done, st);
   }
   CMM_TRY(launch_block_to_planes<T>(nc, npix, pc->sig_inv, r, planes, done, st));
   CMM_TRY(fft2<T>(pc->plan, planes, nc, -1, done, st));

@@ -767,14 +767,16 @@ __global__ void k_planes_block_dot(const V2<T>* __restrict__ planes, double scal
 // carries both, X_T(f) = (Z(f) + conj Z(-f)) / 2 and X_Q(f) = (Z(f) - conj Z(-f)) / 2i).
 // First step of the circulant apply: plane 0 = (Sigma^-1 x)_T + i (Sigma^-1 x)_Q,
 // plane 1 = (Sigma^-1 x)_U.
-template <typename T>
-__global__ void k_block_to_planes_packed(const double* __restrict__ blk, const double* __restrict__ x,
+// B: the type of Sigma^-1 and of its products (double, or float for FP32 operators,
+// whose spectra are FP32: GB300's FP64 pipe bounds the FP64 form)
+template <typename T, typename B>
+__global__ void k_block_to_planes_packed(const B* __restrict__ blk, const double* __restrict__ x,
                                          V2<T>* __restrict__ planes, long long npix, const int* done) {
   if (done && *done) return;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
-    const double* b = blk + 6 * p;
-    const double x0 = x[p], x1 = x[npix + p], x2 = x[2 * npix + p];
+    const B* b = blk + 6 * p;
+    const B x0 = (B)x[p], x1 = (B)x[npix + p], x2 = (B)x[2 * npix + p];
     planes[p] = V2<T>{(T)(b[0] * x0 + b[1] * x1 + b[2] * x2), (T)(b[1] * x0 + b[3] * x1 + b[4] * x2)};
     planes[npix + p] = V2<T>{(T)(b[2] * x0 + b[4] * x1 + b[5] * x2), (T)0};
   }
@@ -782,21 +784,22 @@ __global__ void k_block_to_planes_packed(const double* __restrict__ blk, const d
 
 // Last step, from the packed planes: t = scale (Re P0, Im P0, Re P1), y = Sigma^-1 t,
 // and the partial sums of w^T y.
-template <typename T>
+template <typename T, typename B>
 __global__ void k_planes_block_dot_packed(const V2<T>* __restrict__ planes, double scale,
-                                          const double* __restrict__ blk, double* __restrict__ y, long long npix,
+                                          const B* __restrict__ blk, double* __restrict__ y, long long npix,
                                           const double* __restrict__ w, double* __restrict__ partial,
                                           const int* done) {
   if (done && *done) return;
   double acc = 0.0;
+  const B sc = (B)scale;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
-    const double* b = blk + 6 * p;
+    const B* b = blk + 6 * p;
     const V2<T> z0 = planes[p];
-    const double x0 = (double)z0.x * scale, x1 = (double)z0.y * scale, x2 = (double)planes[npix + p].x * scale;
-    const double y0 = b[0] * x0 + b[1] * x1 + b[2] * x2;
-    const double y1 = b[1] * x0 + b[3] * x1 + b[4] * x2;
-    const double y2 = b[2] * x0 + b[4] * x1 + b[5] * x2;
+    const B x0 = (B)z0.x * sc, x1 = (B)z0.y * sc, x2 = (B)planes[npix + p].x * sc;
+    const double y0 = (double)(b[0] * x0 + b[1] * x1 + b[2] * x2);
+    const double y1 = (double)(b[1] * x0 + b[3] * x1 + b[4] * x2);
+    const double y2 = (double)(b[2] * x0 + b[4] * x1 + b[5] * x2);
     y[p] = y0;
     y[npix + p] = y1;
     y[2 * npix + p] = y2;
@@ -1269,30 +1272,35 @@ template int launch_planes_block_dot<float>(int, int64_t, const float2*, double,
 template int launch_planes_block_dot<double>(int, int64_t, const double2*, double, const double*, double*,
                                              const double*, double*, const int*, cudaStream_t);
 
-template <typename T>
-int launch_block_to_planes_packed(int64_t npix, const double* blk, const double* x, V2<T>* planes, const int* done,
+template <typename T, typename B>
+int launch_block_to_planes_packed(int64_t npix, const B* blk, const double* x, V2<T>* planes, const int* done,
                                   cudaStream_t s) {
-  k_block_to_planes_packed<T><<<grid_for(npix), 256, 0, s>>>(blk, x, planes, npix, done);
+  k_block_to_planes_packed<T, B><<<grid_for(npix), 256, 0, s>>>(blk, x, planes, npix, done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
-template int launch_block_to_planes_packed<float>(int64_t, const double*, const double*, float2*, const int*,
-                                                  cudaStream_t);
-template int launch_block_to_planes_packed<double>(int64_t, const double*, const double*, double2*, const int*,
-                                                   cudaStream_t);
+template int launch_block_to_planes_packed<float, float>(int64_t, const float*, const double*, float2*, const int*,
+                                                         cudaStream_t);
+template int launch_block_to_planes_packed<float, double>(int64_t, const double*, const double*, float2*,
+                                                          const int*, cudaStream_t);
+template int launch_block_to_planes_packed<double, double>(int64_t, const double*, const double*, double2*,
+                                                           const int*, cudaStream_t);
 
-template <typename T>
-int launch_planes_block_dot_packed(int64_t npix, const V2<T>* planes, double scale, const double* blk, double* y,
+template <typename T, typename B>
+int launch_planes_block_dot_packed(int64_t npix, const V2<T>* planes, double scale, const B* blk, double* y,
                                    const double* w, double* partial, const int* done, cudaStream_t s) {
   const int g = partial ? kRedBlocks : grid_for(npix);
-  k_planes_block_dot_packed<T><<<g, 256, 0, s>>>(planes, scale, blk, y, npix, w, partial, done);
+  k_planes_block_dot_packed<T, B><<<g, 256, 0, s>>>(planes, scale, blk, y, npix, w, partial, done);
   CMM_LAUNCH_CHECK();
   return CMM_OK;
 }
-template int launch_planes_block_dot_packed<float>(int64_t, const float2*, double, const double*, double*,
-                                                   const double*, double*, const int*, cudaStream_t);
-template int launch_planes_block_dot_packed<double>(int64_t, const double2*, double, const double*, double*,
-                                                    const double*, double*, const int*, cudaStream_t);
+template int launch_planes_block_dot_packed<float, float>(int64_t, const float2*, double, const float*, double*,
+                                                          const double*, double*, const int*, cudaStream_t);
+template int launch_planes_block_dot_packed<float, double>(int64_t, const float2*, double, const double*, double*,
+                                                           const double*, double*, const int*, cudaStream_t);
+template int launch_planes_block_dot_packed<double, double>(int64_t, const double2*, double, const double*,
+                                                            double*, const double*, double*, const int*,
+                                                            cudaStream_t);
 
 template <typename T, typename H>
 int launch_mode_apply_packed(V2<T>* planes, const H* hinv, int ny, int nx, const int* done, cudaStream_t s) {

@@ -115,11 +115,11 @@ template <typename T, typename H>
 int launch_mode_apply(int ncomp, V2<T>* planes, const H* hinv, long long npix, const int* done,
                       cudaStream_t s);
 int launch_to_f32(const double* x, float* y, long long n, cudaStream_t s);
-template <typename T>
-int launch_block_to_planes_packed(int64_t npix, const double* blk, const double* x, V2<T>* planes, const int* done,
+template <typename T, typename B>
+int launch_block_to_planes_packed(int64_t npix, const B* blk, const double* x, V2<T>* planes, const int* done,
                                   cudaStream_t s);
-template <typename T>
-int launch_planes_block_dot_packed(int64_t npix, const V2<T>* planes, double scale, const double* blk, double* y,
+template <typename T, typename B>
+int launch_planes_block_dot_packed(int64_t npix, const V2<T>* planes, double scale, const B* blk, double* y,
                                    const double* w, double* partial, const int* done, cudaStream_t s);
 template <typename T, typename H>
 int launch_mode_apply_packed(V2<T>* planes, const H* hinv, int ny, int nx, const int* done, cudaStream_t s);
