@@ -281,7 +281,9 @@ int cmm_dot(cmm_op* op, const double* x, const double* y, int64_t n, double* res
  *   (Eq. 11) inverted per Fourier mode with eigenvalues floored at pd_eps * max;
  *   applied as z = Sigma^-1 F^-1 H^-1 F Sigma^-1 r (Eq. 12).
  * opts may be NULL (taper off, centre reference pixel, pd_eps 1e-6).  The circulant
- * build runs ncomp applications of A.
+ * build runs ncomp applications of A, all in FP64; FP32/BF16 operators apply FP32
+ * copies of Sigma^-1 and H^-1 with FP32 map FFTs.  The map sides must factor into
+ * 2, 3 and 5 and be below 65536 pixels (else CMM_ERR_UNSUPPORTED).
  */
 int cmm_precon_create(cmm_op* op, int32_t kind, const cmm_precon_opts* opts, cmm_precon** out);
 int cmm_precon_destroy(cmm_precon* pc);
