@@ -1168,6 +1168,13 @@ int fft2_plan_init(Fft2Plan& p, int ny, int nx) {
 template int fft2_plan_init<float>(Fft2Plan&, int, int);
 template int fft2_plan_init<double>(Fft2Plan&, int, int);
 
+#ifndef CMM_FFT_ROW_KB
+#define CMM_FFT_ROW_KB 96
+#endif
+#ifndef CMM_FFT_COL_KB
+#define CMM_FFT_COL_KB 64
+#endif
+
 template <typename T>
 static int lines_launch(const Fft2Plan& p, V2<T>* data, int nplanes, bool rows, int sign, const int* done,
                         cudaStream_t s) {
@@ -1176,7 +1183,7 @@ static int lines_launch(const Fft2Plan& p, V2<T>* data, int nplanes, bool rows, 
   const long long line_stride = rows ? p.nx : 1;
   const long long elem_stride = rows ? 1 : p.nx;
   const long long plane_stride = (long long)p.ny * p.nx;
-  const int budget = 96 * 1024;
+  const int budget = (rows ? CMM_FFT_ROW_KB : CMM_FFT_COL_KB) * 1024;   // shared memory per CTA
   int lpc = std::max(1, std::min(rows ? 4 : 16, budget / (int)(2 * sizeof(V2<T>) * L)));
   const size_t smem = 2 * sizeof(V2<T>) * (size_t)lpc * L;
   const V2<T>* tw = reinterpret_cast<const V2<T>*>(p.tw) + (rows ? 0 : p.nx);
