@@ -436,7 +436,7 @@ def run_ours(args, rank, world):
         "setup_seconds": round(setup_s, 2),
         "clocks": clocks,
     }
-    out["gpu_launches"] = launches_per_iteration(scan.n_det, chunk_dets) * args.steps
+    out["gpu_launches"] = launches_per_iteration(scan.n_det, chunk_dets) * args.steps + SETUP_LAUNCHES + CIRC_LAUNCHES
     return out
 
 
@@ -646,10 +646,15 @@ def launches_per_iteration(n_det, chunk):
     return a + CG_LAUNCHES + CIRC_LAUNCHES
 
 
-# kernels per iteration outside the A-application, from the launch list of this
-# bench (profiles/apply_kernels_1024x2p20.md)
-CG_LAUNCHES = 7
-CIRC_LAUNCHES = 10
+# kernels per iteration outside the A-application (cmm_solve's FP64 PCG step):
+# p^T q partials, alpha, x and r update with ||r||^2, convergence check, beta, p update
+CG_LAUNCHES = 6
+# the circulant apply: Sigma^-1 into the packed planes, 2 + 2 line-FFT passes, the
+# per-mode products, Sigma^-1 out of the planes with the r^T z partials
+CIRC_LAUNCHES = 7
+# once per cmm_solve call before its iterations: b^T b (partials and sum), r0, the
+# solver state (plus one preconditioner apply, CIRC_LAUNCHES)
+SETUP_LAUNCHES = 4
 
 
 # sources of the three A-application kernels of the two-detector path: the traffic
