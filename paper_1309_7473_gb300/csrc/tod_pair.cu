@@ -17,14 +17,16 @@
 //   k_pair_fwd:     P m for both detectors at (c, kr), the R-point column FFTs over
 //                   kr (register-resident, one shared-memory exchange), times
 //                   w_{n_t}^{c k1}.
-//   k_pair_filter:  row pairs (k1, R - k1): C-point row FFTs, the pair filter, the
-//                   inverse row FFTs and the conjugate twiddle.
+//   k_pair_filter:  row pairs (k1, R - k1): C-point row FFTs, the pair filter in
+//                   registers (each thread against the elements of one partner
+//                   thread), the inverse row FFTs and the conjugate twiddle.
 //   k_pair_inv_bin: inverse column FFTs into a padded tile; each lane then takes 8
 //                   consecutive samples of a row and bins them for each detector
 //                   with a run accumulator (one vector FP32 reduction per run into
-//                   the L2-resident partial map).
-//   k_fast_flush (tod_fast.cu) adds the FP32 partial map into the FP64 map after
-//   every kFlushDets detectors (256), as on the one-detector path.
+//                   the L2-resident partial map of its group of kFlushDets = 256
+//                   detectors).
+//   k_fast_flush_maps (tod_fast.cu) sums a launch's partial maps in FP64 into the
+//   FP64 map, so no FP32 sum covers more than 256 detectors.
 //
 // A chunk with an odd number of detectors pairs its last detector with nothing
 // (the imaginary part stays zero and is not binned).
