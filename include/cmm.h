@@ -397,6 +397,21 @@ int cmm_unet_train_step(cmm_unet* net, int32_t batch, const float* in, const flo
  * waits for the result. */
 int cmm_spectra(cmm_ctx* ctx, int32_t ny, int32_t nx, double pix_rad, int32_t nmaps, const double* maps,
                 int32_t nbins, double lmax, double* cls_host, int64_t* nmodes_host);
+/* When each spectrum bin of a sequence of PCG iterates has converged (Results
+ * section: the step after which the iterate's spectrum stays within `level`
+ * (the paper uses 0.1) times cosmic variance of the input map's).  Host-only
+ * arithmetic, no device call.  iters: host int32 [n_snap], the iteration of each
+ * snapshot; cls_iter: host double [n_snap][nspec][nbins] (cmm_spectra of the
+ * snapshots); cls_true: host double [nspec][nbins], the input map's spectra;
+ * nmodes: host int64 [nbins] modes per bin.  sigma_b = cls_true * sqrt(2 /
+ * max(nmodes_b, 1)); out: host int32 [nspec][nbins] receives iters[k + 1] for the
+ * last snapshot k with |cls_iter - cls_true| >= level sigma_b (iters[0] when there
+ * is none, -1 when it is the last snapshot).  A bin whose cls_true is 0 has no
+ * scale and reads as converged at iters[0].  CMM_ERR_ARG on a NULL pointer, a
+ * non-positive count or level <= 0. */
+int cmm_spectra_converged_at(int32_t n_snap, const int32_t* iters, int32_t nspec, int32_t nbins,
+                             const double* cls_iter, const double* cls_true, const int64_t* nmodes, double level,
+                             int32_t* out);
 
 /* ---------------------------------------------------------------- batches and tuning
  * Batched solves (many Monte-Carlo realisations or patches of uneven size): n

@@ -72,6 +72,7 @@ _SIGS = {
     "cmm_noise_set_correlated": [_vp, _i32, _vp, _vp, _vp, _vp],
     "cmm_noise_set_table": [_vp, _vp],
     "cmm_spectra": [_vp, _i32, _i32, C.c_double, _i32, _vp, _i32, C.c_double, _vp, _vp],
+    "cmm_spectra_converged_at": [_i32, _vp, _i32, _i32, _vp, _vp, _vp, C.c_double, _vp],
     "cmm_noise_diag": [_vp, _vp],
     "cmm_op_create": [_vp, _vp, _vp, _i32, _i32, _PP],
     "cmm_op_destroy": [_vp],
@@ -220,6 +221,22 @@ def cmm_spectra(ctx, maps, pix_rad, nbins, lmax):
     _check(_lib.cmm_spectra(ctx, ny, nx, float(pix_rad), nm, _dev(maps, name="maps"), int(nbins), float(lmax),
                             cls.ctypes.data_as(C.c_void_p), nmodes.ctypes.data_as(C.c_void_p)))
     return cls, nmodes
+
+
+def cmm_spectra_converged_at(cls_iter, iters, cls_true, nmodes, level=0.1):
+    """cls_iter [n_snap, nspec, nbins] at the iterations ``iters``, cls_true [nspec,
+    nbins], nmodes [nbins]; returns int32 [nspec, nbins] (see include/cmm.h)."""
+    ci, pci = _host(cls_iter, np.float64)
+    ct, pct = _host(cls_true, np.float64)
+    it, pit = _host(iters, np.int32)
+    nm, pnm = _host(nmodes, np.int64)
+    if ci.ndim != 3 or ct.shape != ci.shape[1:] or it.shape != (ci.shape[0],) or nm.shape != (ci.shape[2],):
+        raise ValueError("shapes: cls_iter [n_snap, nspec, nbins], iters [n_snap], cls_true [nspec, nbins], "
+                         "nmodes [nbins]")
+    out = np.zeros(ct.shape, dtype=np.int32)
+    _check(_lib.cmm_spectra_converged_at(ci.shape[0], pit, ci.shape[1], ci.shape[2], pci, pct, pnm, float(level),
+                                         out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 def cmm_noise_set_table(h, w=None):

@@ -1638,8 +1638,9 @@ int cmm_batch_solve(int32_t n, cmm_op* const* ops, cmm_precon* const* pcs, const
   long long total = 0;
   for (long long w : work) total += w;
   // automatic width: one lane when the solves average 10^8 samples or more (their
-  // passes fill the GPU and concurrent solves only share the L2), else 8 lanes (at
-  // 128 detectors x 2^18 samples on 256x256 maps, 8 lanes run 15 % faster than 1)
+  // passes fill the GPU and concurrent solves only share the L2), else 8 lanes (64
+  // solves of 128 detectors x 2^18 samples on 256x256 maps: 0.442 s in 8 lanes
+  // against 0.539 s one after another)
   int width = opts->batch_width > 0 ? opts->batch_width : (total / n >= 100000000LL ? 1 : 8);
   width = std::max(1, std::min(width, n));
   std::vector<int> order(n);

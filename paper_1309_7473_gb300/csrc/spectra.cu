@@ -8,7 +8,11 @@
 // phi = atan2(ly, lx): E = Q cos 2phi + U sin 2phi, B = -Q sin 2phi + U cos 2phi.
 // C_b = pix^2 / (ny nx) * mean over the modes of bin b of |X|^2, for TT, EE and BB;
 // bin b holds lmax b / nbins <= |l| < lmax (b + 1) / nbins (l = 0 excluded).
-#include <math.h>
+// cmm_spectra_converged_at turns the spectra of a sequence of iterates into the
+// Results section's count: the iteration from which each bin stays within a
+// fraction of cosmic variance of the input map's spectrum (host arithmetic on a
+// few hundred numbers).
+#include <cmath>
 
 #include <vector>
 
@@ -112,6 +116,27 @@ int cmm_spectra(cmm_ctx* ctx, int32_t ny, int32_t nx, double pix_rad, int32_t nm
   if (counts) cudaFree(counts);
   if (plan.tw) cudaFree(plan.tw);
   return s;
+}
+
+int cmm_spectra_converged_at(int32_t n_snap, const int32_t* iters, int32_t nspec, int32_t nbins,
+                             const double* cls_iter, const double* cls_true, const int64_t* nmodes, double level,
+                             int32_t* out) {
+  if (n_snap <= 0 || nspec <= 0 || nbins <= 0 || !iters || !cls_iter || !cls_true || !nmodes || !out ||
+      !(level > 0))
+    return fail(CMM_ERR_ARG, "bad argument");
+  for (int c = 0; c < nspec; ++c)
+    for (int b = 0; b < nbins; ++b) {
+      const size_t cb = (size_t)c * nbins + b;
+      // cosmic variance of the bin: C_b sqrt(2 / n_b) over its n_b modes
+      const double sigma = cls_true[cb] * std::sqrt(2.0 / (double)std::max<int64_t>(nmodes[b], 1));
+      int last_far = -1;   // last snapshot whose error is level sigma or more
+      for (int k = 0; k < n_snap; ++k) {
+        const double e = std::fabs(cls_iter[(size_t)k * nspec * nbins + cb] - cls_true[cb]);
+        if (sigma > 0 ? e >= level * sigma : false) last_far = k;
+      }
+      out[cb] = last_far + 1 < n_snap ? iters[last_far + 1] : -1;
+    }
+  return CMM_OK;
 }
 
 }  // extern "C"
