@@ -189,7 +189,11 @@ def test_A_against_dense_matrices():
     scan = gen.small_scan(cfg=102, ny=4, nx=5, n_t=256, ncols=2, nrows=1, spacing_px=1.0,
                           throw_px=8.0, rot=25.0)
     noise = gen.noise_params(scan.n_det, sigma=1.0, fknee=20.0, alpha=2.0, scatter=0.3, cfg=102)
-    op = om.make_operator(scan, noise)
+    # two pixels that the scan hits are masked by hand: their samples leave P (R4)
+    mask = om.pixel_mask(scan)
+    hit = np.flatnonzero(om.hit_blocks(scan)[:, 0, 0] > 0)
+    mask[hit[[1, 4]]] = False
+    op = om.make_operator(scan, noise, mask=mask)
     nc, npix, n_t = 3, scan.npix, scan.n_t
     pix = om.sample_pixels(scan, np.arange(scan.n_det))
     wts = om.sample_weights(scan, np.arange(scan.n_det))
@@ -214,7 +218,12 @@ def test_A_against_dense_matrices():
     np.testing.assert_allclose(a, ref, atol=1e-10 * np.abs(ref).max())
     # nothing outside the unmasked set
     rest = np.setdiff1d(np.arange(nc * npix), sel)
-    assert np.abs(a_ref[np.ix_(rest, rest)]).max() == 0.0 if rest.size else True
+    assert rest.size >= 2 * nc and np.abs(a_ref[np.ix_(rest, rest)]).max() == 0.0
+    # on every unknown, masked ones included: A e_p = 0 and (A m)_p = 0 for a masked
+    # pixel p, whatever m holds there
+    m = np.random.default_rng(7).standard_normal((nc, scan.ny, scan.nx))
+    am = a_ref @ m.ravel()
+    np.testing.assert_allclose(om.apply_A(op, m).ravel(), am, atol=1e-10 * np.abs(am).max())
 
 
 def test_A_symmetric_positive(tiny, tiny_dense):
@@ -243,6 +252,10 @@ def test_white_noise_T_only_is_hit_count():
             hits[p] += 1
     m = np.random.default_rng(1).standard_normal((1, 6, 7))
     np.testing.assert_allclose(om.apply_A(op, m).ravel(), hits * m.ravel() / 4.0, atol=1e-12)
+    # Jacobi (Eq. 5, a = 1): unit-weight blocks, the hit counts themselves
+    mj = om.BlockPrecon(op, "jacobi")
+    np.testing.assert_array_equal(mj.blocks[:, 0, 0], hits * op.mask)
+    np.testing.assert_allclose(mj(m).ravel()[op.mask], m.ravel()[op.mask] / hits[op.mask], rtol=1e-14)
     # M_B = M_J * 4 = A^-1 there: PCG stops after one iteration
     mb = om.BlockPrecon(op, "binned")
     b = om.apply_A(op, m)
@@ -302,6 +315,30 @@ def test_pcg_matches_dense_cholesky(tiny, tiny_dense):
                                    atol=1e-8 * np.abs(ref).max())
 
 
+def test_pcg_from_a_given_start(tiny, tiny_dense):
+    """A start x0 enters through r0 = b - A x0: from the solution itself PCG stops
+    at once, from any other start it reaches the same solution."""
+    a, (comp, pixs) = tiny_dense
+    g = np.random.default_rng(12)
+    b = np.zeros(tiny.shape)
+    b.reshape(3, -1)[comp, pixs] = g.standard_normal(comp.size)
+    xs = np.zeros(tiny.shape)
+    xs.reshape(3, -1)[comp, pixs] = np.linalg.solve(a, b.reshape(3, -1)[comp, pixs])
+    mb = om.BlockPrecon(tiny)
+    x, info = om.pcg(lambda v: om.apply_A(tiny, v), mb, b, tol=1e-9, x0=xs)
+    assert info.iterations == 0 and info.rel_resid[0] <= 1e-9
+    np.testing.assert_array_equal(x, xs)
+    x0 = np.zeros(tiny.shape)
+    x0.reshape(3, -1)[comp, pixs] = g.standard_normal(comp.size)
+    for flexible, window in ((False, 1), (True, 1), (True, 4)):
+        x, info = om.pcg(lambda v: om.apply_A(tiny, v), mb, b, tol=1e-12, maxit=2000, x0=x0,
+                         flexible=flexible, window=window)
+        assert info.converged
+        assert info.rel_resid[0] == pytest.approx(
+            np.linalg.norm(b - om.apply_A(tiny, x0)) / np.linalg.norm(b), rel=1e-12)
+        np.testing.assert_allclose(x, xs, atol=1e-8 * np.abs(xs).max())
+
+
 def test_noise_free_data_recover_input_map():
     """Sec. Test setup: noise-free TOD d = P m recover m (on the unmasked pixels)."""
     scan = gen.small_scan(cfg=105, ny=12, nx=12, n_t=1 << 12, ncols=4, nrows=2, throw_px=18.0)
@@ -334,6 +371,13 @@ def test_anorm_error_identity(tiny, tiny_dense):
         assert terms[i:].sum() == pytest.approx(exact, rel=1e-6)
     est = om.anorm_estimate(terms, d=4)
     assert np.all(est <= np.cumsum(terms[::-1])[::-1][:est.size] * (1 + 1e-12))
+    # each term is the drop of the squared error A-norm over one step, so the d-term
+    # estimate is ||x_i - x||_A^2 - ||x_{i+d} - x||_A^2
+    err = [float((it.reshape(3, -1)[comp, pixs] - xs) @ a @ (it.reshape(3, -1)[comp, pixs] - xs))
+           for it in info.iterates]
+    assert est.size == info.iterations - 3
+    for i in (0, 1, 3, est.size - 1):
+        assert est[i] == pytest.approx(err[i] - err[i + 4], rel=1e-6, abs=1e-9 * err[0])
 
 
 def test_flexible_cg_equals_pcg_for_fixed_preconditioner(tiny):
@@ -464,17 +508,18 @@ def test_eq11_fourier_convention_against_direct_convolution():
     np.testing.assert_allclose(om.circulant_forward(q, x), ref, atol=1e-12)
 
 
-@pytest.mark.parametrize("diagonal", [False, True])
-def test_circulant_is_exact_inverse_on_bccb_scan(diagonal):
+@pytest.mark.parametrize("diagonal, ref", [(False, None), (True, None), (True, 1 * 8 + 2), (False, 5 * 8 + 7)])
+def test_circulant_is_exact_inverse_on_bccb_scan(diagonal, ref):
     """On a periodic translation-invariant scan A is block circulant (footnotes of
-    Sec. Implementation), so M_C = A^-1 and PCG converges in one iteration."""
+    Sec. Implementation), so M_C = A^-1 and PCG converges in one iteration, whichever
+    pixel the row is measured at (Eq. 10: offsets taken from the reference)."""
     ny, nx = 6, 8
     n_t = 16 * math.lcm(nx, ny)
     scan = gen.bccb_scan(ny, nx, n_t, diagonal=diagonal)
     noise = gen.Noise(np.ones(scan.n_det), np.full(scan.n_det, 30.0), np.full(scan.n_det, 2.0))
     op = om.make_operator(scan, noise)
     assert op.mask.all()
-    mc = om.CirculantPrecon(op)
+    mc = om.CirculantPrecon(op, ref=ref)
     assert mc.n_clamped == 0
     g = np.random.default_rng(4)
     x = g.standard_normal(op.shape)
@@ -496,12 +541,38 @@ def test_circulant_precon_symmetric_and_taper(tiny):
     assert tp[0, 0] == 1.0
     assert tp[1, 0] == pytest.approx(math.exp(-1 / 8)) and tp[5, 0] == tp[1, 0]
     assert tp[0, 6] == tp[0, 1]
+    # even in the offset on both sides, odd (7) and even (6): g(k) = g(-k)
+    np.testing.assert_array_equal(tp[:, 1:], tp[:, :0:-1])
+    np.testing.assert_array_equal(tp[1:, :], tp[:0:-1, :])
     assert np.all(om.taper(4, 4, math.inf) == 1.0)
     # R9 reference pixel and its fallback
     mask = np.ones(64, bool)
     assert om.reference_pixel(mask, 8, 8) == 4 * 8 + 4
+    assert om.reference_pixel(np.ones(60, bool), 6, 10) == 3 * 10 + 5
+    assert om.reference_pixel(np.ones(63, bool), 9, 7) == 4 * 7 + 3
     mask[4 * 8 + 4] = False
     assert om.reference_pixel(mask, 8, 8) == 3 * 8 + 4
+
+
+def test_circulant_inverts_its_model_and_floors_relative(tiny):
+    """Eq. 8 and Eq. 12 describe one matrix and its inverse: with no mode floored,
+    M_C (Sigma^T Q Sigma x) = x on a TQU scan whose mode blocks are complex
+    Hermitian, not real symmetric (so a dropped conjugate or a transposed block
+    shows); the model Sigma^T Q Sigma is symmetric once q_k = q_{-k}^T (R5).  With a
+    floor that bites, the smallest eigenvalue of the floored mode blocks is pd_eps
+    times the largest (R6: relative to the largest over all modes)."""
+    mc = om.CirculantPrecon(tiny)
+    assert mc.n_clamped == 0
+    h = np.conj(np.fft.fft2(mc.q, axes=(-2, -1))).transpose(2, 3, 0, 1)
+    assert np.abs(h - h.transpose(0, 1, 3, 2)).max() > 1e-3 * np.abs(h).max()
+    g = np.random.default_rng(9)
+    x, y = g.standard_normal((2,) + tiny.shape)
+    np.testing.assert_allclose(mc(mc.approx_A(x)), x, atol=1e-12 * np.abs(x).max())
+    assert np.vdot(x, mc.approx_A(y)) == pytest.approx(np.vdot(y, mc.approx_A(x)), rel=1e-12)
+    mf = om.CirculantPrecon(tiny, pd_eps=0.5)
+    lam = np.linalg.eigvalsh(np.linalg.inv(mf.h_inv))
+    assert mf.n_clamped > 0 and lam.max() > 1.05
+    assert lam.min() == pytest.approx(0.5 * lam.max(), rel=1e-10)
 
 
 def test_circulant_beats_binned_on_drift_scan():

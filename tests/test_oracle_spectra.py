@@ -20,6 +20,11 @@ def test_plane_wave_closed_form():
     assert np.isclose(cls[0, b], expect, rtol=1e-12)
     assert np.all(np.delete(cls[0], b) < 1e-20 * expect)
     assert np.all(cls[1:] == 0)
+    # in bins 1/20 as wide the wave still lands at |l| = l0, the wavenumbers scaled
+    # by the map's own side in each direction
+    fine, _ = osp.flat_spectra(m, PIX, 20 * nbins, lmax)
+    bf = int(l0 // (lmax / (20 * nbins)))
+    assert fine[0, bf] > 0 and np.all(np.delete(fine[0], bf) < 1e-20 * fine[0, bf])
 
 
 def test_pure_e_has_no_b_and_rotation_swaps():

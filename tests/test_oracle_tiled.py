@@ -14,6 +14,10 @@ def test_windows_partition_of_unity():
         assert np.all(w >= 0) and np.allclose(w.sum(axis=0), 1.0, atol=1e-14)
         # smooth: no jump larger than the raised cosine's slope allows
         assert np.abs(np.diff(w, axis=1)).max() <= np.pi / 2 * t / n + 1e-12
+    # centres at (i + 1/2) n / t, half height half a spacing away
+    w = om.tile_windows_1d(16, 4)
+    np.testing.assert_allclose(w[:, [2, 6, 10, 14]], np.eye(4), atol=1e-15)
+    np.testing.assert_allclose([w[1, 4], w[1, 8], w[2, 8], w[2, 12]], 0.5, atol=1e-15)
     phi = om.tile_windows(30, 40, 2, 3)
     assert phi.shape == (6, 30, 40) and np.allclose(phi.sum(axis=0), 1.0)
 
