@@ -117,28 +117,35 @@ class ClockSampler:
     def summary(self):
         if self.proc is None:
             return None
-        rows = []
         with open(self.path) as fh:
             lines = fh.readlines()
         try:
             os.remove(self.path)
         except OSError:
             pass
-        for line in lines:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
-            except ValueError:
-                continue
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
-        loaded = [r for r in rows if r[2] > 200.0] or rows
-        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+        return summarize_clocks(lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock under load (samples drawing more than 200 W, else all), the
+    maximum SM clock and the throttle reasons seen active, from nvidia-smi rows in
+    ClockSampler.FIELDS order (csv, no header, no units); None without a valid row."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+    loaded = [r for r in rows if r[2] > 200.0] or rows
+    return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
 
 
 # ---------------------------------------------------------------- oracle timing
