@@ -375,6 +375,9 @@ int cmm_unet_get_params(cmm_unet* net, float* params);
  * correction starts near zero); resets Adam.  Draws on the host (64-bit Mersenne
  * twister), uploads, and waits. */
 int cmm_unet_init(cmm_unet* net, uint64_t seed);
+/* out = U(in): device FP32 [batch][3][ny][nx] each, 1 <= batch <= batch_max (else
+ * CMM_ERR_ARG).  in is rounded to the BF16 activations first, so in and out may be
+ * the same buffer. */
 int cmm_unet_forward(cmm_unet* net, int32_t batch, const float* in, float* out);
 /* Loss and its gradient w.r.t. the parameters (grad: device FP32 [n], may be NULL);
  * *loss_host (may be NULL) receives the loss and makes the call wait. */
