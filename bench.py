@@ -240,6 +240,19 @@ class OraclePool:
                 "nproc": self.cores, "cpu_model": self.model}
 
 
+def oracle_solve_estimate(rate, n_s, solves):
+    """The oracle's time to solve the whole workload to 1e-6, estimated (a full FP64
+    CPU solve of 10^9 samples over hundreds of iterations takes hours): one
+    A-application of all n_s samples at the measured oracle rate, times the
+    circulant PCG iterations the GPU needed.  None without that solve."""
+    circ = (solves or {}).get("circulant")
+    if not circ or not rate:
+        return None
+    return {"value": n_s / rate * circ["iterations"], "unit": "s", "iterations": circ["iterations"],
+            "what": "estimate, not run: oracle samples/s over one A-application of the workload, "
+                    "times the GPU's circulant iterations to 1e-6"}
+
+
 def job_ms(ms, world, device):
     """The job's time: the slowest rank's (max over ranks; the ranks ran after a barrier)."""
     if world <= 1:
@@ -957,6 +970,8 @@ def main():
         rate, sample = pool.rate(args, args.cpu_seconds)
         pool.close()
         out["cpu_baseline"] = pool.baseline(rate, sample)
+        out["cpu_baseline"]["solve_to_1e-6_estimate"] = oracle_solve_estimate(
+            rate, args.n_det * args.n_t, out.get("solves_to_1e-6"))
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -43,3 +43,11 @@ def test_launch_count_of_one_iteration():
     assert bench.launches_per_iteration(4096, 4096) == 2 + 2 + 2 * 2 + 6 + 7
     # a ragged last chunk of 100 detectors still takes its own launches
     assert bench.launches_per_iteration(612, 256) == 2 + 3 * 4 + 6 + 7
+
+
+def test_oracle_solve_estimate():
+    est = bench.oracle_solve_estimate(2.0e8, 1 << 30, {"circulant": {"iterations": 434}, "binned": {}})
+    assert est["value"] == pytest.approx((1 << 30) / 2.0e8 * 434)
+    assert est["iterations"] == 434 and "estimate" in est["what"]
+    assert bench.oracle_solve_estimate(2.0e8, 1 << 30, None) is None
+    assert bench.oracle_solve_estimate(2.0e8, 1 << 30, {"binned": {"iterations": 3}}) is None
