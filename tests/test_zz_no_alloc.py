@@ -1,6 +1,7 @@
 """cmm_apply_A_noalloc (A with its temporaries in the library's static scratch
-array) against cmm_apply_A on the same operator and map, over consecutive calls
-that leave the shared array holding another operator's data in between.
+array) against the FP64 oracle, and against cmm_apply_A on the same operator and
+map over consecutive calls that leave the shared array holding another operator's
+data in between.
 
 Collected last so it also runs after every other GPU test in one process; it
 builds its own context and passes alone in a fresh process too.
@@ -61,6 +62,25 @@ def test_noalloc_matches_apply_A_on_consecutive_calls(cmm, ctx, prec):
             torch.cuda.synchronize()
             assert torch.isfinite(out).all()
             assert rel(out, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_oracle(cmm, ctx, prec):
+    """Against the FP64 oracle itself, on the scan and map of the small A-application
+    parity test, with its error measure (the larger of the norm-wise and the
+    element-wise relative error)."""
+    from oracle import mapmaker as om
+    scan = gen.small_scan(cfg=201, ny=24, nx=20, n_t=1 << 12, ncols=4, nrows=2, throw_px=30.0, ncomp=3)
+    noise = gen.noise_params(scan.n_det, fknee=2.0, alpha=3.5, scatter=0.2, cfg=201)
+    op = cmm.Operator(ctx, scan, noise, precision=prec)
+    m = gen.random_maps(3, scan.ny, scan.nx, 1, cfg=203)[0]
+    out = torch.full((3, scan.ny, scan.nx), float("nan"), dtype=torch.float64, device="cuda:0")
+    cmm.cmm_apply_A_noalloc(op.h, torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float64, device="cuda:0"),
+                            out)
+    torch.cuda.synchronize()
+    y, ref = out.cpu().numpy(), om.apply_A(om.make_operator(scan, noise), m)
+    err = max(np.linalg.norm(y - ref) / np.linalg.norm(ref), np.abs(y - ref).max() / np.abs(ref).max())
+    assert err < TOL[prec]
 
 
 def test_noalloc_tiny_patch(cmm, ctx):
