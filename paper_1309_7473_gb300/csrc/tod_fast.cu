@@ -20,6 +20,10 @@
 //                   FP32 partial sums a bounded number of samples (operators with
 //                   more samples on a pixel than that allows bin with the generic
 //                   kernel instead, see kF32HitLimit).
+//   k_fast_flush_maps: the same for the two-detector path, whose binning launch
+//                   fills up to kMaxPartialMaps partial maps (one per group of
+//                   kFlushDets detectors): sums them in FP64 into the accumulator
+//                   and clears them.
 #include <math.h>
 
 #include <algorithm>
