@@ -43,3 +43,33 @@ def test_version_and_error_string(lib):
 def test_binding_wraps_every_symbol(lib):
     from paper_1309_7473_gb300 import cmm
     assert sorted(cmm.EXPORTED) == declared_symbols()
+
+
+def test_null_arguments_are_rejected_before_any_device_work(lib):
+    """Every entry point checks its handles and pointers first: with null ones it
+    returns CMM_ERR_ARG and says why (no crash, no device call); destroying a null
+    handle is a no-op that returns CMM_OK."""
+    from paper_1309_7473_gb300 import cmm
+    ints = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64)
+    for name, argtypes in cmm._SIGS.items():
+        f = getattr(cmm._lib, name)
+        args = [0 if t in ints else 0.0 if t in (ctypes.c_double, ctypes.c_float) else None for t in argtypes]
+        rc = f(*args)
+        if name.endswith("_destroy"):
+            assert rc == 0, name
+        else:
+            assert rc == 1, (name, rc)
+            assert cmm._lib.cmm_last_error(), name
+
+
+def test_context_without_a_gpu_fails_loudly(lib):
+    """No CPU fallback: without a usable device the context cannot be made, and the
+    error names the CUDA call that failed."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1309_7473_gb300 import cmm
+    h = ctypes.c_void_p()
+    assert cmm._lib.cmm_ctx_create(0, None, ctypes.byref(h)) == 2   # CMM_ERR_CUDA
+    assert h.value is None
+    assert b"cuda" in cmm._lib.cmm_last_error().lower()
